@@ -1,0 +1,145 @@
+"""Seeded synthetic inputs for the self-join workloads.
+
+This module only draws random numbers; it holds none of the join's
+arithmetic, so both the CUDA path and the CPU oracle may be fed from it.
+
+Every stream is counter based: value k of stream (seed, sub) is the
+splitmix64 output for state ``seed * G + (sub << 40) + (k + 1) * G`` with
+``G = 0x9E3779B97F4A7C15`` (the splitmix64 increment), so the same numbers
+come out on any machine and any chunking.  A uniform double in [0, 1) is
+``(z >> 11) * 2^-53``.
+
+Workloads (the paper's synthetic datasets, Section VI-A: coordinates i.i.d.
+uniform in [0, 100]^n, FP64):
+  * ``uniform(n, d, seed)`` -- the Syn- datasets.
+  * ``eps_for_neighbors(n, d, k)`` -- the epsilon at which a ball holds k
+    points on average at the uniform density n / 100^d (boundary effects
+    lower the realised mean).
+  * ``clustered(n, d, seed)`` -- skewed density: 90 % of the points from
+    1,000 isotropic Gaussian clusters (centres uniform in [0, 100]^d, sigma
+    log-uniform in [0.1, 5], cluster chosen uniformly), 10 % uniform.
+  * ``serving_requests(count, seed)`` -- a request stream of self-joins of
+    uneven size and dimension with Poisson arrivals.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_G = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_CHUNK = 1 << 22
+
+
+def _splitmix(state: np.ndarray) -> np.ndarray:
+    z = state.copy()
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def raw64(seed: int, sub: int, count: int, start: int = 0) -> np.ndarray:
+    """``count`` raw 64-bit values of stream (seed, sub) from index ``start``."""
+    out = np.empty(count, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        base = (np.uint64(seed & (2**64 - 1)) * _G + np.uint64((sub << 40) & (2**64 - 1)))
+        for c0 in range(0, count, _CHUNK):
+            c1 = min(count, c0 + _CHUNK)
+            k = np.arange(start + c0 + 1, start + c1 + 1, dtype=np.uint64)
+            out[c0:c1] = _splitmix(base + k * _G)
+    return out
+
+
+def unit(seed: int, sub: int, count: int, start: int = 0) -> np.ndarray:
+    """``count`` uniform doubles in [0, 1)."""
+    z = raw64(seed, sub, count, start)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform(n: int, d: int, seed: int, lo: float = 0.0, hi: float = 100.0) -> np.ndarray:
+    """(n, d) row-major FP64 points uniform in [lo, hi)^d."""
+    u = unit(seed, 0, n * d)
+    if lo == 0.0:
+        return (u * hi).reshape(n, d)
+    return (lo + u * (hi - lo)).reshape(n, d)
+
+
+def ball_volume(d: int) -> float:
+    """Volume of the unit ball in d dimensions, pi^(d/2) / Gamma(d/2 + 1)."""
+    return math.pi ** (d / 2.0) / math.gamma(d / 2.0 + 1.0)
+
+
+def eps_for_neighbors(n: int, d: int, k: float, side: float = 100.0) -> float:
+    """epsilon with ball volume x density = k (self excluded)."""
+    rho = n / side ** d
+    return (k / (ball_volume(d) * rho)) ** (1.0 / d)
+
+
+def clustered(n: int, d: int, seed: int, clusters: int = 1000,
+              frac_clustered: float = 0.9) -> np.ndarray:
+    """Skewed-density points (see module docstring), FP64, not clipped."""
+    centres = unit(seed, 1, clusters * d).reshape(clusters, d) * 100.0
+    lu = unit(seed, 2, clusters)
+    sigma = np.exp(math.log(0.1) + lu * (math.log(5.0) - math.log(0.1)))
+    n_cl = int(round(n * frac_clustered))
+    which = np.minimum((unit(seed, 3, n_cl) * clusters).astype(np.int64), clusters - 1)
+    # Box-Muller on pairs of uniforms
+    m = n_cl * d
+    u1 = unit(seed, 4, m)
+    u2 = unit(seed, 5, m)
+    g = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+    pts_cl = centres[which] + g.reshape(n_cl, d) * sigma[which][:, None]
+    pts_bg = unit(seed, 6, (n - n_cl) * d).reshape(n - n_cl, d) * 100.0
+    pts = np.concatenate([pts_cl, pts_bg], axis=0)
+    perm = np.argsort(raw64(seed, 7, n), kind="stable")
+    return np.ascontiguousarray(pts[perm])
+
+
+def serving_requests(count: int, seed: int, rate_hz: float = 1000.0,
+                     n_lo: float = 1e3, n_hi: float = 1e6):
+    """List of dicts {arrival_s, n, d, k, eps, seed} for a stream of
+    self-join requests: Poisson arrivals at ``rate_hz``, n log-uniform in
+    [n_lo, n_hi], d uniform in {2..6}, k uniform in [8, 128] nominal
+    neighbours, points uniform in [0, 100]^d drawn from the request's seed."""
+    u = unit(seed, 10, 4 * count).reshape(count, 4)
+    gaps = -np.log1p(-u[:, 0]) / rate_hz
+    arrivals = np.cumsum(gaps)
+    ns = np.exp(math.log(n_lo) + u[:, 1] * (math.log(n_hi) - math.log(n_lo))).astype(np.int64)
+    ds = 2 + np.minimum((u[:, 2] * 5).astype(np.int64), 4)
+    ks = 8.0 + u[:, 3] * 120.0
+    out = []
+    for r in range(count):
+        n, d = int(ns[r]), int(ds[r])
+        out.append(dict(arrival_s=float(arrivals[r]), n=n, d=d, k=float(ks[r]),
+                        eps=eps_for_neighbors(n, d, float(ks[r])),
+                        seed=int(seed * 1000003 + r)))
+    return out
+
+
+# The five workloads, by name.
+CONFIG1 = dict(name="uniform-2d-20k", n=20000, d=2, seed=1, eps=2.0)
+
+
+def config2(d: int) -> dict:
+    """2,000,000 uniform points in [0,100]^d, 64 mean neighbours."""
+    return dict(name=f"uniform-{d}d-2M", n=2_000_000, d=d, seed=2 + d,
+                eps=eps_for_neighbors(2_000_000, d, 64))
+
+
+def config3(d: int) -> dict:
+    """10,000,000 uniform points in [0,100]^d, 128 mean neighbours."""
+    return dict(name=f"uniform-{d}d-10M", n=10_000_000, d=d, seed=20 + d,
+                eps=eps_for_neighbors(10_000_000, d, 128))
+
+
+def config4(d: int) -> dict:
+    """5,000,000 clustered points, eps = 0.5."""
+    return dict(name=f"clustered-{d}d-5M", n=5_000_000, d=d, seed=40 + d, eps=0.5)
+
+
+def make_points(cfg: dict) -> np.ndarray:
+    if cfg["name"].startswith("clustered"):
+        return clustered(cfg["n"], cfg["d"], cfg["seed"])
+    return uniform(cfg["n"], cfg["d"], cfg["seed"])
