@@ -1,0 +1,353 @@
+"""Throughput benchmark of the GB300 epsilon self-join.
+
+One step = the full hot path (index build, adjacent-cell search, refine,
+pair output) over the 2,000,000-point uniform workload in every dimension
+d = 2..6 with epsilon set for 64 mean neighbours: five self-joins, about
+5.9e8 result pairs, every pair written to device memory.
+
+Printed JSON line (rank 0):
+  value        result pairs/s of the FP32-filter + FP64-recheck join, inputs
+               resident in HBM, device time of the timed steps (CUDA events
+               on the launching stream; L2 flushed between steps)
+  e2e          the same metric through sj_selfjoin with host input and host
+               result (host->device copy of the points and device->host copy
+               of every pair inside the timed region)
+  fp64         the plain FP64 GPU join on the same inputs (same metric)
+  roofline     the search-and-refine kernel of the dominant launch against
+               max(FLOPs / FP32 peak, bytes / HBM bandwidth)
+  cpu_baseline the CPU oracle on the host cores, on a bounded sample
+--impl reference times the CPU oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1803_04120_gb300 import datagen  # noqa: E402
+
+DIMS = (2, 3, 4, 5, 6)
+METRIC = "result pairs/s FP32+FP64-recheck vs plain FP64 (exact set); serving p50/p99 ms"
+UNIT = "pairs/s"
+WORKLOAD = "uniform 2,000,000 points in [0,100]^d for d=2..6, eps for 64 mean neighbours"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6800.0, "fallback"
+    sm_mhz = 2070.0
+    if os.path.exists(path):
+        try:
+            j = json.load(open(path))
+            hbm = float(j.get("hbm_gbs", hbm))
+            sm_mhz = float(j.get("sm_max_mhz", sm_mhz))
+            src = "measured"
+        except Exception:
+            pass
+    # FP32 (CUDA-core) peak: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
+    fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return hbm, src, fp32_tflops
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    out = []
+    for d in DIMS:
+        cfg = datagen.config2(d)
+        out.append((cfg, datagen.make_points(cfg)))
+    return out
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(data, budget_s: float):
+    """Times the oracle's grid search on a sample of query points of every
+    dataset; returns (pairs/s, cores, description)."""
+    from oracle import oracle as orc
+    cores = orc.default_threads()
+    tot_pairs, tot_time, desc = 0, 0.0, []
+    per = budget_s / len(data)
+    for cfg, pts in data:
+        n = pts.shape[0]
+        rng = np.random.default_rng(cfg["d"])
+        m = 2000
+        while True:
+            q = np.sort(rng.choice(n, size=min(m, n), replace=False)).astype(np.uint32)
+            t0 = time.perf_counter()
+            offs, _ = orc.grid_neighbors(pts, cfg["eps"], q, nthreads=cores)
+            dt = time.perf_counter() - t0
+            if dt > per * 0.3 or m >= n:
+                break
+            m = int(min(n, m * max(2.0, per * 0.5 / max(dt, 1e-3))))
+        tot_pairs += int(offs[-1])
+        tot_time += dt
+        desc.append(f"d={cfg['d']}: {len(q)} queries")
+    return tot_pairs / tot_time, cores, "; ".join(desc) + " (grid build included)"
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    from paper_1803_04120_gb300 import sj
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    data = workload()
+    stream = torch.cuda.Stream()
+    d_pts = [torch.from_numpy(p).cuda() for _, p in data]
+    ctx32 = [sj.Context(prec=sj.SJ_PREC_FP32_RECHECK, device=dev, profile=True) for _ in DIMS]
+    ctx64 = sj.Context(prec=sj.SJ_PREC_FP64, device=dev)
+    counts = [c.sj_selfjoin_count(p, cfg["eps"]) for c, p, (cfg, _) in zip(ctx32, d_pts, data)]
+    outs = [torch.empty((c, 2), dtype=torch.int32, device="cuda") for c in counts]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    pairs_step = sum(counts)
+
+    def step(ctxs, s):
+        tot, launches, ev = 0, 0, []
+        for c, p, o, (cfg, _) in zip(ctxs, d_pts, outs, data):
+            tot += c.sj_selfjoin_device(p, cfg["eps"], o, stream=s)
+            launches += c.sj_last_stats()["kernel_launches"]
+        return tot, launches
+
+    def timed(ctxs, steps, warmup):
+        for _ in range(warmup):
+            with torch.cuda.stream(stream):
+                step(ctxs, stream)
+        torch.cuda.synchronize()
+        for c in ctxs:
+            c.sj_profile_read() if c.config.profile else None
+        times, launches = [], 0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            n, l = step(ctxs, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert n == pairs_step, (n, pairs_step)
+            times.append(e0.elapsed_time(e1))
+            launches += l
+        return times, launches
+
+    clk = ClockSampler(dev)
+    clk.start()
+    t32, launches = timed(ctx32, args.steps, args.warmup)
+    clocks = clk.stop()
+    prof = [c.sj_profile_read() for c in ctx32]        # per-d join kernel (ms total, launches)
+    stats = []
+    for c, p, (cfg, _) in zip(ctx32, d_pts, data):     # evaluations per d (one extra count pass)
+        c.sj_selfjoin_count(p, cfg["eps"])
+        stats.append(c.sj_last_stats())
+    ms_step = sum(t32) / len(t32)
+    value = pairs_step / (ms_step / 1e3)
+
+    # plain FP64 join, same inputs, fewer steps (it is much slower)
+    t64, _ = timed([ctx64] * len(DIMS), max(1, min(args.steps, 2)), 1)
+    fp64_value = pairs_step / (sum(t64) / len(t64) / 1e3)
+
+    # end to end: host points in, host pairs out, through sj_selfjoin
+    host_pts = [torch.from_numpy(p).pin_memory() for _, p in data]
+    e2e_times = []
+    for it in range(1 + max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot = 0
+        for c, hp, (cfg, _) in zip(ctx32, host_pts, data):
+            r = c.sj_selfjoin_raw(hp.numpy(), cfg["eps"])
+            tot += c.sj_result_count(r)
+            c.sj_result_free(r)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_times.append(time.perf_counter() - t0)
+        assert tot == pairs_step
+    e2e_value = pairs_step / (sum(e2e_times) / len(e2e_times))
+    h2d = sum(p.nbytes for _, p in data)
+
+    # roofline of the join kernel, per launch, per d
+    hbm, psrc, fp32 = peaks()
+    roof_all = []
+    for (cfg, pts), (ms, nl), st, cnt in zip(data, prof, stats, counts):
+        d = cfg["d"]
+        t = ms / max(nl, 1) / 1e3
+        flops = (3 * d - 1) * st["evaluations"]
+        byts = 8 * pts.size + 8 * cnt
+        t_alu, t_hbm = flops / (fp32 * 1e12), byts / (hbm * 1e9)
+        bound = "alu" if t_alu >= t_hbm else "hbm"
+        if bound == "alu":
+            ach, pk, unit = flops / t / 1e12, fp32, "TFLOP/s"
+        else:
+            ach, pk, unit = byts / t / 1e9, hbm, "GB/s"
+        roof_all.append(dict(d=d, bound=bound, achieved=round(ach, 3), peak=round(pk, 1), unit=unit,
+                             frac=round(ach / pk, 4), kernel_ms=round(t * 1e3, 4),
+                             roofline_ms=round(max(t_alu, t_hbm) * 1e3, 4),
+                             evaluations=st["evaluations"], pairs=cnt, rechecks=st["rechecks"]))
+    dom = max(roof_all, key=lambda r: r["kernel_ms"])
+    roofline = dict(bound=dom["bound"], achieved=dom["achieved"], peak=dom["peak"], unit=dom["unit"],
+                    frac=dom["frac"], traffic=None, kernel=f"join_kernel d={dom['d']}",
+                    peak_source=("fp32: 152 SMs x 128 lanes x 2 x max SM clock" if dom["bound"] == "alu"
+                                 else f"hbm_gbs {psrc}"),
+                    all_launches_frac=round(sum(r["roofline_ms"] for r in roof_all)
+                                            / sum(r["kernel_ms"] for r in roof_all), 4))
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded uniform, stands in for the paper's Syn- datasets)",
+        "config": {"workload": WORKLOAD, "n": 2_000_000, "dims": list(DIMS),
+                   "eps": [round(c["eps"], 6) for c, _ in data], "pairs_per_step": pairs_step,
+                   "precision": "FP32 filter with proven margin + FP64 recheck (exact set)",
+                   "unicomp": True, "l2": "flushed between steps (512 MiB write)"},
+        "fp64": {"value": round(fp64_value, 1), "unit": UNIT,
+                 "ms_per_step": round(sum(t64) / len(t64), 4), "speedup_fp32": round(value / fp64_value, 2)},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 8 * pairs_step},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "roofline_all": roof_all,
+        "clocks": clocks,
+    }
+    if not args.no_cpu:
+        v, cores, desc = cpu_oracle_sample(data, args.cpu_budget)
+        line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    for c in ctx32:
+        c.close()
+    ctx64.close()
+    return line
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    data = workload()
+    vals = []
+    cores, desc = None, None
+    for _ in range(args.warmup):
+        cpu_oracle_sample(data, 2.0)
+    t_all = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        v, cores, desc = cpu_oracle_sample(data, args.cpu_budget / max(1, args.steps))
+        t_all.append(time.perf_counter() - t0)
+        vals.append(v)
+    value = statistics.mean(vals)
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t_all), 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD + " (bounded query sample per step)"},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args)
+        if line:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        # replicas: each rank runs the same workload on its own GPU; the
+        # whole-job value is the sum over ranks of pairs over the max time
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        args.no_cpu = args.no_cpu or rank != 0
+        line = run_gpu(args)
+        t = torch.tensor([line["ms_per_step"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            ms = float(t.item())
+            line["n_gpus"] = world
+            line["ms_per_step"] = round(ms, 4)
+            line["value"] = round(world * line["config"]["pairs_per_step"] / (ms / 1e3), 1)
+            line["config"]["parallelism"] = f"replicas x{world}"
+            print(json.dumps(line))
+        dist.destroy_process_group()
+        return
+    print(json.dumps(run_gpu(args)))
+
+
+if __name__ == "__main__":
+    main()

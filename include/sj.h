@@ -1,0 +1,284 @@
+/*
+ * sj.h -- C ABI of the GB300 grid-indexed Euclidean epsilon self-join.
+ *
+ * The operation (Gowanlock & Karsin, "GPU Accelerated Self-join for the
+ * Distance Similarity Metric", Section III): given |D| points of n
+ * dimensions and a distance epsilon, return every ordered pair (i, j) of point
+ * ids with dist(p_i, p_j) <= epsilon, Euclidean distance.  Point ids are the
+ * 0-based row numbers of the input.  Self-pairs (i, i) are included, and
+ * (i, j) is returned exactly when (j, i) is.
+ *
+ * Membership is decided bit-exactly in FP64 as
+ *     s = 0; for j = 0..n-1 { t = x_i[j] - x_j[j]; s = s + t * t; }
+ *     member  <=>  s <= fl(eps * eps)
+ * with every subtraction, product and sum rounded to nearest on its own (no
+ * fused multiply-add).  Comparing squared values is the library's reading of
+ * the Section III predicate dist <= eps; it differs from rounding sqrt(s)
+ * only at rounding ties.  Both precision modes return this exact set:
+ *   SJ_PREC_FP64          distances in FP64 only (the paper's arithmetic);
+ *   SJ_PREC_FP32_RECHECK  distances filtered in FP32 with a proven error
+ *                         margin, and only pairs within that margin of
+ *                         epsilon recomputed in FP64.
+ *
+ * Method: the grid index of Section IV-B/C (cells of side ~epsilon, only
+ * non-empty cells stored: lookup array B of sorted linear cell ids, cell
+ * ranges G into the point permutation A, per-dimension masks M_j), the
+ * bounded adjacent-cell search of Section IV-D, the UNICOMP duplicate-search
+ * removal of Section V-B (each adjacent cell pair compared once, both ordered
+ * pairs emitted), and the result batching of Section V-A (at least 3 batches
+ * for host output, device result buffers bounded by a byte cap).
+ *
+ * Conventions for every call:
+ *   - `pts` is n x d row-major FP64.  It may be a host or a device pointer;
+ *     the library detects which.  The caller keeps ownership; the library
+ *     copies what it needs and does not hold the pointer after the call
+ *     returns (sj_submit: until the request completes, see there).
+ *   - A pair is two consecutive uint32 values (i, j).  Results returned in
+ *     sj_result are library-owned host memory, valid until sj_result_free.
+ *   - Pair order is unspecified unless sj_config.sorted = 1, which orders
+ *     pairs ascending by the 64-bit key (i << 32) | j.
+ *   - Errors: SJ_EINVAL for a NULL argument, n = 0, d outside [1, 8],
+ *     eps <= 0 or non-finite, or any NaN/Inf coordinate; SJ_ERANGE when
+ *     n >= 2^32, a dimension would need 2^31 or more cells, or the product of
+ *     the cell counts reaches 2^63; SJ_ENOMEM when device or pinned memory
+ *     runs out; SJ_ECUDA for any other CUDA error (the message is in
+ *     sj_last_error); SJ_ETIMEOUT when a bounded device wait expired;
+ *     SJ_EOVERFLOW when a caller-provided output buffer is too small (the
+ *     required count is still reported).
+ *   - One context serves one CUDA device.  sj_submit and sj_poll may be
+ *     called from any thread; all other calls on one context must not run
+ *     concurrently with each other.
+ */
+#ifndef SJ_H
+#define SJ_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SJ_API __attribute__((visibility("default")))
+#else
+#define SJ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sj_ctx sj_ctx;
+typedef struct sj_index sj_index;
+typedef struct sj_result sj_result;
+
+typedef enum {
+    SJ_OK = 0,
+    SJ_PENDING = 1,
+    SJ_EINVAL = -1,
+    SJ_ENOMEM = -2,
+    SJ_ERANGE = -3,
+    SJ_ECUDA = -4,
+    SJ_ETIMEOUT = -5,
+    SJ_EBUSY = -6,
+    SJ_EOVERFLOW = -7,
+    SJ_ENOTFOUND = -8
+} sj_status;
+
+typedef enum { SJ_PREC_FP64 = 0, SJ_PREC_FP32_RECHECK = 1 } sj_precision;
+
+/* Cell lookup used by the adjacent-cell search (Section IV-D).
+ * SJ_LOOKUP_SEARCH binary-searches the sorted array B of non-empty cell ids,
+ * as the paper does.  SJ_LOOKUP_DENSE adds a table over all cells of the grid
+ * (4 bytes per cell) that answers a lookup with one load; SJ_LOOKUP_AUTO uses
+ * it when the grid has at most max(2^25, 16 n) cells.  Results are identical. */
+typedef enum { SJ_LOOKUP_AUTO = 0, SJ_LOOKUP_DENSE = 1, SJ_LOOKUP_SEARCH = 2 } sj_lookup;
+
+typedef struct {
+    int32_t prec;            /* sj_precision; default SJ_PREC_FP32_RECHECK */
+    int32_t unicomp;         /* 1 (default): Section V-B duplicate-search removal;
+                                0: every point searches all 3^n adjacent cells
+                                (Algorithm 1) and emits only (p, q) */
+    uint64_t out_cap_bytes;  /* device memory for result batches of calls that
+                                return host results; default 2 GiB */
+    int32_t min_batches;     /* minimum result batches for host results
+                                (Section V-A uses 3); default 3 */
+    int32_t sorted;          /* 1: host results sorted by (i << 32) | j */
+    int32_t autotune;        /* 1 (default): launch parameters from the tuner */
+    int32_t device;          /* CUDA device ordinal; default 0 */
+    int32_t lookup;          /* sj_lookup; default SJ_LOOKUP_AUTO */
+    int32_t profile;         /* 1: time every join-kernel launch with CUDA
+                                events (read with sj_profile_read) */
+    int32_t max_inflight;    /* sj_submit: most requests admitted at once; default 64 */
+    uint64_t serve_mem_bytes;/* sj_submit: device bytes the admitted requests may
+                                hold together; default 8 GiB */
+    int32_t reserved[8];
+} sj_config;
+
+/* Fills *cfg with the defaults listed above. */
+SJ_API void sj_config_default(sj_config *cfg);
+
+/* Creates a context on cfg->device (NULL cfg: defaults).  *out is set on
+ * success.  Errors: SJ_EINVAL, SJ_ECUDA (no such device), SJ_ENOMEM. */
+SJ_API sj_status sj_create(const sj_config *cfg, sj_ctx **out);
+
+/* Destroys the context.  Results and indexes it produced stay valid;
+ * pending sj_submit requests are cancelled.  NULL is ignored. */
+SJ_API void sj_destroy(sj_ctx *ctx);
+
+/* Message of the last error on this context ("" if none); valid until the
+ * next call on the context. */
+SJ_API const char *sj_last_error(const sj_ctx *ctx);
+
+/* Static name of a status code. */
+SJ_API const char *sj_status_str(sj_status st);
+
+/* ------------------------------------------------------------------ */
+/* Grid index (Section IV-B, IV-C).                                   */
+/* ------------------------------------------------------------------ */
+
+/* Builds the grid index of pts on the device: bounds g_min = min - eps and
+ * g_max = max + eps per dimension (Section IV-B), cells of side
+ * w = eps * (1 + 2^-16), |g_j| = floor((g_max_j - g_min_j) / w) + 1 cells in
+ * dimension j, linear cell ids with dimension 1 fastest, the arrays B, G, A
+ * and M_j of Section IV-C, and the cell-ordered coordinate copies the
+ * search reads.  The index owns device memory until sj_index_free; pts is
+ * not referenced after the call.  Errors as listed in the file comment. */
+SJ_API sj_status sj_build_index(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                         double eps, sj_index **out);
+
+/* Frees the index and its device memory.  NULL is ignored. */
+SJ_API void sj_index_free(sj_index *idx);
+
+/* Sizes and geometry of an index. */
+typedef struct {
+    uint64_t n;              /* |D| */
+    int32_t d;               /* n in the paper's notation: dimensions */
+    int32_t dense;           /* 1 when the dense lookup table was built */
+    double eps;
+    double cell_width;       /* w */
+    uint64_t n_cells;        /* |G| = |B|, non-empty cells */
+    uint64_t grid_cells;     /* product of |g_j|, all cells of the grid */
+    double gmin[8], gmax[8]; /* g_min_j, g_max_j */
+    int64_t ng[8];           /* |g_j| */
+    uint64_t device_bytes;   /* device memory the index holds */
+} sj_index_desc;
+
+SJ_API sj_status sj_index_info(const sj_index *idx, sj_index_desc *out);
+
+/* Copies the Section IV-C arrays to host memory (any pointer may be NULL):
+ *   B[n_cells]          sorted linear ids of the non-empty cells;
+ *   G[n_cells + 1]      cell h holds A[G[h] .. G[h+1]);
+ *   A[n]                point ids in cell order;
+ *   M[d * ceil(max_j |g_j| / 32)]  bit c of row j is set when some point
+ *                       has cell coordinate c in dimension j.
+ * For tests and tools; synchronous. */
+SJ_API sj_status sj_index_export(const sj_index *idx, uint64_t *B, uint32_t *G,
+                          uint32_t *A, uint32_t *M);
+
+/* ------------------------------------------------------------------ */
+/* Self-join.                                                         */
+/* ------------------------------------------------------------------ */
+
+/* The full join into library-owned host memory: builds the index, sizes the
+ * result from a sampled count pass, and streams the pairs out in
+ * max(min_batches, needed) batches whose device buffers stay within
+ * out_cap_bytes, overlapping each batch's kernel with the previous batch's
+ * copy to the host (Section V-A).  A batch that overflows its buffer is
+ * split and re-run.  *out is set on success. */
+SJ_API sj_status sj_selfjoin(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                      double eps, sj_result **out);
+
+/* The same on a built index (which is not modified). */
+SJ_API sj_status sj_selfjoin_index(sj_ctx *ctx, const sj_index *idx, sj_result **out);
+
+/* Device-resident join: d_pairs is a device buffer of cap_pairs pairs
+ * (2 * cap_pairs uint32).  All work is enqueued on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream) and the call returns once *count is
+ * known.  *count receives the number of pairs even when it exceeds
+ * cap_pairs; then only the first cap_pairs are written and the call returns
+ * SJ_EOVERFLOW.  pts may be host or device memory. */
+SJ_API sj_status sj_selfjoin_device(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                             double eps, uint32_t *d_pairs, uint64_t cap_pairs,
+                             uint64_t *count, void *stream);
+
+/* Device-resident join on a built index. */
+SJ_API sj_status sj_selfjoin_index_device(sj_ctx *ctx, const sj_index *idx,
+                                   uint32_t *d_pairs, uint64_t cap_pairs,
+                                   uint64_t *count, void *stream);
+
+/* Counts the pairs without writing them. */
+SJ_API sj_status sj_selfjoin_count(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                            double eps, uint64_t *count);
+
+/* Streaming join: like sj_selfjoin, but each batch is handed to `cb` as it
+ * arrives (pairs points to 2 * k uint32 in pinned host memory, valid only
+ * during the callback) instead of being gathered.  A non-zero return from cb
+ * stops the join (the call then returns SJ_OK after the batches in flight
+ * finish, with no more callbacks). */
+typedef int (*sj_chunk_cb)(const uint32_t *pairs, uint64_t k, void *user);
+SJ_API sj_status sj_selfjoin_stream(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                             double eps, sj_chunk_cb cb, void *user);
+
+/* ------------------------------------------------------------------ */
+/* Results.                                                           */
+/* ------------------------------------------------------------------ */
+
+SJ_API uint64_t sj_result_count(const sj_result *r);
+SJ_API const uint32_t *sj_result_pairs(const sj_result *r);   /* 2 * count uint32 */
+SJ_API void sj_result_free(sj_result *r);                     /* NULL is ignored */
+
+/* ------------------------------------------------------------------ */
+/* Statistics of the last join on a context.                          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t pairs;          /* pairs returned */
+    uint64_t evaluations;    /* point-pair distance evaluations the method
+                                requires: sum over visited cell pairs of
+                                |C_a| |C_b|, home cells |C| (|C| - 1) / 2 under
+                                UNICOMP (|C|^2 without) */
+    uint64_t rechecks;       /* FP32 results inside the margin, recomputed in FP64 */
+    uint64_t n_cells;        /* |G| */
+    uint32_t batches;        /* result batches */
+    uint32_t retries;        /* batches re-run after an overflow */
+    uint64_t estimate;       /* pair count predicted by the sampled pass */
+    double ms_index;         /* host wall time of the index build */
+    double ms_join;          /* host wall time of the join after the index */
+    double ms_total;
+    uint64_t kernel_launches;/* CUDA kernels the library launched for the call */
+} sj_stats;
+
+SJ_API sj_status sj_last_stats(const sj_ctx *ctx, sj_stats *out);
+
+/* With sj_config.profile = 1: total device time (ms, CUDA events on the
+ * launching stream) and launch count of the search-and-refine kernel since
+ * the last read; resets both.  Synchronises the context's work. */
+SJ_API sj_status sj_profile_read(sj_ctx *ctx, double *kernel_ms, uint64_t *launches);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of join requests.                     */
+/* ------------------------------------------------------------------ */
+
+/* Queues a self-join request and returns at once with a ticket.  The pts
+ * buffer is copied before sj_submit returns.  A scheduler thread admits
+ * queued requests while fewer than max_inflight are running and their
+ * estimated device memory fits in serve_mem_bytes; admitted requests share
+ * persistent multi-join kernel launches, so requests that arrive while
+ * others run overlap with them on the device.  Errors: as sj_selfjoin for
+ * the arguments, SJ_ENOMEM if the request alone exceeds serve_mem_bytes. */
+SJ_API sj_status sj_submit(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                    double eps, uint64_t *ticket);
+
+/* SJ_PENDING while the request runs; SJ_OK with *out set when it finished
+ * (the ticket is then consumed); the request's error otherwise;
+ * SJ_ENOTFOUND for an unknown ticket.  wait_ms > 0 blocks up to that long. */
+SJ_API sj_status sj_poll(sj_ctx *ctx, uint64_t ticket, int wait_ms, sj_result **out);
+
+/* Per-request timestamps (seconds since the context was created) of a
+ * finished result: submitted, admitted, completed.  Zero for results not
+ * produced by sj_submit. */
+SJ_API sj_status sj_result_times(const sj_result *r, double *t_submit, double *t_admit,
+                          double *t_done);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SJ_H */

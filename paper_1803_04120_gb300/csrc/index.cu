@@ -1,0 +1,531 @@
+// index.cu -- grid index build (Section IV-B and IV-C).
+//
+// Steps, all on the device of the stream:
+//   1. bounds: per-dimension min and max of the points (one host read-back,
+//      the only synchronisation of the build); the host derives
+//      g_min = min - eps, g_max = max + eps, the cell side w = eps (1 + 2^-16),
+//      |g_j| = floor((g_max_j - g_min_j) / w) + 1 and the FP32 margin.
+//   2. cell ids: c_j = floor((x_j - g_min_j) * (1 / w)) and the linear id
+//      sum_j c_j * prod_{k<j} |g_k| (dimension 1 fastest), FP64.
+//   3. sort by cell: a counting sort through a table over all grid cells
+//      when the grid is small (the table then doubles as the dense lookup),
+//      else an LSD radix sort.  The sorted point ids are the array A.
+//   4. run-length compaction: B (sorted ids of the non-empty cells) and G
+//      (start of each cell's range in A; cell h holds A[G[h] .. G[h+1])).
+//   5. cell coordinates of every non-empty cell and the occupancy bitmaps
+//      M_j (bit c of M_j set when some point has coordinate c in dim j).
+//   6. cell-ordered point records: FP32 y_j = fl32(x_j - g_min_j) followed by
+//      the point id (16 or 32 bytes per point, TMA/bulk-copy friendly), and
+//      on demand the FP64 coordinates with the id.
+//   7. work items (cell h, query block b): one per 32 points of each cell.
+// Arrays whose length depends on |G| are allocated at their upper bound
+// (|G| <= n), so no count has to come back to the host.
+#include <cmath>
+#include <cstring>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__host__ __device__ inline double from_order_key(unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & 0x7fffffffffffffffULL) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    std::memcpy(&x, &b, sizeof(x));
+    return x;
+#endif
+}
+
+// minmax[2j] = min over points of x_j (order key), minmax[2j+1] = max.
+// flag[0] |= 1 when a coordinate is NaN or infinite.
+__global__ void __launch_bounds__(kThreads) bounds_kernel(const double *__restrict__ pts,
+                                                          uint64_t n, int d,
+                                                          unsigned long long *minmax,
+                                                          uint32_t *flag) {
+    unsigned long long lo[kMaxDim], hi[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) { lo[j] = ~0ULL; hi[j] = 0ULL; }
+    bool bad = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < kMaxDim; ++j) {
+            if (j < d) {
+                double x = pts[i * d + j];
+                unsigned long long b = (unsigned long long)__double_as_longlong(x);
+                bad |= (b & 0x7ff0000000000000ULL) == 0x7ff0000000000000ULL;
+                unsigned long long k = order_key(x);
+                lo[j] = k < lo[j] ? k : lo[j];
+                hi[j] = k > hi[j] ? k : hi[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < d) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[j], o);
+                unsigned long long b = __shfl_xor_sync(0xffffffffu, hi[j], o);
+                lo[j] = a < lo[j] ? a : lo[j];
+                hi[j] = b > hi[j] ? b : hi[j];
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&minmax[2 * j], lo[j]);
+                atomicMax(&minmax[2 * j + 1], hi[j]);
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+__global__ void init_minmax_kernel(unsigned long long *minmax, int d, uint32_t *flag) {
+    int j = threadIdx.x;
+    if (j < d) { minmax[2 * j] = ~0ULL; minmax[2 * j + 1] = 0ULL; }
+    if (j == 0) *flag = 0;
+}
+
+struct CellParams {
+    int d;
+    double gmin[kMaxDim];
+    double inv_w;
+    int64_t ng[kMaxDim];
+    uint64_t stride[kMaxDim];
+};
+
+__device__ __forceinline__ uint64_t linear_cell(const double *p, const CellParams &cp) {
+    uint64_t id = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < cp.d) {
+            double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
+            int64_t c = (int64_t)floor(q);
+            c = c < 0 ? 0 : c;
+            c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+            id += (uint64_t)c * cp.stride[j];
+        }
+    }
+    return id;
+}
+
+// Linear cell id of each point; with a dense count table also the point's
+// rank inside its cell.
+__global__ void __launch_bounds__(kThreads) cell_kernel(const double *__restrict__ pts, uint64_t n,
+                                                        CellParams cp, uint64_t *__restrict__ key,
+                                                        uint32_t *__restrict__ val,
+                                                        uint32_t *__restrict__ count) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t id = linear_cell(pts + i * cp.d, cp);
+    key[i] = id;
+    if (count)
+        val[i] = atomicAdd(&count[id], 1u);
+    else
+        val[i] = (uint32_t)i;
+}
+
+// Counting-sort scatter: A[lut[id] + rank] = i, sorted key alongside.
+__global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *__restrict__ key,
+                                                           const uint32_t *__restrict__ rank,
+                                                           const uint32_t *__restrict__ lut,
+                                                           uint64_t n, uint32_t *__restrict__ A,
+                                                           uint64_t *__restrict__ skey) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t id = key[i];
+    uint32_t pos = lut[id] + rank[i];
+    A[pos] = (uint32_t)i;
+    skey[pos] = id;
+}
+
+__global__ void __launch_bounds__(kThreads) head_kernel(const uint64_t *__restrict__ skey,
+                                                        uint64_t n, uint32_t *__restrict__ head) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    head[k] = (k == 0 || skey[k] != skey[k - 1]) ? 1u : 0u;
+}
+
+// head[] holds the exclusive scan of the head flags; a position k starts a
+// cell when the scan steps at k.
+__global__ void __launch_bounds__(kThreads) rle_kernel(const uint64_t *__restrict__ skey,
+                                                       const uint32_t *__restrict__ hscan, uint64_t n,
+                                                       const uint32_t *__restrict__ n_cells,
+                                                       uint64_t *__restrict__ B,
+                                                       uint32_t *__restrict__ G) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    bool is_head = (k == 0) || (skey[k] != skey[k - 1]);
+    if (is_head) {
+        uint32_t h = hscan[k];
+        B[h] = skey[k];
+        G[h] = (uint32_t)k;
+    }
+    if (k == 0) G[*n_cells] = (uint32_t)n;
+}
+
+__global__ void __launch_bounds__(kThreads) cells_kernel(const uint64_t *__restrict__ B,
+                                                         const uint32_t *__restrict__ n_cells,
+                                                         CellParams cp, uint32_t mwords,
+                                                         int32_t *__restrict__ cc,
+                                                         uint32_t *__restrict__ M) {
+    uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= *n_cells) return;
+    uint64_t id = B[h];
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < cp.d) {
+            uint64_t c = (id / cp.stride[j]) % (uint64_t)cp.ng[j];
+            cc[h * cp.d + j] = (int32_t)c;
+            if (M) {
+                uint32_t *w = &M[(uint64_t)j * mwords + (c >> 5)];
+                uint32_t bit = 1u << (c & 31);
+                if ((*(volatile uint32_t *)w & bit) == 0) atomicOr(w, bit);
+            }
+        }
+    }
+}
+
+// FP32 record: y_j = fl32(x_j - g_min_j) for j < d, then the point id.
+__global__ void __launch_bounds__(kThreads) rec32_kernel(const double *__restrict__ pts,
+                                                         const uint32_t *__restrict__ A, uint64_t n,
+                                                         CellParams cp, int rs,
+                                                         float *__restrict__ rec) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t i = A[k];
+    const double *p = pts + (uint64_t)i * cp.d;
+    float *r = rec + k * rs;
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j)
+        if (j < cp.d) r[j] = __double2float_rn(__dsub_rn(p[j], cp.gmin[j]));
+    r[cp.d] = __uint_as_float(i);
+    for (int j = cp.d + 1; j < rs; ++j) r[j] = 0.0f;
+}
+
+__global__ void __launch_bounds__(kThreads) rec64_kernel(const double *__restrict__ pts,
+                                                         const uint32_t *__restrict__ A, uint64_t n,
+                                                         int d, int rs, double *__restrict__ rec) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t i = A[k];
+    const double *p = pts + (uint64_t)i * d;
+    double *r = rec + k * rs;
+    for (int j = 0; j < d; ++j) r[j] = p[j];
+    r[d] = __longlong_as_double((long long)i);
+    for (int j = d + 1; j < rs; ++j) r[j] = 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) item_count_kernel(const uint32_t *__restrict__ G,
+                                                              const uint32_t *__restrict__ n_cells,
+                                                              uint64_t cap,
+                                                              uint32_t *__restrict__ cnt) {
+    uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= cap) return;
+    uint32_t nc = *n_cells;
+    cnt[h] = h < nc ? (G[h + 1] - G[h] + kQueryBlock - 1) / kQueryBlock : 0u;
+}
+
+__global__ void __launch_bounds__(kThreads) item_fill_kernel(const uint32_t *__restrict__ G,
+                                                             const uint32_t *__restrict__ n_cells,
+                                                             const uint32_t *__restrict__ off,
+                                                             uint2 *__restrict__ items) {
+    uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= *n_cells) return;
+    uint32_t nb = (G[h + 1] - G[h] + kQueryBlock - 1) / kQueryBlock;
+    uint32_t o = off[h];
+    for (uint32_t b = 0; b < nb; ++b) items[o + b] = make_uint2((uint32_t)h, b);
+}
+
+inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// FP32 filter thresholds.  Notation: u = 2^-24, v = 2^-53, a_j = x_j - g_min_j
+// with 0 <= a_j <= A_j, the stored coordinate y_j = fl32(fl64(a_j)) and
+// Delta = x_p - x_q.
+//  * |y_j - a_j| <= A_j (u + v + uv) + 2^-150 =: rho_j, so the FP32 difference
+//    vector delta = y_p - y_q satisfies ||delta - Delta|| <= H = ||2 rho||.
+//  * the FP32 sum s32 of d squares of t_j = fl32(delta_j) (product and sum
+//    rounded, fused or not) obeys
+//    (1-u)^2 (1-g32) ||delta||^2 - a32 <= s32 <= (1+u)^2 (1+g32) ||delta||^2 + a32
+//    with g32 = (d+1)u / (1-(d+1)u) and a32 = 2d 2^-149 (subnormal results).
+//  * the FP64 predicate value obeys |s64 - ||Delta||^2| <= g64 ||Delta||^2 + a64,
+//    g64 = (d+3)v / (1-(d+3)v), a64 = 2d 2^-1074.
+// "member" certain:  s32 <= lo  =>  ||delta|| <= r_lo  =>  ||Delta|| <= r_lo + H
+//    =>  s64 <= (1+g64)(r_lo+H)^2 + a64 <= E2, solved for lo.
+// "not a member" certain: s64 <= E2 => ||Delta|| <= R2 => s32 <= hi, so
+//    s32 > hi => s64 > E2.
+void fp32_margin(Geometry &g) {
+    const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
+    const int d = g.d;
+    double H2 = 0.0, Amax = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double A = (g.gmax[j] - g.gmin[j]) * (1.0 + 4.0 * v);
+        Amax = A > Amax ? A : Amax;
+        double rho = A * (u + v + u * v) + std::ldexp(1.0, -150);
+        H2 += 4.0 * rho * rho;
+    }
+    double H = std::sqrt(H2) * (1.0 + 4.0 * v);
+    const double g32 = (d + 1) * u / (1.0 - (d + 1) * u);
+    const double a32 = 2.0 * d * std::ldexp(1.0, -149);
+    const double g64 = (d + 3) * v / (1.0 - (d + 3) * v);
+    const double a64 = 2.0 * d * std::ldexp(1.0, -1074);
+    const double safety = std::ldexp(1.0, -20);  // covers rounding of this computation
+    g.fp32_ok = 0;
+    g.lo32 = -1.0f;
+    g.hi32 = 0.0f;
+    if (!std::isfinite(g.E2) || !(Amax < std::ldexp(1.0, 100)) || g.E2 < std::ldexp(1.0, -100))
+        return;
+    // hi: largest s32 a member can produce
+    double R2 = std::sqrt((g.E2 + a64) / (1.0 - g64)) * (1.0 + 4.0 * v);
+    double hi = (1.0 + u) * (1.0 + u) * (1.0 + g32) * (R2 + H) * (R2 + H) + a32;
+    hi *= (1.0 + safety);
+    if (!(hi < std::ldexp(1.0, 100))) return;
+    float hi32 = (float)hi;
+    if ((double)hi32 < hi) hi32 = std::nextafter(hi32, INFINITY);
+    // lo: largest s32 that still guarantees membership
+    double R1 = std::sqrt((g.E2 - a64) / (1.0 + g64)) * (1.0 - 4.0 * v) - H;
+    float lo32 = -1.0f;
+    if (R1 > 0.0) {
+        double lo = (1.0 - u) * (1.0 - u) * (1.0 - g32) * R1 * R1 - a32;
+        lo *= (1.0 - safety);
+        if (lo > 0.0) {
+            lo32 = (float)lo;
+            if ((double)lo32 > lo) lo32 = std::nextafter(lo32, -INFINITY);
+        }
+    }
+    // a band wider than half of E2 makes the filter pointless
+    if ((double)hi32 - (double)(lo32 > 0 ? lo32 : 0.0f) > 0.5 * g.E2) return;
+    g.lo32 = lo32;
+    g.hi32 = hi32;
+    g.fp32_ok = 1;
+}
+
+}  // namespace
+
+void free_index(Index &ix, cudaStream_t s) {
+    DevBuf *all[] = {&ix.pts, &ix.rec32, &ix.rec64, &ix.A, &ix.B, &ix.G,
+                     &ix.cc,  &ix.M,     &ix.lut,   &ix.items, &ix.counts_dev};
+    for (DevBuf *b : all) dev_free(*b, s);
+}
+
+// Small device scratch for counts that the host may read later.
+struct BuildScratch {
+    DevBuf minmax, counts;  // counts: [0] flag, [1] n_cells, [2] n_items, [3] lut total
+};
+
+sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
+                      int lookup_mode, cudaStream_t s, Index &ix) {
+    ix = Index();
+    ix.owner_stream = s;
+    if (pts_any == nullptr || n == 0 || d < 1 || d > kMaxDim || !(eps > 0.0) || !std::isfinite(eps))
+        return fail(err, SJ_EINVAL, "invalid argument (pts, n, d in [1,8], eps > 0 finite)");
+    if (n >= (1ull << 32)) return fail(err, SJ_ERANGE, "n must be below 2^32");
+    Geometry &g = ix.g;
+    g.d = d;
+    g.n = n;
+    g.eps = eps;
+    g.E2 = eps * eps;
+    g.w = eps * (1.0 + std::ldexp(1.0, -16));
+
+    // 1. points to the device (the index keeps its own copy)
+    SJ_TRY(dev_alloc(err, ix.pts, n * d * sizeof(double), s));
+    SJ_CUDA_TRY(cudaMemcpyAsync(ix.pts.p, pts_any, n * d * sizeof(double), cudaMemcpyDefault, s));
+    const double *pts = static_cast<const double *>(ix.pts.p);
+
+    // bounds
+    DevBuf scratch;
+    SJ_TRY(dev_alloc(err, scratch, (2 * kMaxDim) * sizeof(unsigned long long) + 64, s));
+    unsigned long long *d_minmax = static_cast<unsigned long long *>(scratch.p);
+    uint32_t *d_counts = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxDim);
+    SJ_CUDA_TRY(cudaMemsetAsync(d_counts, 0, 64, s));
+    init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_counts); note_launch();
+    {
+        int blocks = 2 * sm_count(-1);
+        uint64_t need = (n + kThreads - 1) / kThreads;
+        if ((uint64_t)blocks > need) blocks = (int)need;
+        bounds_kernel<<<blocks, kThreads, 0, s>>>(pts, n, d, d_minmax, d_counts); note_launch();
+    }
+    SJ_CUDA_TRY(cudaGetLastError());
+    unsigned long long h_mm[2 * kMaxDim + 8];
+    SJ_CUDA_TRY(cudaMemcpyAsync(h_mm, d_minmax, sizeof(h_mm), cudaMemcpyDeviceToHost, s));
+    SJ_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t *h_counts = reinterpret_cast<const uint32_t *>(h_mm + 2 * kMaxDim);
+    if (h_counts[0] & 1u) { dev_free(scratch, s); return fail(err, SJ_EINVAL, "non-finite coordinate"); }
+
+    // geometry (Section IV-B)
+    double total = 1.0;
+    uint64_t stride = 1;
+    for (int j = 0; j < d; ++j) {
+        double mn = from_order_key(h_mm[2 * j]), mx = from_order_key(h_mm[2 * j + 1]);
+        g.gmin[j] = mn - eps;
+        g.gmax[j] = mx + eps;
+        double cells = std::floor((g.gmax[j] - g.gmin[j]) / g.w) + 1.0;
+        if (!(cells < 2147483648.0)) {
+            dev_free(scratch, s);
+            return fail(err, SJ_ERANGE, "a dimension needs 2^31 or more cells");
+        }
+        g.ng[j] = (int64_t)cells;
+        total *= cells;
+        if (!(total < 9.2e18)) { dev_free(scratch, s); return fail(err, SJ_ERANGE, "grid has 2^63 or more cells"); }
+        g.stride[j] = stride;
+        stride *= (uint64_t)g.ng[j];
+    }
+    g.grid_cells = stride;
+    fp32_margin(g);
+
+    // 2-3. cell ids and the sort by cell
+    uint64_t dense_limit = (uint64_t)16 * n;
+    if (dense_limit < (1ull << 25)) dense_limit = 1ull << 25;
+    bool dense = (lookup_mode == SJ_LOOKUP_DENSE && g.grid_cells < (1ull << 32) - 1) ||
+                 (lookup_mode == SJ_LOOKUP_AUTO && g.grid_cells <= dense_limit);
+    ix.dense = dense ? 1 : 0;
+
+    CellParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.d = d;
+    cp.inv_w = 1.0 / g.w;
+    for (int j = 0; j < d; ++j) {
+        cp.gmin[j] = g.gmin[j];
+        cp.ng[j] = g.ng[j];
+        cp.stride[j] = g.stride[j];
+    }
+
+    DevBuf key, val, skey_buf, head;
+    auto cleanup = [&]() {
+        dev_free(key, s); dev_free(val, s); dev_free(skey_buf, s); dev_free(head, s);
+        dev_free(scratch, s);
+    };
+    sj_status st = SJ_OK;
+#define SJ_B(expr) do { st = (expr); if (st != SJ_OK) { cleanup(); return st; } } while (0)
+#define SJ_BC(expr) do { cudaError_t e__ = (expr); if (e__ != cudaSuccess) { set_cuda_error(err, e__, #expr, __FILE__, __LINE__); cleanup(); return err.st; } } while (0)
+    SJ_B(dev_alloc(err, key, n * sizeof(uint64_t), s));
+    SJ_B(dev_alloc(err, val, n * sizeof(uint32_t), s));
+    SJ_B(dev_alloc(err, ix.A, n * sizeof(uint32_t), s));
+    uint64_t *skey = nullptr;
+    if (dense) {
+        SJ_B(dev_alloc(err, ix.lut, (g.grid_cells + 1) * sizeof(uint32_t), s));
+        uint32_t *lut = static_cast<uint32_t *>(ix.lut.p);
+        SJ_BC(cudaMemsetAsync(lut, 0, (g.grid_cells + 1) * sizeof(uint32_t), s));
+        cell_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, cp, static_cast<uint64_t *>(key.p),
+                                                     static_cast<uint32_t *>(val.p), lut); note_launch();
+        SJ_BC(cudaGetLastError());
+        SJ_B(exclusive_scan_u32(err, lut, lut, g.grid_cells + 1, d_counts + 3, s));
+        SJ_B(dev_alloc(err, skey_buf, n * sizeof(uint64_t), s));
+        skey = static_cast<uint64_t *>(skey_buf.p);
+        scatter_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(key.p),
+                                                        static_cast<uint32_t *>(val.p), lut, n,
+                                                        static_cast<uint32_t *>(ix.A.p), skey); note_launch();
+        SJ_BC(cudaGetLastError());
+    } else {
+        cell_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, cp, static_cast<uint64_t *>(key.p),
+                                                     static_cast<uint32_t *>(val.p), nullptr); note_launch();
+        SJ_BC(cudaGetLastError());
+        int bits = 0;
+        while (bits < 64 && (g.grid_cells - 1) >> bits) ++bits;
+        SJ_B(radix_sort_pairs(err, static_cast<uint64_t *>(key.p), static_cast<uint32_t *>(val.p),
+                              n, bits, s));
+        SJ_BC(cudaMemcpyAsync(ix.A.p, val.p, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        skey = static_cast<uint64_t *>(key.p);
+    }
+
+    // 4. B and G
+    SJ_B(dev_alloc(err, head, n * sizeof(uint32_t), s));
+    uint32_t *hs = static_cast<uint32_t *>(head.p);
+    head_kernel<<<grid_for(n), kThreads, 0, s>>>(skey, n, hs); note_launch();
+    SJ_BC(cudaGetLastError());
+    SJ_B(exclusive_scan_u32(err, hs, hs, n, d_counts + 1, s));
+    SJ_B(dev_alloc(err, ix.B, n * sizeof(uint64_t), s));
+    SJ_B(dev_alloc(err, ix.G, (n + 1) * sizeof(uint32_t), s));
+    // the scan total counts heads before position n = |G|
+    rle_kernel<<<grid_for(n), kThreads, 0, s>>>(skey, hs, n, d_counts + 1,
+                                                 static_cast<uint64_t *>(ix.B.p),
+                                                 static_cast<uint32_t *>(ix.G.p)); note_launch();
+    SJ_BC(cudaGetLastError());
+
+    // 5. cell coordinates and M_j
+    uint64_t maxng = 1;
+    for (int j = 0; j < d; ++j) maxng = (uint64_t)g.ng[j] > maxng ? (uint64_t)g.ng[j] : maxng;
+    ix.mwords = (uint32_t)((maxng + 31) / 32);
+    SJ_B(dev_alloc(err, ix.cc, n * d * sizeof(int32_t), s));
+    SJ_B(dev_alloc(err, ix.M, (uint64_t)d * ix.mwords * sizeof(uint32_t), s));
+    SJ_BC(cudaMemsetAsync(ix.M.p, 0, (uint64_t)d * ix.mwords * sizeof(uint32_t), s));
+    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(ix.B.p), d_counts + 1, cp,
+                                                  ix.mwords, static_cast<int32_t *>(ix.cc.p),
+                                                  static_cast<uint32_t *>(ix.M.p)); note_launch();
+    SJ_BC(cudaGetLastError());
+
+    // 6. FP32 records
+    ix.rs32 = (d + 1 + 3) / 4 * 4;
+    ix.rs64 = (d + 1 + 1) / 2 * 2;
+    SJ_B(dev_alloc(err, ix.rec32, n * ix.rs32 * sizeof(float), s));
+    rec32_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, static_cast<uint32_t *>(ix.A.p), n, cp,
+                                                  ix.rs32, static_cast<float *>(ix.rec32.p)); note_launch();
+    SJ_BC(cudaGetLastError());
+
+    // 7. work items
+    uint32_t *icnt = static_cast<uint32_t *>(val.p);  // reuse: n entries
+    item_count_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint32_t *>(ix.G.p), d_counts + 1, n,
+                                                       icnt); note_launch();
+    SJ_BC(cudaGetLastError());
+    SJ_B(exclusive_scan_u32(err, icnt, icnt, n, d_counts + 2, s));
+    SJ_B(dev_alloc(err, ix.items, n * sizeof(uint2), s));
+    item_fill_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint32_t *>(ix.G.p), d_counts + 1,
+                                                      icnt, static_cast<uint2 *>(ix.items.p)); note_launch();
+    SJ_BC(cudaGetLastError());
+
+    dev_free(key, s);
+    dev_free(val, s);
+    dev_free(skey_buf, s);
+    dev_free(head, s);
+    // keep the counters (n_cells, n_items) on the device inside the index
+    ix.counts_dev = scratch;
+    ix.bytes = ix.pts.bytes + ix.rec32.bytes + ix.A.bytes + ix.B.bytes + ix.G.bytes + ix.cc.bytes +
+               ix.M.bytes + ix.lut.bytes + ix.items.bytes + scratch.bytes;
+#undef SJ_B
+#undef SJ_BC
+    return SJ_OK;
+}
+
+// Builds the FP64 records when a FP64-mode join first needs them.
+sj_status ensure_rec64(Error &err, Index &ix, cudaStream_t s) {
+    if (ix.rec64.p) return SJ_OK;
+    const uint64_t n = ix.g.n;
+    SJ_TRY(dev_alloc(err, ix.rec64, n * ix.rs64 * sizeof(double), s));
+    rec64_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<const double *>(ix.pts.p),
+                                                  static_cast<const uint32_t *>(ix.A.p), n, ix.g.d,
+                                                  ix.rs64, static_cast<double *>(ix.rec64.p)); note_launch();
+    SJ_CUDA_TRY(cudaGetLastError());
+    ix.bytes += ix.rec64.bytes;
+    return SJ_OK;
+}
+
+// Reads |G| and the number of work items back to the host (synchronises s).
+sj_status read_counts(Error &err, Index &ix, cudaStream_t s) {
+    if (ix.counts_read) return SJ_OK;
+    uint32_t h[4];
+    const uint32_t *d_counts = reinterpret_cast<const uint32_t *>(
+        static_cast<unsigned long long *>(ix.counts_dev.p) + 2 * kMaxDim);
+    SJ_CUDA_TRY(cudaMemcpyAsync(h, d_counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SJ_CUDA_TRY(cudaStreamSynchronize(s));
+    ix.n_cells = h[1];
+    ix.n_items = h[2];
+    ix.counts_read = 1;
+    return SJ_OK;
+}
+
+const uint32_t *n_items_dev(const Index &ix) {
+    return reinterpret_cast<const uint32_t *>(static_cast<unsigned long long *>(ix.counts_dev.p) +
+                                              2 * kMaxDim) + 2;
+}
+
+}  // namespace sj

@@ -1,0 +1,180 @@
+// sj_internal.cuh -- internal declarations of the GB300 self-join library.
+//
+// Layout of the library:
+//   scan.cu     device-wide exclusive scan (u32) used by the index build
+//   sort.cu     LSD radix sort of (u64 key, u32 value) for grids too large
+//               for the dense cell table
+//   index.cu    grid index build (Section IV-B, IV-C): bounds, cell ids,
+//               counting or radix sort by cell, B / G / A / M_j, cell-ordered
+//               FP32 and FP64 point records, work items
+//   join.cu     the persistent search-and-refine kernel (Section IV-D, IV-E,
+//               V-B) in both precision modes
+//   api.cu      the C ABI of include/sj.h: contexts, batching (Section V-A),
+//               results, statistics, the serving loop
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sj.h"
+
+namespace sj {
+
+constexpr int kMaxDim = 8;
+constexpr int kWarpsPerBlock = 8;      // 256 threads per block, as in Section VI-B
+constexpr int kQueryBlock = 32;        // query points per work item
+constexpr uint32_t kErrTimeout = 1u;   // device error word bits
+constexpr uint32_t kErrBadRange = 2u;
+
+// Status propagation ---------------------------------------------------------
+
+struct Error {
+    sj_status st = SJ_OK;
+    std::string msg;
+};
+
+#define SJ_CUDA_TRY(expr)                                                        \
+    do {                                                                         \
+        cudaError_t e__ = (expr);                                                \
+        if (e__ != cudaSuccess) {                                                \
+            ::sj::set_cuda_error(err, e__, #expr, __FILE__, __LINE__);           \
+            return err.st;                                                       \
+        }                                                                        \
+    } while (0)
+
+#define SJ_TRY(expr)                                                             \
+    do {                                                                         \
+        sj_status s__ = (expr);                                                  \
+        if (s__ != SJ_OK) return s__;                                            \
+    } while (0)
+
+void set_cuda_error(Error &err, cudaError_t e, const char *expr, const char *file, int line);
+sj_status fail(Error &err, sj_status st, const std::string &msg);
+
+// Device memory from the stream-ordered pool of the context's device.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+sj_status dev_alloc(Error &err, DevBuf &b, size_t bytes, cudaStream_t s);
+void dev_free(DevBuf &b, cudaStream_t s);
+
+// Grid geometry (Section IV-B), computed on the host from the bounds.
+struct Geometry {
+    int d = 0;
+    uint64_t n = 0;
+    double eps = 0, E2 = 0, w = 0;
+    double gmin[kMaxDim] = {}, gmax[kMaxDim] = {};
+    int64_t ng[kMaxDim] = {};
+    uint64_t stride[kMaxDim] = {};     // linear id = sum c_j * stride[j], stride[0] = 1
+    uint64_t grid_cells = 0;           // product of ng
+    // FP32 filter thresholds: s32 <= lo32 -> member, s32 > hi32 -> not a
+    // member, otherwise recompute in FP64.  fp32_ok = 0 when the margin is
+    // unusable and the FP32 mode falls back to FP64 arithmetic.
+    float lo32 = -1.0f, hi32 = 0.0f;
+    int fp32_ok = 0;
+};
+
+// Device-resident grid index.
+struct Index {
+    Geometry g;
+    int dense = 0;                 // dense lookup table built
+    uint64_t n_cells = 0;          // |G|
+    uint32_t n_items = 0;          // work items (cell, query block)
+    uint32_t max_cell = 0;         // largest cell population
+    int rs32 = 0, rs64 = 0;        // record strides (floats / doubles)
+    DevBuf pts;                    // n x d FP64 input copy (row-major)
+    DevBuf rec32;                  // cell-ordered FP32 records: y_0..y_{d-1}, id
+    DevBuf rec64;                  // cell-ordered FP64 records: x_0..x_{d-1}, id
+    DevBuf A;                      // u32[n] point ids in cell order
+    DevBuf B;                      // u64[|G|] sorted linear ids of non-empty cells
+    DevBuf G;                      // u32[|G|+1] cell starts in cell order
+    DevBuf cc;                     // i32[|G| * d] cell coordinates
+    DevBuf M;                      // u32[d * mwords] occupancy bitmaps M_j
+    DevBuf lut;                    // u32[grid_cells + 1] dense: points in cells with smaller id
+    DevBuf items;                  // uint2[n_items] (cell h, query block)
+    DevBuf counts_dev;             // device counters: bounds, |G|, work items
+    uint32_t mwords = 0;
+    int counts_read = 0;
+    uint64_t bytes = 0;
+    cudaStream_t owner_stream = nullptr;
+};
+
+sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
+                      int lookup_mode, cudaStream_t s, Index &ix);
+void free_index(Index &ix, cudaStream_t s);
+sj_status ensure_rec64(Error &err, Index &ix, cudaStream_t s);
+sj_status read_counts(Error &err, Index &ix, cudaStream_t s);
+const uint32_t *n_items_dev(const Index &ix);
+
+// Arguments of one search-and-refine launch.
+struct JoinArgs {
+    // index
+    const float *rec32;
+    const double *rec64;
+    const double *pts;              // original points, FP64 recheck
+    const uint32_t *G;
+    const uint64_t *B;
+    const int32_t *cc;
+    const uint32_t *M;
+    const uint32_t *lut;
+    const uint2 *items;
+    uint32_t item_begin, item_end;
+    uint32_t item_stride;           // sampled launches: every item_stride-th item
+    uint32_t n_cells;
+    uint32_t mwords;
+    int dense;
+    int rs;                         // record stride in elements of the mode's type
+    int n_templates;
+    int32_t ng[kMaxDim];
+    uint64_t stride[kMaxDim];
+    float lo32, hi32;
+    double E2;
+    // output
+    uint2 *out;
+    uint64_t cap;
+    unsigned long long *counter;    // [0] pairs, [1] evaluations, [2] rechecks
+    uint32_t *work;                 // work-item cursor
+    uint32_t *error;                // device error word
+    int count_only;
+    int grab;                       // items taken per cursor bump
+    // per-warp shared-memory layout (bytes)
+    int sm_ranges, sm_queries, sm_chunk, sm_emit, sm_warp;
+    int cb;                         // candidates per chunk
+    int eb;                         // emission staging entries
+    uint64_t timeout_ns;
+};
+
+struct JoinLaunch {
+    int prec_fp32 = 1;
+    int unicomp = 1;
+    int blocks = 0;                 // 0: derive from occupancy
+    int grab = 0;
+    uint32_t item_stride = 1;
+};
+int n_templates(int d, bool uni);
+
+sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
+                      uint32_t item_end, uint2 *out, uint64_t cap,
+                      unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
+                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+
+// Device-wide exclusive scan of u32 (in may equal out).  *d_total receives the
+// sum.  Returns SJ_OK or an error.
+sj_status exclusive_scan_u32(Error &err, const uint32_t *in, uint32_t *out, uint64_t n,
+                             uint32_t *d_total, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) by the low `bits` bits of key.
+sj_status radix_sort_pairs(Error &err, uint64_t *keys, uint32_t *vals, uint64_t n, int bits,
+                           cudaStream_t s);
+
+// Host helpers
+double now_ms();
+// Counts kernel launches of the library (read per call into sj_stats).
+void note_launch();
+uint64_t launches_so_far();
+int sm_count(int device);
+
+}  // namespace sj

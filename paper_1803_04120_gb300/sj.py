@@ -1,0 +1,386 @@
+"""Python binding of the C ABI in ``include/sj.h`` (ctypes, marshalling only).
+
+Every function here converts arguments and calls the function of the same
+name in ``libsj.so``; all of the join runs in the library's CUDA kernels.
+There is no fallback: if the library cannot be built or loaded, or no CUDA
+device is present, the calls raise.
+
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (torch is
+used only to own device memory and streams).  Pairs come back as an
+``(count, 2)`` uint32 array of (i, j) point ids.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+SJ_OK, SJ_PENDING = 0, 1
+SJ_EINVAL, SJ_ENOMEM, SJ_ERANGE, SJ_ECUDA = -1, -2, -3, -4
+SJ_ETIMEOUT, SJ_EBUSY, SJ_EOVERFLOW, SJ_ENOTFOUND = -5, -6, -7, -8
+SJ_PREC_FP64, SJ_PREC_FP32_RECHECK = 0, 1
+SJ_LOOKUP_AUTO, SJ_LOOKUP_DENSE, SJ_LOOKUP_SEARCH = 0, 1, 2
+
+# symbols the header declares (checked by the CPU test suite)
+ABI_FUNCTIONS = (
+    "sj_config_default", "sj_create", "sj_destroy", "sj_last_error", "sj_status_str",
+    "sj_build_index", "sj_index_free", "sj_index_info", "sj_index_export",
+    "sj_selfjoin", "sj_selfjoin_index", "sj_selfjoin_device", "sj_selfjoin_index_device",
+    "sj_selfjoin_count", "sj_selfjoin_stream", "sj_result_count", "sj_result_pairs",
+    "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
+    "sj_result_times",
+)
+
+
+class SJError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+class sj_config(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("unicomp", ctypes.c_int32),
+                ("out_cap_bytes", ctypes.c_uint64), ("min_batches", ctypes.c_int32),
+                ("sorted", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("lookup", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("serve_mem_bytes", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class sj_index_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d", ctypes.c_int32), ("dense", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("cell_width", ctypes.c_double),
+                ("n_cells", ctypes.c_uint64), ("grid_cells", ctypes.c_uint64),
+                ("gmin", ctypes.c_double * 8), ("gmax", ctypes.c_double * 8),
+                ("ng", ctypes.c_int64 * 8), ("device_bytes", ctypes.c_uint64)]
+
+
+class sj_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("evaluations", ctypes.c_uint64),
+                ("rechecks", ctypes.c_uint64), ("n_cells", ctypes.c_uint64),
+                ("batches", ctypes.c_uint32), ("retries", ctypes.c_uint32),
+                ("estimate", ctypes.c_uint64), ("ms_index", ctypes.c_double),
+                ("ms_join", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("kernel_launches", ctypes.c_uint64)]
+
+
+CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
+                            ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libsj.so (building it first when out of date)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        lib = ctypes.CDLL(path)
+        P, u64, i32, f64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "sj_config_default": (None, [ctypes.POINTER(sj_config)]),
+            "sj_create": (i32, [ctypes.POINTER(sj_config), PP]),
+            "sj_destroy": (None, [P]),
+            "sj_last_error": (ctypes.c_char_p, [P]),
+            "sj_status_str": (ctypes.c_char_p, [i32]),
+            "sj_build_index": (i32, [P, P, u64, i32, f64, PP]),
+            "sj_index_free": (None, [P]),
+            "sj_index_info": (i32, [P, ctypes.POINTER(sj_index_desc)]),
+            "sj_index_export": (i32, [P, P, P, P, P]),
+            "sj_selfjoin": (i32, [P, P, u64, i32, f64, PP]),
+            "sj_selfjoin_index": (i32, [P, P, PP]),
+            "sj_selfjoin_device": (i32, [P, P, u64, i32, f64, P, u64,
+                                         ctypes.POINTER(ctypes.c_uint64), P]),
+            "sj_selfjoin_index_device": (i32, [P, P, P, u64, ctypes.POINTER(ctypes.c_uint64), P]),
+            "sj_selfjoin_count": (i32, [P, P, u64, i32, f64, ctypes.POINTER(ctypes.c_uint64)]),
+            "sj_selfjoin_stream": (i32, [P, P, u64, i32, f64, CHUNK_CB, P]),
+            "sj_result_count": (u64, [P]),
+            "sj_result_pairs": (P, [P]),
+            "sj_result_free": (None, [P]),
+            "sj_last_stats": (i32, [P, ctypes.POINTER(sj_stats)]),
+            "sj_profile_read": (i32, [P, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+            "sj_submit": (i32, [P, P, u64, i32, f64, ctypes.POINTER(ctypes.c_uint64)]),
+            "sj_poll": (i32, [P, u64, i32, PP]),
+            "sj_result_times": (i32, [P, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_name(st: int) -> str:
+    try:
+        return load().sj_status_str(st).decode()
+    except Exception:  # pragma: no cover
+        return str(st)
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _host_points(points) -> np.ndarray:
+    a = np.ascontiguousarray(points, dtype=np.float64)
+    if a.ndim != 2:
+        raise ValueError("points must be (n, d)")
+    return a
+
+
+def _points_ptr(points):
+    """(pointer, n, d, keepalive) for a numpy array or a torch tensor."""
+    if hasattr(points, "data_ptr") and hasattr(points, "is_cuda"):
+        t = points
+        if t.dtype.__repr__() != "torch.float64" or t.dim() != 2 or not t.is_contiguous():
+            raise ValueError("device points must be a contiguous (n, d) float64 tensor")
+        return ctypes.c_void_p(t.data_ptr()), t.shape[0], t.shape[1], t
+    a = _host_points(points)
+    return ctypes.c_void_p(a.ctypes.data), a.shape[0], a.shape[1], a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _result_to_numpy(lib, r) -> np.ndarray:
+    n = lib.sj_result_count(r)
+    p = lib.sj_result_pairs(r)
+    out = np.empty((n, 2), dtype=np.uint32)
+    if n:
+        ctypes.memmove(out.ctypes.data, p, n * 8)
+    return out
+
+
+class Context:
+    """A library context (one CUDA device)."""
+
+    def __init__(self, prec: int = SJ_PREC_FP32_RECHECK, unicomp: bool = True,
+                 out_cap_bytes: int = 2 << 30, min_batches: int = 3, sorted: bool = False,
+                 device: int = 0, lookup: int = SJ_LOOKUP_AUTO, profile: bool = False,
+                 max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True):
+        lib = load()
+        cfg = sj_config()
+        lib.sj_config_default(ctypes.byref(cfg))
+        cfg.prec, cfg.unicomp = prec, int(bool(unicomp))
+        cfg.out_cap_bytes, cfg.min_batches, cfg.sorted = out_cap_bytes, min_batches, int(sorted)
+        cfg.device, cfg.lookup, cfg.profile = device, lookup, int(profile)
+        cfg.max_inflight, cfg.serve_mem_bytes, cfg.autotune = max_inflight, serve_mem_bytes, int(autotune)
+        h = ctypes.c_void_p()
+        st = lib.sj_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != SJ_OK:
+            raise SJError(st, "sj_create failed")
+        self._lib, self._h, self.config = lib, h, cfg
+
+    # -- plumbing
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int, what: str):
+        if st != SJ_OK:
+            raise SJError(st, f"{what}: {self._lib.sj_last_error(self._h).decode()}")
+
+    # -- joins
+    def sj_selfjoin(self, points, eps: float) -> np.ndarray:
+        """All pairs within eps, host result, as an (count, 2) uint32 array."""
+        p, n, d, keep = _points_ptr(points)
+        r = ctypes.c_void_p()
+        self._check(self._lib.sj_selfjoin(self._h, p, n, d, float(eps), ctypes.byref(r)), "sj_selfjoin")
+        try:
+            return _result_to_numpy(self._lib, r)
+        finally:
+            self._lib.sj_result_free(r)
+
+    def sj_selfjoin_raw(self, points, eps: float):
+        """Like sj_selfjoin but returns the library's result handle (caller
+        frees it with sj_result_free); avoids the copy into numpy."""
+        p, n, d, keep = _points_ptr(points)
+        r = ctypes.c_void_p()
+        self._check(self._lib.sj_selfjoin(self._h, p, n, d, float(eps), ctypes.byref(r)), "sj_selfjoin")
+        return r
+
+    def sj_result_count(self, r) -> int:
+        return int(self._lib.sj_result_count(r))
+
+    def sj_result_free(self, r):
+        self._lib.sj_result_free(r)
+
+    def sj_selfjoin_device(self, points, eps: float, out, stream=None, raise_overflow=True) -> int:
+        """Join into a device uint32 tensor ``out`` of shape (cap, 2); returns
+        the pair count (which may exceed cap: then SJEOVERFLOW is raised
+        unless raise_overflow is False)."""
+        p, n, d, keep = _points_ptr(points)
+        cap = 0 if out is None else out.shape[0]
+        optr = ctypes.c_void_p(out.data_ptr()) if out is not None and cap else None
+        cnt = ctypes.c_uint64(0)
+        st = self._lib.sj_selfjoin_device(self._h, p, n, d, float(eps), optr, cap,
+                                          ctypes.byref(cnt), _stream_ptr(stream))
+        if st == SJ_EOVERFLOW and not raise_overflow:
+            return int(cnt.value)
+        self._check(st, "sj_selfjoin_device")
+        return int(cnt.value)
+
+    def sj_selfjoin_count(self, points, eps: float) -> int:
+        p, n, d, keep = _points_ptr(points)
+        cnt = ctypes.c_uint64(0)
+        self._check(self._lib.sj_selfjoin_count(self._h, p, n, d, float(eps), ctypes.byref(cnt)),
+                    "sj_selfjoin_count")
+        return int(cnt.value)
+
+    def sj_selfjoin_stream(self, points, eps: float, callback) -> None:
+        """callback(pairs: np.ndarray (k, 2) uint32) per batch; return True to stop."""
+        p, n, d, keep = _points_ptr(points)
+
+        def tramp(ptr, k, user):
+            arr = np.ctypeslib.as_array(ptr, shape=(int(k) * 2,)).reshape(-1, 2).copy()
+            return 1 if callback(arr) else 0
+
+        cb = CHUNK_CB(tramp)
+        self._check(self._lib.sj_selfjoin_stream(self._h, p, n, d, float(eps), cb, None),
+                    "sj_selfjoin_stream")
+
+    # -- index
+    def sj_build_index(self, points, eps: float) -> "Index":
+        p, n, d, keep = _points_ptr(points)
+        h = ctypes.c_void_p()
+        self._check(self._lib.sj_build_index(self._h, p, n, d, float(eps), ctypes.byref(h)),
+                    "sj_build_index")
+        return Index(self, h)
+
+    def sj_selfjoin_index(self, index: "Index") -> np.ndarray:
+        r = ctypes.c_void_p()
+        self._check(self._lib.sj_selfjoin_index(self._h, index._h, ctypes.byref(r)),
+                    "sj_selfjoin_index")
+        try:
+            return _result_to_numpy(self._lib, r)
+        finally:
+            self._lib.sj_result_free(r)
+
+    def sj_selfjoin_index_device(self, index: "Index", out, stream=None) -> int:
+        cap = 0 if out is None else out.shape[0]
+        optr = ctypes.c_void_p(out.data_ptr()) if out is not None and cap else None
+        cnt = ctypes.c_uint64(0)
+        self._check(self._lib.sj_selfjoin_index_device(self._h, index._h, optr, cap,
+                                                        ctypes.byref(cnt), _stream_ptr(stream)),
+                    "sj_selfjoin_index_device")
+        return int(cnt.value)
+
+    # -- serving
+    def sj_submit(self, points, eps: float) -> int:
+        p, n, d, keep = _points_ptr(points)
+        t = ctypes.c_uint64(0)
+        self._check(self._lib.sj_submit(self._h, p, n, d, float(eps), ctypes.byref(t)), "sj_submit")
+        return int(t.value)
+
+    def sj_poll(self, ticket: int, wait_ms: int = 0):
+        """None while pending, else (pairs array, (t_submit, t_admit, t_done))."""
+        r = ctypes.c_void_p()
+        st = self._lib.sj_poll(self._h, ticket, int(wait_ms), ctypes.byref(r))
+        if st == SJ_PENDING:
+            return None
+        self._check(st, "sj_poll")
+        try:
+            ts = [ctypes.c_double() for _ in range(3)]
+            self._lib.sj_result_times(r, *[ctypes.byref(x) for x in ts])
+            return _result_to_numpy(self._lib, r), tuple(x.value for x in ts)
+        finally:
+            self._lib.sj_result_free(r)
+
+    # -- diagnostics
+    def sj_last_stats(self) -> dict:
+        s = sj_stats()
+        self._check(self._lib.sj_last_stats(self._h, ctypes.byref(s)), "sj_last_stats")
+        return {k: getattr(s, k) for k, _ in sj_stats._fields_}
+
+    def sj_profile_read(self):
+        ms = ctypes.c_double(0)
+        n = ctypes.c_uint64(0)
+        self._check(self._lib.sj_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)),
+                    "sj_profile_read")
+        return ms.value, int(n.value)
+
+
+class Index:
+    """A device-resident grid index (Section IV-B/C)."""
+
+    def __init__(self, ctx: Context, h):
+        self._ctx, self._h = ctx, h
+
+    def free(self):
+        if self._h:
+            self._ctx._lib.sj_index_free(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def sj_index_info(self) -> dict:
+        dsc = sj_index_desc()
+        st = self._ctx._lib.sj_index_info(self._h, ctypes.byref(dsc))
+        if st != SJ_OK:
+            raise SJError(st, "sj_index_info")
+        d = dsc.d
+        return dict(n=dsc.n, d=d, dense=dsc.dense, eps=dsc.eps, cell_width=dsc.cell_width,
+                    n_cells=dsc.n_cells, grid_cells=dsc.grid_cells,
+                    gmin=list(dsc.gmin)[:d], gmax=list(dsc.gmax)[:d], ng=list(dsc.ng)[:d],
+                    device_bytes=dsc.device_bytes)
+
+    def sj_index_export(self):
+        """(B, G, A, M) as numpy arrays (Section IV-C)."""
+        info = self.sj_index_info()
+        nc, n, d = info["n_cells"], info["n"], info["d"]
+        mwords = (max(info["ng"]) + 31) // 32
+        B = np.empty(nc, np.uint64)
+        G = np.empty(nc + 1, np.uint32)
+        A = np.empty(n, np.uint32)
+        M = np.empty((d, mwords), np.uint32)
+        st = self._ctx._lib.sj_index_export(self._h, B.ctypes.data, G.ctypes.data, A.ctypes.data,
+                                            M.ctypes.data)
+        if st != SJ_OK:
+            raise SJError(st, "sj_index_export")
+        return B, G, A, M
+
+
+def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:
+    """(count, 2) uint32 pairs -> sorted uint64 keys (i << 32) | j."""
+    p = np.asarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    k = (p[:, 0].astype(np.uint64) << np.uint64(32)) | p[:, 1].astype(np.uint64)
+    k.sort()
+    return k

@@ -1,0 +1,321 @@
+"""Parity of the CUDA self-join with the CPU oracle (GPU required).
+
+Every comparison is element-by-element on sorted (i << 32) | j keys: the
+result must equal the oracle's exactly, in both precision modes, with and
+without UNICOMP, through every entry point.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1803_04120_gb300 import datagen, sj
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MODES = [(sj.SJ_PREC_FP32_RECHECK, True), (sj.SJ_PREC_FP64, True),
+         (sj.SJ_PREC_FP32_RECHECK, False), (sj.SJ_PREC_FP64, False)]
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    out = {}
+    for prec, uni in MODES:
+        for lookup in (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH):
+            out[(prec, uni, lookup)] = sj.Context(prec=prec, unicomp=uni, lookup=lookup)
+    yield out
+    for c in out.values():
+        c.close()
+
+
+def gpu_keys(ctx, pts, eps):
+    return sj.pairs_to_keys(ctx.sj_selfjoin(pts, eps))
+
+
+def assert_same(got, want, what=""):
+    if got.shape != want.shape or not np.array_equal(got, want):
+        gs, ws = set(got.tolist()), set(want.tolist())
+        missing = sorted(ws - gs)[:5]
+        extra = sorted(gs - ws)[:5]
+        dup = got.size - len(gs)
+        pytest.fail(f"{what}: got {got.size} want {want.size}; missing {[(k >> 32, k & 0xffffffff) for k in missing]} "
+                    f"extra {[(k >> 32, k & 0xffffffff) for k in extra]} duplicates {dup}")
+
+
+# ------------------------------------------------------------------ small cases
+
+@pytest.mark.parametrize("prec,uni", MODES)
+def test_config1_equals_bruteforce(ctxs, prec, uni):
+    cfg = datagen.CONFIG1
+    pts = datagen.make_points(cfg)
+    want = orc.bruteforce(pts, cfg["eps"])
+    for lookup in (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH):
+        got = gpu_keys(ctxs[(prec, uni, lookup)], pts, cfg["eps"])
+        assert_same(got, want, f"config1 prec={prec} unicomp={uni} lookup={lookup}")
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_random_all_dims_all_modes(ctxs, d):
+    rng = np.random.default_rng(1000 + d)
+    for trial in range(3):
+        n = int(rng.integers(50, 3000))
+        pts = rng.uniform(-10, 10, size=(n, d))
+        if trial == 1:
+            pts[n // 3: 2 * n // 3] = pts[: 2 * n // 3 - n // 3]   # duplicates
+        vol = 20.0 ** d
+        k = float(rng.choice([4.0, 40.0, 400.0]))
+        eps = (k * vol / (n * datagen.ball_volume(d))) ** (1.0 / d)
+        want = orc.grid_join(pts, eps)
+        for key, ctx in ctxs.items():
+            got = gpu_keys(ctx, pts, eps)
+            assert_same(got, want, f"d={d} trial={trial} n={n} eps={eps} mode={key}")
+
+
+def test_heavy_cell_spans_many_items_and_chunks(ctxs):
+    # one cell with 3000 points (many query blocks and candidate chunks) plus
+    # a sparse background
+    rng = np.random.default_rng(5)
+    dense = rng.uniform(0, 0.2, size=(3000, 2))
+    bg = rng.uniform(0, 50, size=(500, 2))
+    pts = np.concatenate([dense, bg])
+    eps = 0.25
+    want = orc.grid_join(pts, eps)
+    for key, ctx in ctxs.items():
+        assert_same(gpu_keys(ctx, pts, eps), want, f"heavy cell {key}")
+
+
+def test_edge_cases(ctxs):
+    ctx = ctxs[(sj.SJ_PREC_FP32_RECHECK, True, sj.SJ_LOOKUP_AUTO)]
+    # a single point
+    one = np.array([[1.0, 2.0, 3.0]])
+    assert_same(gpu_keys(ctx, one, 0.5), np.array([0], dtype=np.uint64), "n=1")
+    # all points identical: n^2 pairs
+    same = np.full((100, 4), 7.25)
+    assert gpu_keys(ctx, same, 1e-9).size == 100 * 100
+    # eps larger than the data range: all pairs
+    pts = datagen.uniform(300, 3, seed=9)
+    assert gpu_keys(ctx, pts, 1000.0).size == 300 * 300
+    # eps tiny: self-pairs only
+    k = gpu_keys(ctx, pts, 1e-12)
+    assert_same(k, (np.arange(300, dtype=np.uint64) << np.uint64(32)) | np.arange(300, dtype=np.uint64), "tiny eps")
+    # negative and large-offset coordinates
+    off = datagen.uniform(2000, 2, seed=10) - 1e6
+    assert_same(gpu_keys(ctx, off, 0.7), orc.grid_join(off, 0.7), "offset coordinates")
+
+
+@pytest.mark.parametrize("d,m", [(2, 30), (3, 12), (4, 7)])
+def test_unit_lattice_closed_form_gpu(ctxs, d, m):
+    axes = [np.arange(m, dtype=np.float64)] * d
+    pts = np.stack([g.ravel() for g in np.meshgrid(*axes, indexing="ij")], axis=1)
+    expect = m ** d + 2 * d * (m - 1) * m ** (d - 1)
+    for key, ctx in ctxs.items():
+        assert gpu_keys(ctx, pts, 1.0).size == expect, key
+        assert gpu_keys(ctx, pts, 1.0 - 2.0 ** -40).size == m ** d, key
+
+
+def test_fma_contraction_detector_gpu(ctxs):
+    # fl(fl(a0^2) + fl(a1^2)) > fl(eps^2) >= fma(a1, a1, fl(a0^2)): not a member
+    pts = np.array([[0.9433567169983137, 0.6489745531369242], [0.0, 0.0]])
+    eps = 1.1450283254684606
+    for key, ctx in ctxs.items():
+        got = gpu_keys(ctx, pts, eps)
+        assert_same(got, np.array([0, (1 << 32) | 1], dtype=np.uint64), f"fma detector {key}")
+
+
+def test_adversarial_band_pairs(ctxs):
+    # pairs at squared distance E2 * (1 +- k 2^-24) and +- a few FP64 ulps:
+    # inside the FP32 margin, so the FP64 recheck must decide them
+    rng = np.random.default_rng(77)
+    for d in (2, 3, 6):
+        eps = 0.37
+        base = rng.uniform(0, 30, size=(400, d))
+        extra = []
+        for p in base:
+            v = rng.normal(size=d)
+            v /= np.linalg.norm(v)
+            f = 1.0 + float(rng.choice([-3, -1, 0, 1, 3])) * 2.0 ** -24 * float(rng.random())
+            if rng.random() < 0.5:
+                f = 1.0 + float(rng.integers(-4, 5)) * 2.0 ** -52
+            extra.append(p + v * eps * f)
+        pts = np.concatenate([base, np.array(extra)])
+        want = orc.grid_join(pts, eps)
+        for key, ctx in ctxs.items():
+            assert_same(gpu_keys(ctx, pts, eps), want, f"band d={d} {key}")
+        st = ctxs[(sj.SJ_PREC_FP32_RECHECK, True, sj.SJ_LOOKUP_AUTO)]
+        st.sj_selfjoin(pts, eps)
+        assert st.sj_last_stats()["rechecks"] > 0
+
+
+def test_cell_boundary_plants(ctxs):
+    rng = np.random.default_rng(8)
+    for d in (2, 3, 5):
+        eps = 0.3
+        base = rng.uniform(0, 3, size=(200, d))
+        extra = []
+        for p in base:
+            k = int(rng.integers(0, d))
+            for f in (1.0, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -52):
+                q = p.copy()
+                q[k] += eps * f
+                extra.append(q)
+        pts = np.concatenate([base, np.array(extra)])
+        want = orc.bruteforce(pts, eps)
+        for key, ctx in ctxs.items():
+            assert_same(gpu_keys(ctx, pts, eps), want, f"boundary d={d} {key}")
+
+
+# ------------------------------------------------------------------ entry points
+
+def test_device_entry_point_and_overflow():
+    torch = pytest.importorskip("torch")
+    pts = datagen.uniform(5000, 3, seed=12)
+    eps = 3.0
+    want = orc.grid_join(pts, eps)
+    with sj.Context() as ctx:
+        d_pts = torch.from_numpy(pts).cuda()
+        out = torch.empty((want.size + 10, 2), dtype=torch.int32, device="cuda")
+        n = ctx.sj_selfjoin_device(d_pts, eps, out)
+        assert n == want.size
+        got = sj.pairs_to_keys(out[:n].cpu().numpy().view(np.uint32))
+        assert_same(got, want, "device entry point")
+        # host points through the device entry point
+        n2 = ctx.sj_selfjoin_device(pts, eps, out)
+        assert n2 == want.size
+        # too small: the count is still reported
+        small = torch.empty((100, 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(sj.SJError) as ei:
+            ctx.sj_selfjoin_device(d_pts, eps, small)
+        assert ei.value.status == sj.SJ_EOVERFLOW
+        assert ctx.sj_selfjoin_device(d_pts, eps, small, raise_overflow=False) == want.size
+        assert ctx.sj_selfjoin_count(d_pts, eps) == want.size
+        st = ctx.sj_last_stats()
+        assert st["evaluations"] > 0
+
+
+def test_batching_small_cap_many_batches_and_retries():
+    pts = datagen.uniform(20000, 2, seed=13)
+    eps = 1.5
+    want = orc.grid_join(pts, eps)
+    for cap in (1 << 16, 1 << 18, 1 << 20):
+        with sj.Context(out_cap_bytes=cap, sorted=True) as ctx:
+            got = ctx.sj_selfjoin(pts, eps)
+            k = (got[:, 0].astype(np.uint64) << np.uint64(32)) | got[:, 1].astype(np.uint64)
+            assert np.all(np.diff(k.view(np.int64)) > 0), "sorted output"
+            assert_same(k, want, f"cap={cap}")
+            st = ctx.sj_last_stats()
+            assert st["batches"] >= 3
+
+
+def test_stream_entry_point():
+    pts = datagen.uniform(20000, 3, seed=14)
+    eps = 2.5
+    want = orc.grid_join(pts, eps)
+    chunks = []
+    with sj.Context(out_cap_bytes=1 << 20) as ctx:
+        ctx.sj_selfjoin_stream(pts, eps, lambda a: chunks.append(a) and False)
+    got = sj.pairs_to_keys(np.concatenate(chunks))
+    assert len(chunks) >= 3
+    assert_same(got, want, "stream")
+
+
+def test_index_reuse_and_worked_example():
+    fx = json.load(open(os.path.join(GOLDEN, "worked_example_sec4d.json")))
+    pts = np.array(fx["points"])
+    paper = fx["paper"]
+    with sj.Context() as ctx:
+        ix = ctx.sj_build_index(pts, fx["eps"])
+        info = ix.sj_index_info()
+        assert info["ng"] == paper["cells_per_dim"]
+        assert info["n_cells"] == paper["non_empty_cells"]
+        B, G, A, M = ix.sj_index_export()
+        assert B.tolist() == fx["constructed"]["non_empty_linear_ids"]
+        h6 = paper["C6_linear_id"]
+        h = B.tolist().index(h6)
+        assert h + 1 == 6
+        assert sorted(A[G[h]:G[h + 1]].tolist()) == sorted(paper["C6_points"])
+        assert B.tolist().index(paper["query_cell_linear_id"]) + 1 == paper["query_cell_rank_1based"]
+        # M_1: column 3 empty, the others occupied; M_2: all rows occupied
+        assert [(int(M[0, 0]) >> c) & 1 for c in range(7)] == [1, 1, 1, 0, 1, 1, 1]
+        assert [(int(M[1, 0]) >> c) & 1 for c in range(7)] == [1] * 7
+        # G tiles [0, n) and A is a permutation
+        assert G[0] == 0 and G[-1] == len(pts) and np.all(np.diff(G.astype(np.int64)) > 0)
+        assert sorted(A.tolist()) == list(range(len(pts)))
+        want = orc.bruteforce(pts, fx["eps"])
+        assert_same(sj.pairs_to_keys(ctx.sj_selfjoin_index(ix)), want, "index reuse")
+        assert_same(sj.pairs_to_keys(ctx.sj_selfjoin_index(ix)), want, "index reuse twice")
+        ix.free()
+
+
+def test_invalid_arguments():
+    with sj.Context() as ctx:
+        pts = np.zeros((10, 2))
+        for bad_eps in (0.0, -1.0, float("nan"), float("inf")):
+            with pytest.raises(sj.SJError) as ei:
+                ctx.sj_selfjoin(pts, bad_eps)
+            assert ei.value.status == sj.SJ_EINVAL
+        bad = pts.copy()
+        bad[3, 1] = np.nan
+        with pytest.raises(sj.SJError) as ei:
+            ctx.sj_selfjoin(bad, 1.0)
+        assert ei.value.status == sj.SJ_EINVAL
+        with pytest.raises(sj.SJError) as ei:
+            ctx.sj_selfjoin(np.zeros((4, 9)), 1.0)
+        assert ei.value.status == sj.SJ_EINVAL
+        # the context stays usable after errors
+        assert ctx.sj_selfjoin(pts, 1.0).shape[0] == 100
+
+
+def test_unicomp_halves_evaluations():
+    pts = datagen.uniform(50000, 3, seed=15)
+    eps = datagen.eps_for_neighbors(50000, 3, 32, side=100.0)
+    with sj.Context(unicomp=True) as a, sj.Context(unicomp=False) as b:
+        a.sj_selfjoin_count(pts, eps)
+        b.sj_selfjoin_count(pts, eps)
+        ea, eb = a.sj_last_stats()["evaluations"], b.sj_last_stats()["evaluations"]
+    # Without UNICOMP every ordered pair of adjacent cells (a cell with itself
+    # included) costs |C_a||C_b|; with it every unordered pair of distinct
+    # adjacent cells is compared once and a home cell costs |C|(|C|-1)/2.
+    # Summed over cells this is exactly (full - n) / 2.
+    n = 50000
+    assert 2 * ea == eb - n
+
+
+# ------------------------------------------------------------------ full size
+
+@pytest.mark.slow
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 6])
+def test_config2_full_size_sampled(d):
+    torch = pytest.importorskip("torch")
+    cfg = datagen.config2(d)
+    pts = datagen.make_points(cfg)
+    n, eps = cfg["n"], cfg["eps"]
+    with sj.Context() as ctx:
+        d_pts = torch.from_numpy(pts).cuda()
+        cnt = ctx.sj_selfjoin_count(d_pts, eps)
+        out = torch.empty((cnt, 2), dtype=torch.int32, device="cuda")
+        assert ctx.sj_selfjoin_device(d_pts, eps, out) == cnt
+    i = out[:, 0].to(torch.int64) & 0xffffffff
+    j = out[:, 1].to(torch.int64) & 0xffffffff
+    # self pairs, symmetry, no duplicates
+    assert int((i == j).sum()) == n
+    k1 = torch.sort((i << 32) | j).values
+    k2 = torch.sort((j << 32) | i).values
+    assert torch.equal(k1, k2)
+    assert int((k1[1:] == k1[:-1]).sum()) == 0
+    # sampled queries against the oracle, neighbour list by neighbour list
+    rng = np.random.default_rng(d)
+    q = np.sort(rng.choice(n, size=300, replace=False)).astype(np.uint32)
+    offs, ids = orc.grid_neighbors(pts, eps, q)
+    keys = k1.cpu().numpy().view(np.uint64)
+    for t, qq in enumerate(q):
+        lo = np.searchsorted(keys, np.uint64(int(qq) << 32))
+        hi = np.searchsorted(keys, np.uint64((int(qq) + 1) << 32))
+        got = (keys[lo:hi] & np.uint64(0xffffffff)).astype(np.uint32)
+        assert np.array_equal(got, ids[offs[t]:offs[t + 1]]), (d, int(qq))
+    # degree sum statistics: realised mean within 10% of 64 (boundary effects)
+    mean = (cnt - n) / n
+    assert 0.7 * 64 < mean < 1.02 * 64
