@@ -172,6 +172,19 @@ SJ_API sj_status sj_index_info(const sj_index *idx, sj_index_desc *out);
 SJ_API sj_status sj_index_export(const sj_index *idx, uint64_t *B, uint32_t *G,
                           uint32_t *A, uint32_t *M);
 
+/* The classification margin of SJ_PREC_FP32_RECHECK for a grid with
+ * dimension d, distance eps and padded bounds g_min_j, g_max_j
+ * (Section IV-B: g_min_j = min_j - eps, g_max_j = max_j + eps).  The join
+ * kernel computes an FP32 squared distance s32 from coordinates relative to
+ * the centre of the query's cell (see the derivation in csrc/margin.cu);
+ * s32 <= *lo implies membership by the exact FP64 test, s32 > *hi implies
+ * non-membership, and only values in between are recomputed in FP64.
+ * *w32 receives the cell side rounded to FP32.  Host-only, no device needed.
+ * Returns SJ_ERANGE when no useful margin exists (the FP32 mode then
+ * computes every distance in FP64), SJ_EINVAL for bad arguments. */
+SJ_API sj_status sj_fp32_margin(int d, double eps, const double *gmin, const double *gmax,
+                                float *w32, float *lo, float *hi);
+
 /* ------------------------------------------------------------------ */
 /* Self-join.                                                         */
 /* ------------------------------------------------------------------ */

@@ -249,67 +249,6 @@ __global__ void __launch_bounds__(kThreads) item_fill_kernel(const uint32_t *__r
 
 inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-// FP32 filter thresholds.  Notation: u = 2^-24, v = 2^-53, a_j = x_j - g_min_j
-// with 0 <= a_j <= A_j, the stored coordinate y_j = fl32(fl64(a_j)) and
-// Delta = x_p - x_q.
-//  * |y_j - a_j| <= A_j (u + v + uv) + 2^-150 =: rho_j, so the FP32 difference
-//    vector delta = y_p - y_q satisfies ||delta - Delta|| <= H = ||2 rho||.
-//  * the FP32 sum s32 of d squares of t_j = fl32(delta_j) (product and sum
-//    rounded, fused or not) obeys
-//    (1-u)^2 (1-g32) ||delta||^2 - a32 <= s32 <= (1+u)^2 (1+g32) ||delta||^2 + a32
-//    with g32 = (d+1)u / (1-(d+1)u) and a32 = 2d 2^-149 (subnormal results).
-//  * the FP64 predicate value obeys |s64 - ||Delta||^2| <= g64 ||Delta||^2 + a64,
-//    g64 = (d+3)v / (1-(d+3)v), a64 = 2d 2^-1074.
-// "member" certain:  s32 <= lo  =>  ||delta|| <= r_lo  =>  ||Delta|| <= r_lo + H
-//    =>  s64 <= (1+g64)(r_lo+H)^2 + a64 <= E2, solved for lo.
-// "not a member" certain: s64 <= E2 => ||Delta|| <= R2 => s32 <= hi, so
-//    s32 > hi => s64 > E2.
-void fp32_margin(Geometry &g) {
-    const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
-    const int d = g.d;
-    double H2 = 0.0, Amax = 0.0;
-    for (int j = 0; j < d; ++j) {
-        double A = (g.gmax[j] - g.gmin[j]) * (1.0 + 4.0 * v);
-        Amax = A > Amax ? A : Amax;
-        double rho = A * (u + v + u * v) + std::ldexp(1.0, -150);
-        H2 += 4.0 * rho * rho;
-    }
-    double H = std::sqrt(H2) * (1.0 + 4.0 * v);
-    const double g32 = (d + 1) * u / (1.0 - (d + 1) * u);
-    const double a32 = 2.0 * d * std::ldexp(1.0, -149);
-    const double g64 = (d + 3) * v / (1.0 - (d + 3) * v);
-    const double a64 = 2.0 * d * std::ldexp(1.0, -1074);
-    const double safety = std::ldexp(1.0, -20);  // covers rounding of this computation
-    g.fp32_ok = 0;
-    g.lo32 = -1.0f;
-    g.hi32 = 0.0f;
-    if (!std::isfinite(g.E2) || !(Amax < std::ldexp(1.0, 100)) || g.E2 < std::ldexp(1.0, -100))
-        return;
-    // hi: largest s32 a member can produce
-    double R2 = std::sqrt((g.E2 + a64) / (1.0 - g64)) * (1.0 + 4.0 * v);
-    double hi = (1.0 + u) * (1.0 + u) * (1.0 + g32) * (R2 + H) * (R2 + H) + a32;
-    hi *= (1.0 + safety);
-    if (!(hi < std::ldexp(1.0, 100))) return;
-    float hi32 = (float)hi;
-    if ((double)hi32 < hi) hi32 = std::nextafter(hi32, INFINITY);
-    // lo: largest s32 that still guarantees membership
-    double R1 = std::sqrt((g.E2 - a64) / (1.0 + g64)) * (1.0 - 4.0 * v) - H;
-    float lo32 = -1.0f;
-    if (R1 > 0.0) {
-        double lo = (1.0 - u) * (1.0 - u) * (1.0 - g32) * R1 * R1 - a32;
-        lo *= (1.0 - safety);
-        if (lo > 0.0) {
-            lo32 = (float)lo;
-            if ((double)lo32 > lo) lo32 = std::nextafter(lo32, -INFINITY);
-        }
-    }
-    // a band wider than half of E2 makes the filter pointless
-    if ((double)hi32 - (double)(lo32 > 0 ? lo32 : 0.0f) > 0.5 * g.E2) return;
-    g.lo32 = lo32;
-    g.hi32 = hi32;
-    g.fp32_ok = 1;
-}
-
 }  // namespace
 
 void free_index(Index &ix, cudaStream_t s) {
@@ -381,7 +320,7 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
         stride *= (uint64_t)g.ng[j];
     }
     g.grid_cells = stride;
-    fp32_margin(g);
+    fp32_margin(g);  // margin.cu
 
     // 2-3. cell ids and the sort by cell
     uint64_t dense_limit = (uint64_t)16 * n;

@@ -1,8 +1,8 @@
 // join.cu -- persistent search-and-refine kernel (Section IV-D, IV-E, V-B).
 //
 // Work decomposition.  A work item is (non-empty cell h, block of up to 32
-// of its points); items are taken from a global cursor by whole warps, so
-// heavy cells are spread over many warps.  For its item a warp:
+// of its points).  Items are taken from a global cursor by whole warps, so
+// heavy cells are spread over many warps.  Per item a warp
 //   1. builds the candidate ranges: the adjacent cells the query cell must
 //      search (Section IV-D), chosen by UNICOMP (Section V-B) or all 3^n of
 //      them (Algorithm 1).  Cells adjacent along dimension 1 have consecutive
@@ -11,24 +11,34 @@
 //      skipped when M_j marks one of its fixed coordinates as empty, and is
 //      looked up with two loads of the dense table or two binary searches of
 //      B.  The home cell is range 0.
-//   2. streams the candidates through shared memory in chunks of 64: every
-//      range piece of a chunk is one cp.async.bulk copy (16-byte aligned
-//      records) completing on a per-warp mbarrier, double buffered so the
-//      next chunk is in flight while the current one is compared.
-//   3. compares: lanes own candidates (two each), the item's query points
-//      are broadcast from shared memory.  FP32 mode computes the squared
-//      distance with packed f32x2 arithmetic and classifies it against the
-//      proven margin [lo32, hi32]; only values inside it are recomputed with
-//      the exact FP64 predicate.  FP64 mode evaluates the predicate directly.
-//   4. emits: under UNICOMP each hit (p, q) gives (p, q) and (q, p); in the
+//   2. stages its query points in shared memory, already transformed for the
+//      distance evaluation (see below).
+//   3. streams the candidates through a ring of NBUF shared-memory chunk
+//      buffers: each range piece of a chunk is one cp.async.bulk copy of
+//      16-byte aligned records, completing on the slot's mbarrier.  The
+//      producer side of the warp runs up to NBUF chunks ahead of the
+//      consumer side and crosses into the next work item (two item slots),
+//      so copy latency is hidden also when items are small.
+//   4. compares: lanes own CPL candidates each, the queries are broadcast
+//      from shared memory.
+//        FP32 mode: coordinates relative to the home cell's centre,
+//        z = fl32(y - o), and s = |z_p|^2 + |z_q|^2 - 2 z_p . z_q evaluated
+//        as one add and d fused multiply-adds on packed f32x2 pairs (two
+//        candidates per instruction).  s is classified against the proven
+//        margin [lo32, hi32] computed on the host (index.cu); only values
+//        inside the margin are recomputed with the exact FP64 predicate, in a
+//        warp-uniform branch around a non-inlined function so that the slow
+//        FP64 pipe of GB300 sees only the real rechecks.
+//        FP64 mode: the exact predicate for every candidate.
+//   5. emits: under UNICOMP each hit (p, q) gives (p, q) and (q, p); in the
 //      home cell only q >= p is compared and the self-pair is emitted once.
-//      Pairs are staged per warp in shared memory (ballot-free warp scan for
-//      the offsets) and written out in coalesced blocks after one atomic
-//      reservation per flush.
+//      Pairs are staged per warp in shared memory (ballot + popc offsets) and
+//      written out in coalesced blocks after one atomic reservation per flush.
 // Waits on mbarriers are bounded by a time limit; on expiry the warp records
 // an error bit, waits (bounded) for its copies in flight and leaves.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <type_traits>
 
 #include "sj_internal.cuh"
@@ -37,9 +47,12 @@ namespace sj {
 
 namespace {
 
-constexpr int kCPL = 2;                    // candidates per lane
-constexpr int kChunk = 32 * kCPL;          // candidates per chunk
 constexpr int kEmit = 512;                 // staged pairs per warp
+
+// Candidates per lane by dimension and precision (chunk = 32 * CPL).
+__host__ __device__ constexpr int cpl_for(int d, bool f32) { return f32 ? (d <= 3 ? 2 : 4) : 2; }
+// Depth of the chunk ring (smaller chunks need more of them in flight).
+__host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >= 4) ? 3 : 4; }
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -83,7 +96,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 63 && global_ns() - t0 > limit_ns) return false;
+        if ((it & 15) == 15 && global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -110,14 +123,9 @@ __device__ __forceinline__ f2_t f2_pack(float a, float b) {
 __device__ __forceinline__ void f2_unpack(f2_t r, float &a, float &b) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
 }
-__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
     f2_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
-    f2_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
@@ -127,7 +135,18 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
 }
 
 // The exact predicate of Section III in FP64: every operation rounded to
-// nearest on its own, no contraction.
+// nearest on its own, no contraction.  Kept out of line so that the FP64
+// instructions run only for the pairs that need them.
+__device__ __noinline__ bool exact_member_ni(const double *__restrict__ a,
+                                             const double *__restrict__ b, int d, double E2) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = __dsub_rn(a[j], b[j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s <= E2;
+}
+
 template <int D>
 __device__ __forceinline__ bool exact_member(const double *__restrict__ a,
                                              const double *__restrict__ b, double E2) {
@@ -144,8 +163,8 @@ __device__ __forceinline__ bool exact_member(const double *__restrict__ a,
 __constant__ uint32_t c_pow3[kMaxDim + 1] = {1, 3, 9, 27, 81, 243, 729, 2187, 6561};
 
 // Row template t of the search, for a query cell with coordinates c:
-// outputs the x range [xlo, xhi] and the offsets of dimensions 1..D-1, or
-// false when the template is inactive or leaves the grid.
+// outputs the x range [xlo, xhi] and the coordinates b of dimensions
+// 1..D-1, or false when the template is inactive or leaves the grid.
 //   UNICOMP: t = 0 home cell; t = 1, 2 stage 0 (x - 1, x + 1); then, for
 //   stage k = 1..D-1, 2 * 3^(k-1) rows with dimension k at c_k -+ 1,
 //   dimensions 1..k-1 anywhere in c -+ 1, dimensions above k equal to c.
@@ -165,22 +184,23 @@ __device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, co
             if (!(odd & 1u)) return false;
             xlo = xhi = (t == 1) ? c[0] - 1 : c[0] + 1;
         } else {
-            uint32_t u = (uint32_t)t - 3;
+            const uint32_t u = (uint32_t)t - 3;
             int k = 1;
 #pragma unroll
             for (int kk = 1; kk < D; ++kk)
                 if (u >= c_pow3[kk] - 1) k = kk + 1;
             if (k >= D) return false;
             if (!((odd >> k) & 1u)) return false;
-            uint32_t v = u - (c_pow3[k - 1] - 1);
-            uint32_t p = c_pow3[k - 1];
-            b[k] = c[k] + ((v / p) ? 1 : -1);
+            const uint32_t p = c_pow3[k - 1];
+            const uint32_t v = u - (p - 1);
             uint32_t rem = v % p;
 #pragma unroll
             for (int j = 1; j < D; ++j) {
                 if (j < k) {
                     b[j] = c[j] + (int32_t)(rem % 3) - 1;
                     rem /= 3;
+                } else if (j == k) {
+                    b[j] = c[j] + ((v / p) ? 1 : -1);
                 }
             }
         }
@@ -198,7 +218,7 @@ __device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, co
 #pragma unroll
     for (int j = 1; j < D; ++j) {
         if (b[j] < 0 || b[j] >= a.ng[j]) return false;
-        uint32_t w = a.M[(uint64_t)j * a.mwords + ((uint32_t)b[j] >> 5)];
+        const uint32_t w = a.M[(uint64_t)j * a.mwords + ((uint32_t)b[j] >> 5)];
         if (!((w >> (b[j] & 31)) & 1u)) return false;   // M_j: no point in that slab
     }
     return true;
@@ -209,138 +229,524 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *__restrict__
                                                     uint64_t key) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
+        const uint32_t mid = (lo + hi) >> 1;
         if (__ldg(&B[mid]) < key) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
-// Per-warp shared-memory carve-up.
-struct WarpSmem {
-    uint2 *ranges;        // (begin in cell order, flat end)
-    unsigned char *q;     // query records
-    unsigned char *buf[2];
-    uint2 *emit;
-    uint64_t *bar;        // two mbarriers
+// Per-item header kept in shared memory (one per item slot).
+struct ItemHdr {
+    uint32_t h, qb, nq, home_len, K, nchunks, nranges, pad;
+    float o[kMaxDim];
 };
 
-__device__ __forceinline__ WarpSmem carve(unsigned char *base, const JoinArgs &a, int warp) {
+// Per-warp shared-memory carve-up.
+struct WarpSmem {
+    uint64_t *bar;            // one mbarrier per ring slot
+    ItemHdr *hdr;             // [2]
+    uint2 *ranges[2];         // (begin in cell order, flat end)
+    unsigned char *q[2];      // query records
+    unsigned char *ring;      // chunk buffers
+    uint2 *emit;
+};
+
+__device__ __forceinline__ WarpSmem carve(unsigned char *base, const JoinArgs &a, int warp,
+                                          int nbuf) {
     WarpSmem w;
     unsigned char *p = base + (size_t)warp * a.sm_warp;
     w.bar = reinterpret_cast<uint64_t *>(p);
-    p += 16;
-    w.ranges = reinterpret_cast<uint2 *>(p);
+    p += 64;
+    w.hdr = reinterpret_cast<ItemHdr *>(p);
+    p += 2 * sizeof(ItemHdr);
+    w.ranges[0] = reinterpret_cast<uint2 *>(p);
     p += a.sm_ranges;
-    w.q = p;
+    w.ranges[1] = reinterpret_cast<uint2 *>(p);
+    p += a.sm_ranges;
+    w.q[0] = p;
     p += a.sm_queries;
-    w.buf[0] = p;
-    p += a.sm_chunk;
-    w.buf[1] = p;
-    p += a.sm_chunk;
+    w.q[1] = p;
+    p += a.sm_queries;
+    w.ring = p;
+    p += (size_t)nbuf * a.sm_chunk;
     w.emit = reinterpret_cast<uint2 *>(p);
     return w;
 }
 
-struct Emitter {
-    uint32_t fill = 0;
+// Warp-uniform state of the producer / consumer pipeline.
+struct Pipe {
+    uint32_t grab_pos, grab_end;   // work-cursor positions taken by this warp
+    uint32_t issued, consumed;     // chunks
+    uint32_t prod_seq, cons_seq;   // item sequence numbers (slot = seq & 1)
+    uint32_t p_chunk, c_chunk;
+    uint32_t rcur;                 // producer's range cursor
+    uint32_t fill;                 // staged pairs
+    bool prod_done;
 };
 
-__device__ __forceinline__ void flush(Emitter &em, const WarpSmem &ws, const JoinArgs &a,
-                                      int lane) {
+__device__ __forceinline__ void flush(Pipe &st, const WarpSmem &ws, const JoinArgs &a, int lane) {
     __syncwarp();
-    if (em.fill == 0) return;
+    if (st.fill == 0) return;
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)em.fill);
+    if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)st.fill);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (!a.count_only) {
-        for (uint32_t i = lane; i < em.fill; i += 32) {
-            uint64_t pos = base + i;
+        for (uint32_t i = lane; i < st.fill; i += 32) {
+            const uint64_t pos = base + i;
             if (pos < a.cap) a.out[pos] = ws.emit[i];
         }
     }
     __syncwarp();
-    em.fill = 0;
+    st.fill = 0;
 }
 
-// Stages the pairs of this lane's candidates for one query.
-// n[c] = number of pairs (0, 1 or 2) for candidate slot c.
-__device__ __forceinline__ void emit_pairs(Emitter &em, const WarpSmem &ws, const JoinArgs &a,
-                                           int lane, uint32_t qid, const uint32_t *cid,
-                                           const uint32_t *n) {
-    uint32_t mine = 0;
-#pragma unroll
-    for (int c = 0; c < kCPL; ++c) mine += n[c];
-    uint32_t incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
+// Stages the pairs of candidate slot s of every lane for one query:
+// npairs in {0, 1, 2}.  Offsets come from two ballots.
+__device__ __forceinline__ void emit_slot(Pipe &st, const WarpSmem &ws, const JoinArgs &a, int lane,
+                                          uint32_t qid, uint32_t cid, uint32_t npairs) {
+    const unsigned m1 = __ballot_sync(0xffffffffu, npairs >= 1);
+    if (m1 == 0) return;
+    const unsigned m2 = __ballot_sync(0xffffffffu, npairs == 2);
+    const unsigned lt = (1u << lane) - 1u;
+    if (npairs && !a.count_only) {
+        uint32_t pos = st.fill + __popc(m1 & lt) + __popc(m2 & lt);
+        ws.emit[pos] = make_uint2(qid, cid);
+        if (npairs == 2) ws.emit[pos + 1] = make_uint2(cid, qid);
     }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    if (em.fill + total > (uint32_t)a.eb) flush(em, ws, a, lane);
-    if (!a.count_only) {
-        uint32_t pos = em.fill + incl - mine;
+    st.fill += __popc(m1) + __popc(m2);
+}
+
+// Loads this lane's CPL candidates of a chunk (slot s = position lane + 32 s)
+// from shared memory with 16-byte loads, moves them into the frame of the
+// home cell centre o and packs them in pairs.  Slots past the chunk end get
+// z = 0, |z|^2 = +inf (never a member) and id 0xffffffff.
+template <int D, int CPL>
+__device__ __forceinline__ void load_candidates(const unsigned char *buf, int rs, uint32_t clen,
+                                                int lane, const float *o_smem, f2_t (*z)[D],
+                                                f2_t *qq2, uint32_t *cid) {
+    constexpr int V = (D + 1 + 3) / 4;    // float4 per record (rs = 4 V)
+    float o[D];
 #pragma unroll
-        for (int c = 0; c < kCPL; ++c) {
-            if (n[c] >= 1) ws.emit[pos++] = make_uint2(qid, cid[c]);
-            if (n[c] == 2) ws.emit[pos++] = make_uint2(cid[c], qid);
+    for (int j = 0; j < D; ++j) o[j] = o_smem[j];
+#pragma unroll
+    for (int cp = 0; cp < CPL / 2; ++cp) {
+        float za[2][D], qs[2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int s = 2 * cp + h2;
+            const uint32_t slot = lane + 32 * s;
+            qs[h2] = INFINITY;
+#pragma unroll
+            for (int j = 0; j < D; ++j) za[h2][j] = 0.0f;
+            cid[s] = 0xffffffffu;
+            if (slot < clen) {
+                const float4 *rr = reinterpret_cast<const float4 *>(buf + (size_t)slot * rs * 4);
+                float r[4 * V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const float4 v = rr[k];
+                    r[4 * k] = v.x;
+                    r[4 * k + 1] = v.y;
+                    r[4 * k + 2] = v.z;
+                    r[4 * k + 3] = v.w;
+                }
+                float q2 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const float zz = __fsub_rn(r[j], o[j]);
+                    za[h2][j] = zz;
+                    q2 = __fmaf_rn(zz, zz, q2);
+                }
+                qs[h2] = q2;
+                cid[s] = __float_as_uint(r[D]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) z[cp][j] = f2_pack(za[0][j], za[1][j]);
+        qq2[cp] = f2_pack(qs[0], qs[1]);
+    }
+}
+
+// s32 for one staged query record against this lane's candidates:
+// fl(|z_q|^2 + |z_p|^2) then d fused multiply-adds with m_j = -2 z_p,j.
+template <int D, int NP>
+__device__ __forceinline__ void eval_query(const float *qd, const f2_t (*z)[D], const f2_t *qq2,
+                                           float *sv) {
+    const ulonglong2 *q2 = reinterpret_cast<const ulonglong2 *>(qd);
+    f2_t m[D + 1];
+#pragma unroll
+    for (int k = 0; k < (D + 2) / 2; ++k) {
+        const ulonglong2 v = q2[k];
+        m[2 * k] = v.x;
+        if (2 * k + 1 <= D) m[2 * k + 1] = v.y;
+    }
+    f2_t acc[NP];
+#pragma unroll
+    for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_add(qq2[cp], m[D]);
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_fma(m[j], z[cp][j], acc[cp]);
+#pragma unroll
+    for (int cp = 0; cp < NP; ++cp) f2_unpack(acc[cp], sv[2 * cp], sv[2 * cp + 1]);
+}
+
+// Decides the candidates of one query per lane (hb: values <= hi32) and
+// stages their pairs.  Values above lo32 are recomputed with the exact FP64
+// predicate; in the home cell only candidates at or after the query's own
+// position count, and the self-pair is emitted once.  Every lane may hold a
+// different query (qd, ql).  The caller guarantees room for 2 * 32 * CPL
+// pairs in the staging buffer.
+template <int D, int CPL, bool UNI>
+__device__ __forceinline__ void refine_emit(Pipe &st, const WarpSmem &ws, const JoinArgs &a,
+                                            int lane, const float *qd, const float *sv, uint32_t hb,
+                                            const uint32_t *cid, bool home_chunk, uint32_t kb,
+                                            uint32_t home_len, uint32_t ql,
+                                            unsigned long long &rechecks) {
+    uint32_t selfb = 0, needb = 0;
+#pragma unroll
+    for (int s = 0; s < CPL; ++s) {
+        if (home_chunk) {
+            const uint32_t k = kb + lane + 32 * s;
+            if (k < home_len) {
+                if (k < ql) hb &= ~(1u << s);
+                if (k == ql) selfb |= 1u << s;
+            }
+        }
+        if (((hb >> s) & 1u) && !((selfb >> s) & 1u) && sv[s] > a.lo32) needb |= 1u << s;
+    }
+    const uint32_t qid = __float_as_uint(qd[2 * D + 2]);
+    if (__any_sync(0xffffffffu, needb)) {
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            if ((needb >> s) & 1u) {
+                ++rechecks;
+                if (!exact_member_ni(a.pts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
+                    hb &= ~(1u << s);
+            }
         }
     }
-    em.fill += total;
+    selfb &= hb;
+    const uint32_t n = UNI ? 2u * __popc(hb) - __popc(selfb) : (uint32_t)__popc(hb);
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (n && !a.count_only) {
+        uint32_t pos = st.fill + incl - n;
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            if ((hb >> s) & 1u) {
+                ws.emit[pos++] = make_uint2(qid, cid[s]);
+                if (UNI && !((selfb >> s) & 1u)) ws.emit[pos++] = make_uint2(cid[s], qid);
+            }
+        }
+    }
+    st.fill += total;
 }
 
-// Issues the bulk copies that bring flat candidates [k0, k1) of the item
-// into a chunk buffer.  `rcur` is the first range that may overlap k0.
-__device__ __forceinline__ void issue_chunk(const WarpSmem &ws, int buf, uint32_t k0, uint32_t k1,
-                                            uint32_t nranges, uint32_t &rcur,
-                                            const unsigned char *__restrict__ rec, uint32_t rsb,
-                                            int lane) {
-    while (rcur < nranges && ws.ranges[rcur].y <= k0) ++rcur;
+// Takes the next work item for this warp; false when none is left.
+__device__ __forceinline__ bool fetch_item(Pipe &st, const JoinArgs &a, uint32_t item_end,
+                                           int lane, uint2 &it) {
+    if (st.grab_pos == st.grab_end) {
+        uint32_t first = 0;
+        if (lane == 0) first = atomicAdd(a.work, (uint32_t)a.grab);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        st.grab_pos = first;
+        st.grab_end = first + a.grab;
+    }
+    const uint64_t item = (uint64_t)a.item_begin + (uint64_t)st.grab_pos * a.item_stride;
+    if (item >= item_end) return false;
+    ++st.grab_pos;
+    it = a.items[item];
+    return true;
+}
+
+// Builds ranges, header and staged queries of item `it` in item slot `sl`.
+template <int D, bool F32, bool UNI>
+__device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 it,
+                                             const JoinArgs &a, uint32_t n_cells, int lane,
+                                             unsigned long long &evals) {
+    typedef typename std::conditional<F32, float, double>::type T;
+    const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
+    const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
+                                   : reinterpret_cast<const unsigned char *>(a.rec64);
+    const uint32_t h = it.x;
+    const uint32_t cbeg = __ldg(&a.G[h]), cend = __ldg(&a.G[h + 1]);
+    const uint32_t home_len = cend - cbeg;
+    const uint32_t q0 = cbeg + it.y * kQueryBlock;
+    const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
+
+    int32_t c[D];
+    uint32_t odd = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        c[j] = __ldg(&a.cc[(uint64_t)h * D + j]);
+        odd |= ((uint32_t)c[j] & 1u) << j;
+    }
+
+    // candidate ranges
+    uint2 *rt = ws.ranges[sl];
+    uint32_t nranges = 0, K = 0;
+    for (int t0 = 0; t0 < a.n_templates; t0 += 32) {
+        const int t = t0 + lane;
+        uint32_t beg = 0, len = 0;
+        int32_t xlo, xhi, b[D];
+        if (t < a.n_templates && row_of<D, UNI>(t, c, odd, a, xlo, xhi, b)) {
+            uint64_t base = 0;
+#pragma unroll
+            for (int j = 1; j < D; ++j) base += (uint64_t)b[j] * a.stride[j];
+            const uint64_t id_lo = base + (uint64_t)xlo, id_hi = base + (uint64_t)xhi;
+            uint32_t e;
+            if (a.dense) {
+                beg = __ldg(&a.lut[id_lo]);
+                e = __ldg(&a.lut[id_hi + 1]);
+            } else {
+                const uint32_t hl = lower_bound_u64(a.B, n_cells, id_lo);
+                const uint32_t hh = lower_bound_u64(a.B, n_cells, id_hi + 1);
+                beg = __ldg(&a.G[hl]);
+                e = __ldg(&a.G[hh]);
+            }
+            len = e - beg;
+        }
+        const unsigned nz = __ballot_sync(0xffffffffu, len > 0);
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (len > 0) rt[nranges + __popc(nz & ((1u << lane) - 1u))] = make_uint2(beg, K + incl);
+        nranges += __popc(nz);
+        K += __shfl_sync(0xffffffffu, incl, 31);
+    }
+
+    // staged queries
+    ItemHdr *hd = &ws.hdr[sl];
+    if (F32) {
+        float o[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) o[j] = ((float)c[j] + 0.5f) * a.w32;
+        if (lane < (int)nq) {
+            const float *r = reinterpret_cast<const float *>(rec + (size_t)(q0 + lane) * rsb);
+            float *qd = reinterpret_cast<float *>(ws.q[sl]) + (size_t)lane * a.qrs;
+            float pp = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const float z = __fsub_rn(r[j], o[j]);
+                pp = __fmaf_rn(z, z, pp);
+                const float m = -2.0f * z;
+                qd[2 * j] = m;
+                qd[2 * j + 1] = m;
+            }
+            qd[2 * D] = pp;
+            qd[2 * D + 1] = pp;
+            qd[2 * D + 2] = r[D];   // point id bits
+        }
+        if (lane < D) hd->o[lane] = o[lane];
+    } else {
+        if (lane < (int)nq) {
+            const double *r = reinterpret_cast<const double *>(rec + (size_t)(q0 + lane) * rsb);
+            double *qd = reinterpret_cast<double *>(ws.q[sl]) + (size_t)lane * a.qrs;
+#pragma unroll
+            for (int j = 0; j <= D; ++j) qd[j] = r[j];
+        }
+    }
+    if (lane == 0) {
+        hd->h = h;
+        hd->qb = it.y;
+        hd->nq = nq;
+        hd->home_len = home_len;
+        hd->K = K;
+        hd->nchunks = (K + 32 * cpl_for(D, F32) - 1) / (32 * cpl_for(D, F32));
+        hd->nranges = nranges;
+        // algorithmic evaluations of this item
+        if (UNI) {
+            const uint64_t ql0 = (uint64_t)it.y * kQueryBlock;
+            evals += (uint64_t)nq * (K - home_len) + (uint64_t)nq * (home_len - 1) -
+                     (uint64_t)nq * ql0 - (uint64_t)nq * (nq - 1) / 2;
+        } else {
+            evals += (uint64_t)nq * K;
+        }
+    }
+    __syncwarp();
+}
+
+// Issues the bulk copies of chunk `ch` of the item in slot `sl` into ring
+// slot `r`.
+template <int CB>
+__device__ __forceinline__ void issue_chunk(const WarpSmem &ws, int sl, uint32_t ch, int r,
+                                            uint32_t &rcur, const unsigned char *__restrict__ rec,
+                                            uint32_t rsb, int lane, int sm_chunk) {
+    const ItemHdr *hd = &ws.hdr[sl];
+    const uint32_t K = hd->K, nranges = hd->nranges;
+    const uint2 *rt = ws.ranges[sl];
+    const uint32_t k0 = ch * CB;
+    const uint32_t k1 = min(K, k0 + CB);
+    unsigned char *buf = ws.ring + (size_t)r * sm_chunk;
+    while (rcur < nranges && rt[rcur].y <= k0) ++rcur;
     // earlier generic-proxy reads of this buffer precede the async-proxy writes
     fence_proxy_async_smem();
-    if (lane == 0) mbar_arrive_expect_tx(&ws.bar[buf], (k1 - k0) * rsb);
+    if (lane == 0) mbar_arrive_expect_tx(&ws.bar[r], (k1 - k0) * rsb);
     __syncwarp();
     for (uint32_t r0 = rcur; r0 < nranges; r0 += 32) {
-        const uint32_t r = r0 + lane;
+        const uint32_t rr = r0 + lane;
         bool starts_before = false;
-        if (r < nranges) {
-            const uint2 rg = ws.ranges[r];
-            const uint32_t fs = (r == 0) ? 0u : ws.ranges[r - 1].y;
+        if (rr < nranges) {
+            const uint2 rg = rt[rr];
+            const uint32_t fs = (rr == 0) ? 0u : rt[rr - 1].y;
             const uint32_t fe = rg.y;
             starts_before = fs < k1;
             if (starts_before && fe > k0) {
                 const uint32_t lo = fs > k0 ? fs : k0;
                 const uint32_t hi = fe < k1 ? fe : k1;
-                bulk_g2s(ws.buf[buf] + (size_t)(lo - k0) * rsb,
-                         rec + (size_t)(rg.x + (lo - fs)) * rsb, (hi - lo) * rsb, &ws.bar[buf]);
+                bulk_g2s(buf + (size_t)(lo - k0) * rsb, rec + (size_t)(rg.x + (lo - fs)) * rsb,
+                         (hi - lo) * rsb, &ws.bar[r]);
             }
         }
         if (__ballot_sync(0xffffffffu, starts_before) != 0xffffffffu) break;
     }
 }
 
+// Compares chunk `ch` (in ring slot r) of the item in slot `sl` with the
+// item's queries and stages the pairs found.
+template <int D, bool F32, bool UNI>
+__device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int sl, uint32_t ch,
+                                              int r, const JoinArgs &a, int lane,
+                                              unsigned long long &rechecks) {
+    constexpr int CPL = cpl_for(D, F32);
+    constexpr int CB = 32 * CPL;
+    const ItemHdr *hd = &ws.hdr[sl];
+    const uint32_t K = hd->K, nq = hd->nq, home_len = hd->home_len;
+    const uint32_t kb = ch * CB;
+    const uint32_t clen = min((uint32_t)CB, K - kb);
+    const bool home_chunk = UNI && kb < home_len;
+    const uint32_t ql_base = hd->qb * kQueryBlock;
+    const unsigned char *buf = ws.ring + (size_t)r * a.sm_chunk;
+
+    if (F32) {
+        constexpr int NP = CPL / 2;
+        const float hi32 = a.hi32;
+        f2_t z[NP][D], qq2[NP];
+        uint32_t cid[CPL];
+        load_candidates<D, CPL>(buf, a.rs, clen, lane, hd->o, z, qq2, cid);
+        const float *qbase = reinterpret_cast<const float *>(ws.q[sl]);
+        if (D <= 3) {
+            // frequent hits: decide and emit per query
+            for (uint32_t qi = 0; qi < nq; ++qi) {
+                const float *qd = qbase + (size_t)qi * a.qrs;
+                float sv[CPL];
+                eval_query<D, NP>(qd, z, qq2, sv);
+                uint32_t hb = 0;
+#pragma unroll
+                for (int s = 0; s < CPL; ++s) hb |= (sv[s] <= hi32 ? 1u : 0u) << s;
+                if (!__any_sync(0xffffffffu, hb)) continue;
+                if (st.fill + 2 * 32 * CPL > (uint32_t)a.eb) flush(st, ws, a, lane);
+                refine_emit<D, CPL, UNI>(st, ws, a, lane, qd, sv, hb, cid, home_chunk, kb, home_len,
+                                         ql_base + qi, rechecks);
+            }
+        } else {
+            // rare hits: flag the queries whose value may be a member, one
+            // vote per chunk, then re-evaluate only the flagged queries
+            uint32_t flags = 0;
+            for (uint32_t qi = 0; qi < nq; ++qi) {
+                float sv[CPL];
+                eval_query<D, NP>(qbase + (size_t)qi * a.qrs, z, qq2, sv);
+                float mn = sv[0];
+#pragma unroll
+                for (int s = 1; s < CPL; ++s) mn = fminf(mn, sv[s]);
+                flags |= (mn <= hi32 ? 1u : 0u) << qi;
+            }
+            while (__any_sync(0xffffffffu, flags)) {
+                // one flagged query per lane per round: at most 2 * CPL pairs each
+                if (st.fill + 2 * 32 * CPL > (uint32_t)a.eb) flush(st, ws, a, lane);
+                uint32_t hb = 0, qi = 0;
+                float sv[CPL];
+                const float *qd = qbase;
+                if (flags) {
+                    qi = __ffs(flags) - 1;
+                    flags &= flags - 1;
+                    qd = qbase + (size_t)qi * a.qrs;
+                    eval_query<D, NP>(qd, z, qq2, sv);
+#pragma unroll
+                    for (int s = 0; s < CPL; ++s) hb |= (sv[s] <= hi32 ? 1u : 0u) << s;
+                }
+                refine_emit<D, CPL, UNI>(st, ws, a, lane, qd, sv, hb, cid, home_chunk, kb, home_len,
+                                         ql_base + qi, rechecks);
+            }
+        }
+    } else {
+        double y[CPL][D];
+        uint32_t cid[CPL];
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            const uint32_t slot = lane + 32 * s;
+            cid[s] = 0xffffffffu;
+#pragma unroll
+            for (int j = 0; j < D; ++j) y[s][j] = 0.0;
+            if (slot < clen) {
+                const double *rr = reinterpret_cast<const double *>(buf + (size_t)slot * a.rs * 8);
+#pragma unroll
+                for (int j = 0; j < D; ++j) y[s][j] = rr[j];
+                cid[s] = (uint32_t)__double_as_longlong(rr[D]);
+            }
+        }
+        const double *qbase = reinterpret_cast<const double *>(ws.q[sl]);
+        for (uint32_t qi = 0; qi < nq; ++qi) {
+            const double *qd = qbase + (size_t)qi * a.qrs;
+            bool hit[CPL];
+            bool any = false;
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                hit[s] = cid[s] != 0xffffffffu && exact_member<D>(qd, y[s], a.E2);
+                any |= hit[s];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const uint32_t qid = (uint32_t)__double_as_longlong(qd[D]);
+            const uint32_t ql = ql_base + qi;
+            if (st.fill + 2 * 32 * CPL > (uint32_t)a.eb) flush(st, ws, a, lane);
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                bool self = false;
+                if (home_chunk) {
+                    const uint32_t k = kb + lane + 32 * s;
+                    if (k < home_len) {
+                        if (k < ql) hit[s] = false;
+                        self = (k == ql);
+                    }
+                }
+                const uint32_t np = hit[s] ? ((UNI && !self) ? 2u : 1u) : 0u;
+                emit_slot(st, ws, a, lane, qid, cid[s], np);
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------- the kernel
 
 template <int D, bool F32, bool UNI>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) join_kernel(const JoinArgs a,
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1) join_kernel(const JoinArgs a,
                                                                      const uint32_t *counts) {
+    constexpr int CPL = cpl_for(D, F32);
+    constexpr int CB = 32 * CPL;
+    constexpr int kNBuf = nbuf_for(D, F32);
+    typedef typename std::conditional<F32, float, double>::type T;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const WarpSmem ws = carve(smem, a, warp);
-    typedef typename std::conditional<F32, float, double>::type T;
+    const WarpSmem ws = carve(smem, a, warp, kNBuf);
     const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
                                    : reinterpret_cast<const unsigned char *>(a.rec64);
 
-    if (lane == 0) {
-        mbar_init(&ws.bar[0], 1);
-        mbar_init(&ws.bar[1], 1);
-    }
+    if (lane == 0)
+        for (int i = 0; i < kNBuf; ++i) mbar_init(&ws.bar[i], 1);
     fence_proxy_async_smem();
     __syncwarp();
-    uint32_t phase = 0;  // bit b: parity of the next completion of buffer b
 
     // counts[0] = |G|, counts[1] = number of work items (device-side, so the
     // launch needs no read-back)
@@ -348,232 +754,65 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) join_kernel(const Join
     uint32_t item_end = a.item_end;
     if (counts[1] < item_end) item_end = counts[1];
 
-    Emitter em;
+    Pipe st;
+    st.grab_pos = st.grab_end = 0;
+    st.issued = st.consumed = 0;
+    st.prod_seq = st.cons_seq = 0;
+    st.p_chunk = st.c_chunk = 0;
+    st.rcur = 0;
+    st.fill = 0;
+    st.prod_done = false;
     unsigned long long evals = 0, rechecks = 0;
     bool failed = false;
 
-    for (;;) {
-        uint32_t first = 0;
-        if (lane == 0) first = atomicAdd(a.work, (uint32_t)a.grab);
-        first = __shfl_sync(0xffffffffu, first, 0);
-        // sampled launches take every item_stride-th item
-        const uint64_t f64 = (uint64_t)a.item_begin + (uint64_t)first * a.item_stride;
-        if (f64 >= item_end) break;
-        for (uint32_t g = 0; g < (uint32_t)a.grab && !failed; ++g) {
-            const uint64_t item64 = f64 + (uint64_t)g * a.item_stride;
-            if (item64 >= item_end) break;
-            const uint2 it = a.items[item64];
-            const uint32_t h = it.x;
-            const uint32_t cbeg = a.G[h], cend = a.G[h + 1];
-            const uint32_t home_len = cend - cbeg;
-            const uint32_t q0 = cbeg + it.y * kQueryBlock;
-            const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
-
-            // query records into shared memory
-            {
-                const uint32_t words = rsb / 16;
-                const uint4 *src = reinterpret_cast<const uint4 *>(rec + (size_t)q0 * rsb);
-                uint4 *dst = reinterpret_cast<uint4 *>(ws.q);
-                for (uint32_t i = lane; i < nq * words; i += 32) dst[i] = src[i];
-            }
-
-            // cell coordinates and UNICOMP parity mask
-            int32_t c[D];
-            uint32_t odd = 0;
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                c[j] = a.cc[(uint64_t)h * D + j];
-                odd |= ((uint32_t)c[j] & 1u) << j;
-            }
-
-            // 1. candidate ranges
-            uint32_t nranges = 0, K = 0;
-            for (int t0 = 0; t0 < a.n_templates; t0 += 32) {
-                const int t = t0 + lane;
-                uint32_t beg = 0, len = 0;
-                int32_t xlo, xhi, b[D];
-                if (t < a.n_templates && row_of<D, UNI>(t, c, odd, a, xlo, xhi, b)) {
-                    uint64_t base = 0;
-#pragma unroll
-                    for (int j = 1; j < D; ++j) base += (uint64_t)b[j] * a.stride[j];
-                    const uint64_t id_lo = base + (uint64_t)xlo, id_hi = base + (uint64_t)xhi;
-                    uint32_t e;
-                    if (a.dense) {
-                        beg = __ldg(&a.lut[id_lo]);
-                        e = __ldg(&a.lut[id_hi + 1]);
-                    } else {
-                        const uint32_t hl = lower_bound_u64(a.B, n_cells, id_lo);
-                        const uint32_t hh = lower_bound_u64(a.B, n_cells, id_hi + 1);
-                        beg = __ldg(&a.G[hl]);
-                        e = __ldg(&a.G[hh]);
+    uint2 it;
+    if (fetch_item(st, a, item_end, lane, it)) {
+        prepare_item<D, F32, UNI>(ws, 0, it, a, n_cells, lane, evals);
+        for (;;) {
+            // producer: keep up to kNBuf chunks in flight, crossing into the
+            // next item (at most one item ahead of the consumer)
+            while (st.issued - st.consumed < (uint32_t)kNBuf) {
+                const int ps = st.prod_seq & 1;
+                if (st.p_chunk == ws.hdr[ps].nchunks) {
+                    // the other item slot is free once the consumer has
+                    // reached the producer's item
+                    if (st.prod_done || st.prod_seq > st.cons_seq) break;
+                    if (!fetch_item(st, a, item_end, lane, it)) {
+                        st.prod_done = true;
+                        break;
                     }
-                    len = e - beg;
+                    ++st.prod_seq;
+                    prepare_item<D, F32, UNI>(ws, st.prod_seq & 1, it, a, n_cells, lane, evals);
+                    st.p_chunk = 0;
+                    st.rcur = 0;
+                    continue;
                 }
-                const unsigned nz = __ballot_sync(0xffffffffu, len > 0);
-                uint32_t incl = len;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                if (len > 0) {
-                    const uint32_t pos = nranges + __popc(nz & ((1u << lane) - 1u));
-                    ws.ranges[pos] = make_uint2(beg, K + incl);
-                }
-                nranges += __popc(nz);
-                K += __shfl_sync(0xffffffffu, incl, 31);
+                issue_chunk<CB>(ws, ps, st.p_chunk, st.issued % kNBuf, st.rcur, rec, rsb, lane,
+                                a.sm_chunk);
+                ++st.issued;
+                ++st.p_chunk;
             }
-            __syncwarp();
-
-            // algorithmic evaluations of this item
-            if (lane == 0) {
-                if (UNI) {
-                    const uint64_t ql0 = (uint64_t)it.y * kQueryBlock;
-                    evals += (uint64_t)nq * (K - home_len) + (uint64_t)nq * (home_len - 1) -
-                             (uint64_t)nq * ql0 - (uint64_t)nq * (nq - 1) / 2;
-                } else {
-                    evals += (uint64_t)nq * K;
-                }
+            if (st.consumed == st.issued) break;
+            // consumer
+            const int r = st.consumed % kNBuf;
+            if (!mbar_wait_bounded(&ws.bar[r], (st.consumed / kNBuf) & 1u, a.timeout_ns)) {
+                failed = true;
+                if (lane == 0) atomicOr(a.error, kErrTimeout);
+                // let the other copies in flight land before leaving
+                for (uint32_t k = st.consumed + 1; k < st.issued; ++k)
+                    (void)mbar_wait_bounded(&ws.bar[k % kNBuf], (k / kNBuf) & 1u, a.timeout_ns);
+                break;
             }
-
-            // 2-4. stream the candidates through the chunk buffers
-            const uint32_t nchunks = (K + kChunk - 1) / kChunk;
-            uint32_t rcur = 0;
-            issue_chunk(ws, 0, 0, min(K, (uint32_t)kChunk), nranges, rcur, rec, rsb, lane);
-            for (uint32_t ch = 0; ch < nchunks; ++ch) {
-                const int bsel = ch & 1;
-                if (ch + 1 < nchunks) {
-                    const uint32_t k0 = (ch + 1) * kChunk;
-                    issue_chunk(ws, bsel ^ 1, k0, min(K, k0 + kChunk), nranges, rcur, rec, rsb,
-                                lane);
-                }
-                if (!mbar_wait_bounded(&ws.bar[bsel], (phase >> bsel) & 1u, a.timeout_ns)) {
-                    failed = true;
-                    if (lane == 0) atomicOr(a.error, kErrTimeout);
-                    // let the other buffer's copies land before leaving
-                    if (ch + 1 < nchunks)
-                        (void)mbar_wait_bounded(&ws.bar[bsel ^ 1], (phase >> (bsel ^ 1)) & 1u,
-                                                a.timeout_ns);
-                    break;
-                }
-                phase ^= 1u << bsel;
-
-                const uint32_t kb = ch * kChunk;
-                const uint32_t clen = min((uint32_t)kChunk, K - kb);
-                const T *cb = reinterpret_cast<const T *>(ws.buf[bsel]);
-                const T *qb = reinterpret_cast<const T *>(ws.q);
-                const bool home_chunk = UNI && kb < home_len;
-                const uint32_t ql_base = it.y * kQueryBlock;
-
-                // this lane's candidates
-                T y[kCPL][D];
-                uint32_t cid[kCPL];
-                uint32_t kflat[kCPL];
-#pragma unroll
-                for (int s = 0; s < kCPL; ++s) {
-                    const uint32_t slot = lane + 32 * s;
-                    kflat[s] = kb + slot;
-                    if (slot < clen) {
-                        const T *r = cb + (size_t)slot * a.rs;
-#pragma unroll
-                        for (int j = 0; j < D; ++j) y[s][j] = r[j];
-                        if (F32)
-                            cid[s] = __float_as_uint((float)r[D]);
-                        else
-                            cid[s] = (uint32_t)__double_as_longlong((double)r[D]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < D; ++j) y[s][j] = (T)INFINITY;
-                        cid[s] = 0xffffffffu;
-                    }
-                }
-
-                if (F32) {
-                    f2_t cx[D];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) cx[j] = f2_pack((float)y[0][j], (float)y[1][j]);
-                    const float lo32 = a.lo32, hi32 = a.hi32;
-                    for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const float *qr = reinterpret_cast<const float *>(qb) + (size_t)qi * a.rs;
-                        float qv[D];
-#pragma unroll
-                        for (int j = 0; j < D; ++j) qv[j] = qr[j];
-                        f2_t t = f2_sub(cx[0], f2_pack(qv[0], qv[0]));
-                        f2_t s2 = f2_mul(t, t);
-#pragma unroll
-                        for (int j = 1; j < D; ++j) {
-                            t = f2_sub(cx[j], f2_pack(qv[j], qv[j]));
-                            s2 = f2_fma(t, t, s2);
-                        }
-                        float sv[2];
-                        f2_unpack(s2, sv[0], sv[1]);
-                        bool maybe[kCPL];
-#pragma unroll
-                        for (int s = 0; s < kCPL; ++s) maybe[s] = sv[s] <= hi32;
-                        if (home_chunk) {
-                            const uint32_t ql = ql_base + qi;
-#pragma unroll
-                            for (int s = 0; s < kCPL; ++s)
-                                if (kflat[s] < home_len && kflat[s] < ql) maybe[s] = false;
-                        }
-                        if (!__any_sync(0xffffffffu, maybe[0] | maybe[1])) continue;
-                        const uint32_t qid = __float_as_uint(qr[D]);
-                        uint32_t npairs[kCPL];
-#pragma unroll
-                        for (int s = 0; s < kCPL; ++s) {
-                            bool hit = maybe[s];
-                            const bool self = home_chunk && kflat[s] == ql_base + qi;
-                            if (hit && !self && sv[s] > lo32) {
-                                ++rechecks;
-                                hit = exact_member<D>(a.pts + (size_t)qid * D,
-                                                      a.pts + (size_t)cid[s] * D, a.E2);
-                            }
-                            npairs[s] = hit ? ((UNI && !self) ? 2u : 1u) : 0u;
-                        }
-                        emit_pairs(em, ws, a, lane, qid, cid, npairs);
-                    }
-                } else {
-                    for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const double *qr =
-                            reinterpret_cast<const double *>(qb) + (size_t)qi * a.rs;
-                        double qv[D];
-#pragma unroll
-                        for (int j = 0; j < D; ++j) qv[j] = qr[j];
-                        bool hitv[kCPL];
-#pragma unroll
-                        for (int s = 0; s < kCPL; ++s) {
-                            double sd = 0.0;
-#pragma unroll
-                            for (int j = 0; j < D; ++j) {
-                                double t = __dsub_rn(qv[j], (double)y[s][j]);
-                                sd = __dadd_rn(sd, __dmul_rn(t, t));
-                            }
-                            hitv[s] = (sd <= a.E2) && cid[s] != 0xffffffffu;
-                        }
-                        if (home_chunk) {
-                            const uint32_t ql = ql_base + qi;
-#pragma unroll
-                            for (int s = 0; s < kCPL; ++s)
-                                if (kflat[s] < home_len && kflat[s] < ql) hitv[s] = false;
-                        }
-                        if (!__any_sync(0xffffffffu, hitv[0] | hitv[1])) continue;
-                        const uint32_t qid = (uint32_t)__double_as_longlong(qr[D]);
-                        uint32_t npairs[kCPL];
-#pragma unroll
-                        for (int s = 0; s < kCPL; ++s) {
-                            const bool self = home_chunk && kflat[s] == ql_base + qi;
-                            npairs[s] = hitv[s] ? ((UNI && !self) ? 2u : 1u) : 0u;
-                        }
-                        emit_pairs(em, ws, a, lane, qid, cid, npairs);
-                    }
-                }
-                __syncwarp();
+            consume_chunk<D, F32, UNI>(st, ws, st.cons_seq & 1, st.c_chunk, r, a, lane, rechecks);
+            ++st.consumed;
+            ++st.c_chunk;
+            if (st.c_chunk == ws.hdr[st.cons_seq & 1].nchunks) {
+                ++st.cons_seq;
+                st.c_chunk = 0;
             }
-            __syncwarp();
         }
-        if (failed) break;
     }
-    flush(em, ws, a, lane);
+    if (!failed) flush(st, ws, a, lane);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rechecks += __shfl_xor_sync(0xffffffffu, rechecks, o);
     if (lane == 0) {
@@ -647,6 +886,7 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     }
     a.lo32 = g.lo32;
     a.hi32 = g.hi32;
+    a.w32 = g.w32;
     a.E2 = g.E2;
     a.out = out;
     a.cap = cap;
@@ -657,29 +897,45 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     a.grab = cfg.grab > 0 ? cfg.grab : 1;
     const int esz = f32 ? 4 : 8;
     const int rsb = a.rs * esz;
+    // query record: FP32 (m_j, m_j) pairs, (pp, pp), id -> 2d + 3 floats;
+    // FP64: x_0..x_{d-1}, id
+    a.qrs = f32 ? ((2 * d + 3 + 3) & ~3) : ((d + 1 + 1) & ~1);
+    a.cb = 32 * cpl_for(d, f32);
     a.sm_ranges = round16(a.n_templates * (int)sizeof(uint2));
-    a.sm_queries = round16(kQueryBlock * rsb);
-    a.sm_chunk = round16(kChunk * rsb);
+    a.sm_queries = round16(kQueryBlock * a.qrs * esz);
+    a.sm_chunk = round16(a.cb * rsb);
     a.eb = kEmit;
     a.sm_emit = round16(kEmit * (int)sizeof(uint2));
-    a.sm_warp = 16 + a.sm_ranges + a.sm_queries + 2 * a.sm_chunk + a.sm_emit;
-    a.cb = kChunk;
+    a.sm_warp = 64 + round16(2 * (int)sizeof(ItemHdr)) + 2 * a.sm_ranges + 2 * a.sm_queries +
+                nbuf_for(d, f32) * a.sm_chunk + a.sm_emit;
     a.timeout_ns = 2000000000ull;
 
     KernelFn fn = pick_kernel(d, f32, uni);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
-    const size_t smem = (size_t)a.sm_warp * kWarpsPerBlock;
-    SJ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0;
     SJ_CUDA_TRY(cudaGetDevice(&dev));
-    int per_sm = 0;
-    SJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWarpsPerBlock * 32, smem));
-    if (per_sm < 1) return fail(err, SJ_EINVAL, "join kernel does not fit on an SM");
+    int smem_optin = 0, smem_sm = 0;
+    SJ_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SJ_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    // warps per block: the block size (8, 4, 2 or 1 warps) that keeps the most
+    // warps resident per SM under the shared-memory and register limits
+    SJ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     std::min(smem_optin, (int)a.sm_warp * kWarpsPerBlock)));
+    int wpb = 0, per_sm = 0, best = 0;
+    for (int w = kWarpsPerBlock; w >= 1; w /= 2) {
+        if ((size_t)a.sm_warp * w > (size_t)smem_optin) continue;
+        int b = 0;
+        SJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, w * 32, (size_t)a.sm_warp * w));
+        if (b * w > best) { best = b * w; wpb = w; per_sm = b; }
+    }
+    if (best < 1) return fail(err, SJ_EINVAL, "join kernel does not fit on an SM");
+    const size_t smem = (size_t)a.sm_warp * wpb;
+    (void)smem_sm;
     int blocks = cfg.blocks > 0 ? cfg.blocks : per_sm * sm_count(dev);
     if (item_end <= item_begin) blocks = 1;
     SJ_CUDA_TRY(cudaMemsetAsync(d_work, 0, sizeof(uint32_t), s));
     if (ev0) SJ_CUDA_TRY(cudaEventRecord(ev0, s));
-    fn<<<blocks, kWarpsPerBlock * 32, smem, s>>>(a, n_items_dev(ix) - 1); note_launch();
+    fn<<<blocks, wpb * 32, smem, s>>>(a, n_items_dev(ix) - 1); note_launch();
     SJ_CUDA_TRY(cudaGetLastError());
     if (ev1) SJ_CUDA_TRY(cudaEventRecord(ev1, s));
     return SJ_OK;

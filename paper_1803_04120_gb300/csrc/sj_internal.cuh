@@ -74,6 +74,7 @@ struct Geometry {
     // member, otherwise recompute in FP64.  fp32_ok = 0 when the margin is
     // unusable and the FP32 mode falls back to FP64 arithmetic.
     float lo32 = -1.0f, hi32 = 0.0f;
+    float w32 = 0.0f;                  // fl32(w): cell side in the FP32 frame
     int fp32_ok = 0;
 };
 
@@ -101,6 +102,9 @@ struct Index {
     uint64_t bytes = 0;
     cudaStream_t owner_stream = nullptr;
 };
+
+// FP32 filter margin of a geometry (margin.cu): sets w32, lo32, hi32, fp32_ok.
+void fp32_margin(Geometry &g);
 
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
                       int lookup_mode, cudaStream_t s, Index &ix);
@@ -131,7 +135,9 @@ struct JoinArgs {
     int32_t ng[kMaxDim];
     uint64_t stride[kMaxDim];
     float lo32, hi32;
+    float w32;                      // cell side in the FP32 frame
     double E2;
+    int qrs;                        // staged query record stride (elements)
     // output
     uint2 *out;
     uint64_t cap;

@@ -32,7 +32,7 @@ ABI_FUNCTIONS = (
     "sj_selfjoin", "sj_selfjoin_index", "sj_selfjoin_device", "sj_selfjoin_index_device",
     "sj_selfjoin_count", "sj_selfjoin_stream", "sj_result_count", "sj_result_pairs",
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
-    "sj_result_times",
+    "sj_result_times", "sj_fp32_margin",
 )
 
 
@@ -119,6 +119,8 @@ def load(build: bool = True):
             "sj_result_times": (i32, [P, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+            "sj_fp32_margin": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -376,6 +378,17 @@ class Index:
         if st != SJ_OK:
             raise SJError(st, "sj_index_export")
         return B, G, A, M
+
+
+def sj_fp32_margin(d: int, eps: float, gmin, gmax):
+    """(status, w32, lo, hi) of the FP32 filter margin for a grid (host only)."""
+    lib = load()
+    gmin = np.ascontiguousarray(gmin, dtype=np.float64)
+    gmax = np.ascontiguousarray(gmax, dtype=np.float64)
+    w, lo, hi = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    st = lib.sj_fp32_margin(d, float(eps), gmin.ctypes.data, gmax.ctypes.data,
+                            ctypes.byref(w), ctypes.byref(lo), ctypes.byref(hi))
+    return st, w.value, lo.value, hi.value
 
 
 def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:

@@ -99,9 +99,14 @@ def test_edge_cases(ctxs):
     # eps larger than the data range: all pairs
     pts = datagen.uniform(300, 3, seed=9)
     assert gpu_keys(ctx, pts, 1000.0).size == 300 * 300
-    # eps tiny: self-pairs only
-    k = gpu_keys(ctx, pts, 1e-12)
+    # eps small against the data range: self-pairs only
+    k = gpu_keys(ctx, pts, 1e-4)
     assert_same(k, (np.arange(300, dtype=np.uint64) << np.uint64(32)) | np.arange(300, dtype=np.uint64), "tiny eps")
+    # a grid of 2^63 or more cells is refused, not approximated
+    with pytest.raises(sj.SJError) as ei:
+        ctx.sj_selfjoin(pts, 1e-12)
+    assert ei.value.status == sj.SJ_ERANGE
+    assert ctx.sj_selfjoin(pts, 1e-4).shape[0] == 300
     # negative and large-offset coordinates
     off = datagen.uniform(2000, 2, seed=10) - 1e6
     assert_same(gpu_keys(ctx, off, 0.7), orc.grid_join(off, 0.7), "offset coordinates")

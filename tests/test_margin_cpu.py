@@ -1,0 +1,131 @@
+"""Soundness of the FP32 filter margin (CPU only).
+
+The kernel's FP32 evaluation is emulated here bit-exactly with rational
+arithmetic (every operation rounded to nearest FP32 on its own, fused
+multiply-adds rounded once), and the exact FP64 member test is evaluated the
+same way.  For adversarial pairs placed at the threshold, a value at or below
+the library's ``lo`` must be a member and a value above ``hi`` must not be.
+"""
+import math
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+
+from paper_1803_04120_gb300 import sj
+
+
+def rn(x: F, mant: int, emin: int) -> F:
+    """Round a rational to the nearest binary float with `mant` significand
+    bits and minimum normal exponent `emin` (ties to even, gradual underflow)."""
+    if x == 0:
+        return F(0)
+    s = -1 if x < 0 else 1
+    a = abs(x)
+    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
+    # fix the estimate so that 2^e <= a < 2^(e+1)
+    while F(2) ** e > a:
+        e -= 1
+    while F(2) ** (e + 1) <= a:
+        e += 1
+    e = max(e, emin)
+    q = a / F(2) ** (e - mant + 1)
+    n, r = divmod(q.numerator, q.denominator)
+    rem = F(r, q.denominator)
+    if rem > F(1, 2) or (rem == F(1, 2) and n % 2 == 1):
+        n += 1
+    return s * F(n) * F(2) ** (e - mant + 1)
+
+
+def r32(x):
+    return rn(F(x), 24, -126)
+
+
+def r64(x):
+    return rn(F(x), 53, -1022)
+
+
+def exact_member(a, b, E2):
+    s = F(0)
+    for x, y in zip(a, b):
+        t = r64(F(x) - F(y))
+        s = r64(s + r64(t * t))
+    return s <= E2
+
+
+def cell_of(x, gmin, inv_w, ng):
+    q = float(r64(r64(F(x) - F(gmin)) * F(inv_w)))
+    return min(max(int(math.floor(q)), 0), ng - 1)
+
+
+def kernel_s32(p, q, gmin, w32, cells):
+    """s32 as the kernel computes it for query p (home cell `cells`) and
+    candidate q."""
+    d = len(p)
+    zp, zq = [], []
+    for j in range(d):
+        o = r32(r32(F(cells[j]) + F(1, 2)) * F(w32))
+        yp = r32(r64(F(p[j]) - F(gmin[j])))
+        yq = r32(r64(F(q[j]) - F(gmin[j])))
+        zp.append(r32(yp - o))
+        zq.append(r32(yq - o))
+    pp = F(0)
+    qq = F(0)
+    for j in range(d):
+        pp = r32(zp[j] * zp[j] + pp)
+        qq = r32(zq[j] * zq[j] + qq)
+    acc = r32(qq + pp)
+    for j in range(d):
+        acc = r32((-2 * zp[j]) * zq[j] + acc)
+    return acc
+
+
+@pytest.mark.parametrize("d,eps,scale,offset", [
+    (2, 0.31915, 100.0, 0.0), (3, 1.96949, 100.0, 0.0), (6, 13.55112, 100.0, 0.0),
+    (2, 0.37, 30.0, -1e6), (8, 0.9, 10.0, 5.0), (1, 0.05, 1000.0, 0.0)])
+def test_margin_sound_on_threshold_pairs(d, eps, scale, offset):
+    rng = np.random.default_rng(int(eps * 1000) + d)
+    pts = offset + rng.uniform(0, scale, size=(60, d))
+    extra = []
+    for p in pts:
+        v = rng.normal(size=d)
+        v /= np.linalg.norm(v)
+        for f in (1.0, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -52, 1.0 + 3e-7, 1.0 - 3e-7,
+                  1.0 + 2e-6, 1.0 - 2e-6):
+            extra.append(p + v * eps * f)
+    allp = np.concatenate([pts, np.array(extra)])
+    gmin = allp.min(axis=0) - eps
+    gmax = allp.max(axis=0) + eps
+    st, w32, lo, hi = sj.sj_fp32_margin(d, eps, gmin, gmax)
+    assert st == sj.SJ_OK
+    E2 = r64(F(eps) * F(eps))
+    w = eps * (1.0 + 2.0 ** -16)
+    inv_w = 1.0 / w
+    ng = [int(math.floor((gmax[j] - gmin[j]) / w)) + 1 for j in range(d)]
+    # the band is narrow: its width relative to eps^2 grows with the FP32
+    # rounding of the stored coordinates, u * (range / eps)
+    X = float(np.max(gmax - gmin))
+    assert (hi - max(lo, 0.0)) / float(E2) < 1e-4 + 40 * 2.0 ** -24 * X / eps
+    checked = 0
+    for k, p in enumerate(pts):
+        cells = [cell_of(p[j], gmin[j], inv_w, ng[j]) for j in range(d)]
+        for q in extra[7 * k: 7 * k + 7]:
+            cq = [cell_of(q[j], gmin[j], inv_w, ng[j]) for j in range(d)]
+            if max(abs(a - b) for a, b in zip(cells, cq)) > 1:
+                continue           # not adjacent: never compared
+            s = kernel_s32(p, q, gmin, w32, cells)
+            mem = exact_member(p, q, E2)
+            if s <= F(lo):
+                assert mem, (d, k)
+            if s > F(hi):
+                assert not mem, (d, k)
+            checked += 1
+    assert checked > 100
+
+
+def test_margin_rejects_unusable_grids():
+    # a grid many orders of magnitude wider than eps leaves no useful margin
+    st, _, _, _ = sj.sj_fp32_margin(2, 1e-9, np.array([0.0, 0.0]), np.array([1e8, 1.0]))
+    assert st in (sj.SJ_ERANGE,)
+    st, _, _, _ = sj.sj_fp32_margin(2, -1.0, np.zeros(2), np.ones(2))
+    assert st == sj.SJ_EINVAL
