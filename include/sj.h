@@ -108,7 +108,10 @@ typedef struct {
     int32_t max_inflight;    /* sj_submit: most requests admitted at once; default 64 */
     uint64_t serve_mem_bytes;/* sj_submit: device bytes the admitted requests may
                                 hold together; default 8 GiB */
-    int32_t reserved[8];
+    /* launch tuning of the search-and-refine kernel; -1 (default) lets the
+     * library (or the tuner, with autotune = 1) choose */
+    int32_t grab;            /* work items a warp takes per cursor bump */
+    int32_t reserved[7];
 } sj_config;
 
 /* Fills *cfg with the defaults listed above. */

@@ -226,7 +226,7 @@ JoinLaunch launch_cfg(const sj_ctx *ctx) {
     JoinLaunch l;
     l.prec_fp32 = ctx->cfg.prec == SJ_PREC_FP32_RECHECK;
     l.unicomp = ctx->cfg.unicomp;
-    l.grab = 1;
+    l.grab = ctx->cfg.grab > 0 ? ctx->cfg.grab : 1;
     return l;
 }
 
@@ -549,6 +549,7 @@ void sj_config_default(sj_config *cfg) {
     cfg->profile = 0;
     cfg->max_inflight = 64;
     cfg->serve_mem_bytes = 8ull << 30;
+    cfg->grab = -1;
 }
 
 const char *sj_status_str(sj_status st) {

@@ -48,7 +48,8 @@ class sj_config(ctypes.Structure):
                 ("sorted", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("lookup", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
-                ("serve_mem_bytes", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 8)]
+                ("serve_mem_bytes", ctypes.c_uint64), ("grab", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class sj_index_desc(ctypes.Structure):
@@ -180,7 +181,8 @@ class Context:
     def __init__(self, prec: int = SJ_PREC_FP32_RECHECK, unicomp: bool = True,
                  out_cap_bytes: int = 2 << 30, min_batches: int = 3, sorted: bool = False,
                  device: int = 0, lookup: int = SJ_LOOKUP_AUTO, profile: bool = False,
-                 max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True):
+                 max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True,
+                 grab: int = -1):
         lib = load()
         cfg = sj_config()
         lib.sj_config_default(ctypes.byref(cfg))
@@ -188,6 +190,7 @@ class Context:
         cfg.out_cap_bytes, cfg.min_batches, cfg.sorted = out_cap_bytes, min_batches, int(sorted)
         cfg.device, cfg.lookup, cfg.profile = device, lookup, int(profile)
         cfg.max_inflight, cfg.serve_mem_bytes, cfg.autotune = max_inflight, serve_mem_bytes, int(autotune)
+        cfg.grab = grab
         h = ctypes.c_void_p()
         st = lib.sj_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != SJ_OK:
