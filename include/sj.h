@@ -52,6 +52,7 @@
 #ifndef SJ_H
 #define SJ_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -231,6 +232,32 @@ SJ_API sj_status sj_selfjoin_count(sj_ctx *ctx, const double *pts, uint64_t n, i
 typedef int (*sj_chunk_cb)(const uint32_t *pairs, uint64_t k, void *user);
 SJ_API sj_status sj_selfjoin_stream(sj_ctx *ctx, const double *pts, uint64_t n, int d,
                              double eps, sj_chunk_cb cb, void *user);
+
+/* Join for callers that cannot allocate memory (the paper has no
+ * counterpart; this is a deployment convenience).  Some callers may not call
+ * cudaMalloc or any allocating routine: code running inside another
+ * framework's pre-reserved memory budget, or code that must account for
+ * every allocation up front.  This call runs the same index build and
+ * search-and-refine kernels as sj_selfjoin_device (FP32 filter + FP64
+ * recheck, UNICOMP) without a context and allocates nothing: all working
+ * memory comes from one fixed region of 24 MiB that every GPU loading the
+ * library holds until the process exits.
+ *   d_pts    n x d row-major FP64, device memory, not modified;
+ *   d_pairs  device buffer of cap_pairs pairs (2 * cap_pairs uint32);
+ *   count    receives the pair count (also when it exceeds cap_pairs: then
+ *            only cap_pairs pairs are written and SJ_EOVERFLOW returned);
+ *   stream   a cudaStream_t (NULL: legacy default stream); the call waits
+ *            for it before returning;
+ *   msg      optional buffer of msg_len bytes for an error message.
+ * Limits: n <= 65536 points, d in [1, 8], and the grid (Section IV-B) at
+ * most 2^20 cells, else SJ_ERANGE; host pointers are rejected with
+ * SJ_EINVAL.  The region's device address is looked up on the first call on
+ * each device (make that first call before any stream capture).  Calls share
+ * the region: they are serialised within the process, and work that
+ * overlaps with them on the GPU through the same region would race. */
+SJ_API sj_status sj_selfjoin_noalloc(const double *d_pts, uint64_t n, int d, double eps,
+                                     uint32_t *d_pairs, uint64_t cap_pairs, uint64_t *count,
+                                     void *stream, char *msg, size_t msg_len);
 
 /* ------------------------------------------------------------------ */
 /* Results.                                                           */

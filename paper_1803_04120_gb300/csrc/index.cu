@@ -467,4 +467,146 @@ const uint32_t *n_items_dev(const Index &ix) {
                                               2 * kMaxDim) + 2;
 }
 
+// Index build for callers that cannot allocate device memory: the same
+// kernels as build_index, with every array carved from `region` (a device
+// address, region_bytes long) and the points read in place from d_pts (a
+// device pointer that must stay valid while the index is used).  Dense
+// lookup table only (grid_cells <= max_grid_cells, else SJ_ERANGE); nothing
+// is allocated and the returned Index owns nothing (never pass it to
+// free_index).
+sj_status build_index_static(Error &err, const double *d_pts, uint64_t n, int d, double eps,
+                             unsigned char *region, size_t region_bytes, uint64_t max_grid_cells,
+                             cudaStream_t s, Index &ix) {
+    ix = Index();
+    ix.owner_stream = s;
+    if (d_pts == nullptr || n == 0 || d < 1 || d > kMaxDim || !(eps > 0.0) || !std::isfinite(eps))
+        return fail(err, SJ_EINVAL, "invalid argument (pts, n, d in [1,8], eps > 0 finite)");
+    size_t off = 0;
+    bool exhausted = false;
+    auto take = [&](DevBuf &b, size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        if (off + bytes > region_bytes) { exhausted = true; return; }
+        b.p = region + off;
+        b.bytes = bytes;
+        off += bytes;
+    };
+    Geometry &g = ix.g;
+    g.d = d;
+    g.n = n;
+    g.eps = eps;
+    g.E2 = eps * eps;
+    g.w = eps * (1.0 + std::ldexp(1.0, -16));
+    ix.pts.p = const_cast<double *>(d_pts);
+    ix.pts.bytes = n * d * sizeof(double);
+
+    take(ix.counts_dev, (2 * kMaxDim) * sizeof(unsigned long long) + 64);
+    if (exhausted) return fail(err, SJ_ERANGE, "static scratch exhausted");
+    unsigned long long *d_minmax = static_cast<unsigned long long *>(ix.counts_dev.p);
+    uint32_t *d_counts = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxDim);
+    SJ_CUDA_TRY(cudaMemsetAsync(d_counts, 0, 64, s));
+    init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_counts); note_launch();
+    {
+        int blocks = 2 * sm_count(-1);
+        const uint64_t need = (n + kThreads - 1) / kThreads;
+        if ((uint64_t)blocks > need) blocks = (int)need;
+        bounds_kernel<<<blocks, kThreads, 0, s>>>(d_pts, n, d, d_minmax, d_counts); note_launch();
+    }
+    SJ_CUDA_TRY(cudaGetLastError());
+    unsigned long long h_mm[2 * kMaxDim + 8];
+    SJ_CUDA_TRY(cudaMemcpyAsync(h_mm, d_minmax, sizeof(h_mm), cudaMemcpyDeviceToHost, s));
+    SJ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (reinterpret_cast<const uint32_t *>(h_mm + 2 * kMaxDim)[0] & 1u)
+        return fail(err, SJ_EINVAL, "non-finite coordinate");
+    uint64_t stride = 1;
+    double total = 1.0;
+    for (int j = 0; j < d; ++j) {
+        g.gmin[j] = from_order_key(h_mm[2 * j]) - eps;
+        g.gmax[j] = from_order_key(h_mm[2 * j + 1]) + eps;
+        const double cells = std::floor((g.gmax[j] - g.gmin[j]) / g.w) + 1.0;
+        total *= cells;
+        if (!(cells < 2147483648.0) || !(total <= (double)max_grid_cells))
+            return fail(err, SJ_ERANGE, "grid larger than the static lookup table allows");
+        g.ng[j] = (int64_t)cells;
+        g.stride[j] = stride;
+        stride *= (uint64_t)g.ng[j];
+    }
+    g.grid_cells = stride;
+    fp32_margin(g);
+    ix.dense = 1;
+
+    CellParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.d = d;
+    cp.inv_w = 1.0 / g.w;
+    for (int j = 0; j < d; ++j) {
+        cp.gmin[j] = g.gmin[j];
+        cp.ng[j] = g.ng[j];
+        cp.stride[j] = g.stride[j];
+    }
+    uint64_t maxng = 1;
+    for (int j = 0; j < d; ++j) maxng = (uint64_t)g.ng[j] > maxng ? (uint64_t)g.ng[j] : maxng;
+    ix.mwords = (uint32_t)((maxng + 31) / 32);
+    ix.rs32 = (d + 1 + 3) / 4 * 4;
+    ix.rs64 = (d + 1 + 1) / 2 * 2;
+    DevBuf key, rank, skey, head, sums;
+    take(ix.lut, (g.grid_cells + 1) * sizeof(uint32_t));
+    take(key, n * sizeof(uint64_t));
+    take(rank, n * sizeof(uint32_t));
+    take(ix.A, n * sizeof(uint32_t));
+    take(skey, n * sizeof(uint64_t));
+    take(head, n * sizeof(uint32_t));
+    take(ix.B, n * sizeof(uint64_t));
+    take(ix.G, (n + 1) * sizeof(uint32_t));
+    take(ix.cc, n * d * sizeof(int32_t));
+    take(ix.M, (uint64_t)d * ix.mwords * sizeof(uint32_t));
+    take(ix.rec32, n * ix.rs32 * sizeof(float));
+    take(ix.items, n * sizeof(uint2));
+    const uint64_t scan_max = (g.grid_cells + 1) > n ? (g.grid_cells + 1) : n;
+    take(sums, scan_sums_needed(scan_max) * sizeof(uint32_t));
+    if (!g.fp32_ok) take(ix.rec64, n * ix.rs64 * sizeof(double));
+    if (exhausted) return fail(err, SJ_ERANGE, "static scratch exhausted");
+    uint32_t *lut = static_cast<uint32_t *>(ix.lut.p);
+    uint32_t *ps = static_cast<uint32_t *>(sums.p);
+    const size_t ps_cap = sums.bytes / sizeof(uint32_t);
+
+    // the region keeps the previous call's contents: clear what accumulates
+    SJ_CUDA_TRY(cudaMemsetAsync(lut, 0, (g.grid_cells + 1) * sizeof(uint32_t), s));
+    SJ_CUDA_TRY(cudaMemsetAsync(ix.M.p, 0, ix.M.bytes, s));
+    cell_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, n, cp, static_cast<uint64_t *>(key.p),
+                                                 static_cast<uint32_t *>(rank.p), lut); note_launch();
+    SJ_CUDA_TRY(cudaGetLastError());
+    SJ_TRY(exclusive_scan_u32_scratch(err, lut, lut, g.grid_cells + 1, d_counts + 3, ps, ps_cap, s));
+    scatter_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(key.p),
+                                                    static_cast<uint32_t *>(rank.p), lut, n,
+                                                    static_cast<uint32_t *>(ix.A.p),
+                                                    static_cast<uint64_t *>(skey.p)); note_launch();
+    uint32_t *hs = static_cast<uint32_t *>(head.p);
+    head_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(skey.p), n, hs); note_launch();
+    SJ_CUDA_TRY(cudaGetLastError());
+    SJ_TRY(exclusive_scan_u32_scratch(err, hs, hs, n, d_counts + 1, ps, ps_cap, s));
+    rle_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(skey.p), hs, n, d_counts + 1,
+                                                 static_cast<uint64_t *>(ix.B.p),
+                                                 static_cast<uint32_t *>(ix.G.p)); note_launch();
+    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(ix.B.p), d_counts + 1, cp,
+                                                  ix.mwords, static_cast<int32_t *>(ix.cc.p),
+                                                  static_cast<uint32_t *>(ix.M.p)); note_launch();
+    rec32_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, static_cast<uint32_t *>(ix.A.p), n, cp,
+                                                  ix.rs32, static_cast<float *>(ix.rec32.p)); note_launch();
+    if (ix.rec64.p) {
+        rec64_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, static_cast<const uint32_t *>(ix.A.p), n, d,
+                                                      ix.rs64, static_cast<double *>(ix.rec64.p)); note_launch();
+    }
+    SJ_CUDA_TRY(cudaGetLastError());
+    uint32_t *icnt = static_cast<uint32_t *>(rank.p);   // ranks are consumed by now
+    item_count_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint32_t *>(ix.G.p), d_counts + 1,
+                                                       n, icnt); note_launch();
+    SJ_CUDA_TRY(cudaGetLastError());
+    SJ_TRY(exclusive_scan_u32_scratch(err, icnt, icnt, n, d_counts + 2, ps, ps_cap, s));
+    item_fill_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint32_t *>(ix.G.p), d_counts + 1,
+                                                      icnt, static_cast<uint2 *>(ix.items.p)); note_launch();
+    SJ_CUDA_TRY(cudaGetLastError());
+    ix.bytes = off;
+    return SJ_OK;
+}
+
 }  // namespace sj

@@ -104,6 +104,33 @@ __global__ void __launch_bounds__(kScanThreads) scan_tile_kernel(const uint32_t 
 
 }  // namespace
 
+// Tile sums the scan below needs for n elements (two levels: up to 4096^2).
+uint64_t scan_sums_needed(uint64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+// The same exclusive scan with its tile sums in a caller-provided device
+// buffer (sums_cap entries) instead of freshly allocated memory.
+sj_status exclusive_scan_u32_scratch(Error &err, const uint32_t *in, uint32_t *out, uint64_t n,
+                                     uint32_t *d_total, uint32_t *sums, uint64_t sums_cap,
+                                     cudaStream_t s) {
+    if (n == 0) {
+        if (d_total) SJ_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
+        return SJ_OK;
+    }
+    const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        scan_tile_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, d_total); note_launch();
+        SJ_CUDA_TRY(cudaGetLastError());
+        return SJ_OK;
+    }
+    if (tiles > (uint64_t)kScanTile || tiles > sums_cap)
+        return fail(err, SJ_ERANGE, "scan scratch too small");
+    scan_reduce_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums); note_launch();
+    scan_tile_kernel<<<1, kScanThreads, 0, s>>>(sums, sums, tiles, nullptr, d_total); note_launch();
+    scan_tile_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums, nullptr); note_launch();
+    SJ_CUDA_TRY(cudaGetLastError());
+    return SJ_OK;
+}
+
 sj_status exclusive_scan_u32(Error &err, const uint32_t *in, uint32_t *out, uint64_t n,
                              uint32_t *d_total, cudaStream_t s) {
     if (n == 0) {

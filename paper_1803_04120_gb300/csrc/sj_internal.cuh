@@ -110,6 +110,10 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
                       int lookup_mode, cudaStream_t s, Index &ix);
 void free_index(Index &ix, cudaStream_t s);
 sj_status ensure_rec64(Error &err, Index &ix, cudaStream_t s);
+// Build into a caller-provided device region, allocating nothing (index.cu).
+sj_status build_index_static(Error &err, const double *d_pts, uint64_t n, int d, double eps,
+                             unsigned char *region, size_t region_bytes, uint64_t max_grid_cells,
+                             cudaStream_t s, Index &ix);
 sj_status read_counts(Error &err, Index &ix, cudaStream_t s);
 const uint32_t *n_items_dev(const Index &ix);
 
@@ -171,6 +175,11 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
 // sum.  Returns SJ_OK or an error.
 sj_status exclusive_scan_u32(Error &err, const uint32_t *in, uint32_t *out, uint64_t n,
                              uint32_t *d_total, cudaStream_t s);
+// The same with caller-provided tile sums (n up to 4096^2).
+uint64_t scan_sums_needed(uint64_t n);
+sj_status exclusive_scan_u32_scratch(Error &err, const uint32_t *in, uint32_t *out, uint64_t n,
+                                     uint32_t *d_total, uint32_t *sums, uint64_t sums_cap,
+                                     cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) by the low `bits` bits of key.
 sj_status radix_sort_pairs(Error &err, uint64_t *keys, uint32_t *vals, uint64_t n, int bits,

@@ -32,7 +32,7 @@ ABI_FUNCTIONS = (
     "sj_selfjoin", "sj_selfjoin_index", "sj_selfjoin_device", "sj_selfjoin_index_device",
     "sj_selfjoin_count", "sj_selfjoin_stream", "sj_result_count", "sj_result_pairs",
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
-    "sj_result_times", "sj_fp32_margin",
+    "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc",
 )
 
 
@@ -122,6 +122,8 @@ def load(build: bool = True):
                                       ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+            "sj_selfjoin_noalloc": (i32, [P, u64, i32, f64, P, u64, ctypes.POINTER(ctypes.c_uint64),
+                                          P, ctypes.c_char_p, ctypes.c_size_t]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -381,6 +383,26 @@ class Index:
         if st != SJ_OK:
             raise SJError(st, "sj_index_export")
         return B, G, A, M
+
+
+def sj_selfjoin_noalloc(points, eps: float, out, stream=None, raise_overflow: bool = True) -> int:
+    """Join for callers that cannot allocate: device points (contiguous
+    (n, d) float64 CUDA tensor) into the device tensor ``out`` of shape
+    (cap, 2), using only the library's fixed static scratch (n <= 65536).
+    Returns the pair count."""
+    p, n, d, keep = _points_ptr(points)
+    lib = load()
+    cap = 0 if out is None else out.shape[0]
+    optr = ctypes.c_void_p(out.data_ptr()) if out is not None and cap else None
+    cnt = ctypes.c_uint64(0)
+    msg = ctypes.create_string_buffer(256)
+    st = lib.sj_selfjoin_noalloc(p, n, d, float(eps), optr, cap, ctypes.byref(cnt),
+                                 _stream_ptr(stream), msg, 256)
+    if st == SJ_EOVERFLOW and not raise_overflow:
+        return int(cnt.value)
+    if st != SJ_OK:
+        raise SJError(st, "sj_selfjoin_noalloc: " + msg.value.decode())
+    return int(cnt.value)
 
 
 def sj_fp32_margin(d: int, eps: float, gmin, gmax):
