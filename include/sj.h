@@ -268,6 +268,39 @@ SJ_API const uint32_t *sj_result_pairs(const sj_result *r);   /* 2 * count uint3
 SJ_API void sj_result_free(sj_result *r);                     /* NULL is ignored */
 
 /* ------------------------------------------------------------------ */
+/* Many joins at once.                                                */
+/* ------------------------------------------------------------------ */
+
+/* One join of a multi-join call: n x d row-major FP64 points (host or device
+ * memory, owned by the caller) and its epsilon. */
+typedef struct {
+    const double *pts;
+    uint64_t n;
+    int32_t d;
+    int32_t pad;
+    double eps;
+} sj_job;
+
+/* Runs n_jobs independent self-joins of uneven n, d and eps together
+ * (Section IV and V for each job; the paper runs one join at a time).  The
+ * jobs are grouped into waves of at most 64 whose estimated device memory
+ * fits in serve_mem_bytes; per wave the points of all jobs are bounded in
+ * one launch (one host read-back), then one replay of a captured CUDA graph
+ * builds every job's grid index with batched kernels (each launch covers
+ * all jobs of the wave) and runs ONE persistent search-and-refine launch in
+ * which every warp works through all jobs' work items.  Jobs whose grid is
+ * too large for the dense cell table run alone through sj_selfjoin.
+ * out[i] receives job i's result (library-owned host memory, free with
+ * sj_result_free; pair order unspecified unless sorted = 1) and, when
+ * status is not NULL, status[i] its status.  Returns SJ_OK when every job
+ * succeeded, else the first job error (message in sj_last_error); the other
+ * jobs' results are still returned.  sj_last_stats sums over the jobs
+ * (batches = waves, retries = jobs re-joined alone because their result
+ * outgrew its estimated buffer). */
+SJ_API sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs,
+                                   sj_result **out, sj_status *status);
+
+/* ------------------------------------------------------------------ */
 /* Statistics of the last join on a context.                          */
 /* ------------------------------------------------------------------ */
 
@@ -313,6 +346,25 @@ SJ_API sj_status sj_submit(sj_ctx *ctx, const double *pts, uint64_t n, int d,
  * (the ticket is then consumed); the request's error otherwise;
  * SJ_ENOTFOUND for an unknown ticket.  wait_ms > 0 blocks up to that long. */
 SJ_API sj_status sj_poll(sj_ctx *ctx, uint64_t ticket, int wait_ms, sj_result **out);
+
+/* Counters of the serving scheduler of a context (all zero before the first
+ * sj_submit). */
+typedef struct {
+    uint64_t submitted, completed;
+    uint64_t waves;            /* multi-join waves run */
+    uint64_t max_wave;         /* most requests in one wave */
+    uint64_t overflow_reruns;  /* requests re-joined after their estimate was short */
+    uint64_t standalone;       /* requests run through the stand-alone path */
+    uint64_t graph_launches;   /* CUDA graph replays */
+    uint64_t queued;           /* waiting for admission now */
+    uint64_t mem_in_use;       /* estimated device bytes admitted now */
+    int32_t inflight;          /* admitted requests now */
+    int32_t lanes;             /* waves that may run at the same time */
+    int32_t max_concurrent_waves; /* most waves seen running at once */
+    int32_t reserved;
+} sj_serve_info;
+
+SJ_API sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out);
 
 /* Per-request timestamps (seconds since the context was created) of a
  * finished result: submitted, admitted, completed.  Zero for results not

@@ -133,39 +133,10 @@ PinnedCache &pinned_cache() {
 
 }  // namespace
 
+void *pinned_get(size_t bytes, size_t *got) { return pinned_cache().get(bytes, got); }
+void pinned_put(void *p, size_t bytes) { pinned_cache().put(p, bytes); }
+
 }  // namespace sj
-
-// ---------------------------------------------------------------- opaque types
-
-struct sj_result {
-    uint32_t *pairs = nullptr;
-    uint64_t count = 0;
-    size_t bytes = 0;     // capacity of the pinned buffer
-    double t_submit = 0, t_admit = 0, t_done = 0;
-};
-
-struct sj_index {
-    sj::Index ix;
-    int device = 0;
-};
-
-struct sj_ctx {
-    sj_config cfg;
-    int device = 0;
-    cudaStream_t s_main = nullptr, s_copy = nullptr;
-    sj::DevBuf misc;                         // counters: see kMisc* below
-    unsigned long long *h_misc = nullptr;    // pinned read-back
-    std::string last_err;
-    sj_stats stats;
-    double t0 = 0;
-    // profiling
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
-    size_t prof_used = 0;
-    double prof_ms = 0;
-    uint64_t prof_launches = 0;
-    // serving (see serve.cu)
-    void *serve = nullptr;
-};
 
 namespace sj {
 
@@ -490,6 +461,8 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     return SJ_OK;
 }
 
+}  // namespace
+
 // Sorts the pairs of a host result ascending by (i << 32) | j on all cores.
 void sort_result(sj_result *r) {
     uint64_t *k = reinterpret_cast<uint64_t *>(r->pairs);
@@ -517,6 +490,8 @@ void sort_result(sj_result *r) {
     }
     for (uint64_t i = 0; i < n; ++i) k[i] = swap_halves(k[i]);
 }
+
+namespace {
 
 sj_status host_join(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     if (!(ctx->cfg.prec == SJ_PREC_FP32_RECHECK && ix.g.fp32_ok))

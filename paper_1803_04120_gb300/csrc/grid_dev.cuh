@@ -1,0 +1,157 @@
+// grid_dev.cuh -- device helpers of the grid index (Section IV-B) shared by
+// the single-join build (index.cu) and the batched multi-join build
+// (engine.cu).
+#pragma once
+
+#include <cstring>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+
+// Order-preserving map of a double onto an unsigned integer, so that min and
+// max reduce with integer atomics.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__host__ __device__ inline double from_order_key(unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & 0x7fffffffffffffffULL) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    std::memcpy(&x, &b, sizeof(x));
+    return x;
+#endif
+}
+
+// What the cell-id kernels need of the geometry.
+struct CellParams {
+    int d;
+    double gmin[kMaxDim];
+    double inv_w;
+    int64_t ng[kMaxDim];
+    uint64_t stride[kMaxDim];
+};
+
+inline CellParams cell_params(const Geometry &g) {
+    CellParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.d = g.d;
+    cp.inv_w = 1.0 / g.w;
+    for (int j = 0; j < g.d; ++j) {
+        cp.gmin[j] = g.gmin[j];
+        cp.ng[j] = g.ng[j];
+        cp.stride[j] = g.stride[j];
+    }
+    return cp;
+}
+
+// Linear cell id of point p: c_j = floor((x_j - g_min_j) * (1 / w)) in FP64,
+// clamped to the grid, id = sum_j c_j * stride_j (dimension 1 fastest).
+__device__ __forceinline__ uint64_t linear_cell(const double *p, const CellParams &cp) {
+    uint64_t id = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < cp.d) {
+            double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
+            int64_t c = (int64_t)floor(q);
+            c = c < 0 ? 0 : c;
+            c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+            id += (uint64_t)c * cp.stride[j];
+        }
+    }
+    return id;
+}
+
+// Accumulates per-dimension min / max (order keys) of points i0, i0 + step,
+// ... below n into minmax[2j], minmax[2j + 1] and sets bit 0 of *flag when a
+// coordinate is NaN or infinite.  Called by every thread of full warps.
+__device__ __forceinline__ void bounds_accumulate(const double *__restrict__ pts, uint64_t n, int d,
+                                                  uint64_t i0, uint64_t step,
+                                                  unsigned long long *minmax, uint32_t *flag) {
+    unsigned long long lo[kMaxDim], hi[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) { lo[j] = ~0ULL; hi[j] = 0ULL; }
+    bool bad = false;
+    for (uint64_t i = i0; i < n; i += step) {
+#pragma unroll
+        for (int j = 0; j < kMaxDim; ++j) {
+            if (j < d) {
+                const double x = pts[i * d + j];
+                const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+                bad |= (b & 0x7ff0000000000000ULL) == 0x7ff0000000000000ULL;
+                const unsigned long long k = order_key(x);
+                lo[j] = k < lo[j] ? k : lo[j];
+                hi[j] = k > hi[j] ? k : hi[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < d) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[j], o);
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi[j], o);
+                lo[j] = a < lo[j] ? a : lo[j];
+                hi[j] = b > hi[j] ? b : hi[j];
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&minmax[2 * j], lo[j]);
+                atomicMax(&minmax[2 * j + 1], hi[j]);
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// Cell coordinates of the non-empty cell h with linear id `id`, and its bits
+// in the occupancy bitmaps M_j (when M is given).
+__device__ __forceinline__ void cell_coords(uint64_t id, uint64_t h, const CellParams &cp,
+                                            uint32_t mwords, int32_t *__restrict__ cc,
+                                            uint32_t *__restrict__ M) {
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < cp.d) {
+            const uint64_t c = (id / cp.stride[j]) % (uint64_t)cp.ng[j];
+            cc[h * cp.d + j] = (int32_t)c;
+            if (M) {
+                uint32_t *w = &M[(uint64_t)j * mwords + (c >> 5)];
+                const uint32_t bit = 1u << (c & 31);
+                if ((*(volatile uint32_t *)w & bit) == 0) atomicOr(w, bit);
+            }
+        }
+    }
+}
+
+// FP32 record of the point at cell-order position k: y_j = fl32(x_j - g_min_j)
+// for j < d, then the point id, zero padding up to rs floats.
+__device__ __forceinline__ void write_rec32(const double *__restrict__ pts,
+                                            const uint32_t *__restrict__ A, uint64_t k,
+                                            const CellParams &cp, int rs, float *__restrict__ rec) {
+    const uint32_t i = A[k];
+    const double *p = pts + (uint64_t)i * cp.d;
+    float *r = rec + k * rs;
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j)
+        if (j < cp.d) r[j] = __double2float_rn(__dsub_rn(p[j], cp.gmin[j]));
+    r[cp.d] = __uint_as_float(i);
+    for (int j = cp.d + 1; j < rs; ++j) r[j] = 0.0f;
+}
+
+// FP64 record: x_0 .. x_{d-1}, the point id, zero padding up to rs doubles.
+__device__ __forceinline__ void write_rec64(const double *__restrict__ pts,
+                                            const uint32_t *__restrict__ A, uint64_t k, int d,
+                                            int rs, double *__restrict__ rec) {
+    const uint32_t i = A[k];
+    const double *p = pts + (uint64_t)i * d;
+    double *r = rec + k * rs;
+    for (int j = 0; j < d; ++j) r[j] = p[j];
+    r[d] = __longlong_as_double((long long)i);
+    for (int j = d + 1; j < rs; ++j) r[j] = 0.0;
+}
+
+}  // namespace sj

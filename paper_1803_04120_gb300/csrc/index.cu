@@ -23,7 +23,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "sj_internal.cuh"
+#include "grid_dev.cuh"
 
 namespace sj {
 
@@ -31,92 +31,20 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ unsigned long long order_key(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
-}
-
-__host__ __device__ inline double from_order_key(unsigned long long k) {
-    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & 0x7fffffffffffffffULL) : ~k;
-#ifdef __CUDA_ARCH__
-    return __longlong_as_double((long long)b);
-#else
-    double x;
-    std::memcpy(&x, &b, sizeof(x));
-    return x;
-#endif
-}
-
 // minmax[2j] = min over points of x_j (order key), minmax[2j+1] = max.
 // flag[0] |= 1 when a coordinate is NaN or infinite.
 __global__ void __launch_bounds__(kThreads) bounds_kernel(const double *__restrict__ pts,
                                                           uint64_t n, int d,
                                                           unsigned long long *minmax,
                                                           uint32_t *flag) {
-    unsigned long long lo[kMaxDim], hi[kMaxDim];
-#pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) { lo[j] = ~0ULL; hi[j] = 0ULL; }
-    bool bad = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int j = 0; j < kMaxDim; ++j) {
-            if (j < d) {
-                double x = pts[i * d + j];
-                unsigned long long b = (unsigned long long)__double_as_longlong(x);
-                bad |= (b & 0x7ff0000000000000ULL) == 0x7ff0000000000000ULL;
-                unsigned long long k = order_key(x);
-                lo[j] = k < lo[j] ? k : lo[j];
-                hi[j] = k > hi[j] ? k : hi[j];
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) {
-        if (j < d) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[j], o);
-                unsigned long long b = __shfl_xor_sync(0xffffffffu, hi[j], o);
-                lo[j] = a < lo[j] ? a : lo[j];
-                hi[j] = b > hi[j] ? b : hi[j];
-            }
-            if ((threadIdx.x & 31) == 0) {
-                atomicMin(&minmax[2 * j], lo[j]);
-                atomicMax(&minmax[2 * j + 1], hi[j]);
-            }
-        }
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+    bounds_accumulate(pts, n, d, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (uint64_t)gridDim.x * blockDim.x, minmax, flag);
 }
 
 __global__ void init_minmax_kernel(unsigned long long *minmax, int d, uint32_t *flag) {
     int j = threadIdx.x;
     if (j < d) { minmax[2 * j] = ~0ULL; minmax[2 * j + 1] = 0ULL; }
     if (j == 0) *flag = 0;
-}
-
-struct CellParams {
-    int d;
-    double gmin[kMaxDim];
-    double inv_w;
-    int64_t ng[kMaxDim];
-    uint64_t stride[kMaxDim];
-};
-
-__device__ __forceinline__ uint64_t linear_cell(const double *p, const CellParams &cp) {
-    uint64_t id = 0;
-#pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) {
-        if (j < cp.d) {
-            double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
-            int64_t c = (int64_t)floor(q);
-            c = c < 0 ? 0 : c;
-            c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
-            id += (uint64_t)c * cp.stride[j];
-        }
-    }
-    return id;
 }
 
 // Linear cell id of each point; with a dense count table also the point's
@@ -181,19 +109,7 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(const uint64_t *__restr
                                                          uint32_t *__restrict__ M) {
     uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= *n_cells) return;
-    uint64_t id = B[h];
-#pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) {
-        if (j < cp.d) {
-            uint64_t c = (id / cp.stride[j]) % (uint64_t)cp.ng[j];
-            cc[h * cp.d + j] = (int32_t)c;
-            if (M) {
-                uint32_t *w = &M[(uint64_t)j * mwords + (c >> 5)];
-                uint32_t bit = 1u << (c & 31);
-                if ((*(volatile uint32_t *)w & bit) == 0) atomicOr(w, bit);
-            }
-        }
-    }
+    cell_coords(B[h], h, cp, mwords, cc, M);
 }
 
 // FP32 record: y_j = fl32(x_j - g_min_j) for j < d, then the point id.
@@ -203,14 +119,7 @@ __global__ void __launch_bounds__(kThreads) rec32_kernel(const double *__restric
                                                          float *__restrict__ rec) {
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    uint32_t i = A[k];
-    const double *p = pts + (uint64_t)i * cp.d;
-    float *r = rec + k * rs;
-#pragma unroll
-    for (int j = 0; j < kMaxDim; ++j)
-        if (j < cp.d) r[j] = __double2float_rn(__dsub_rn(p[j], cp.gmin[j]));
-    r[cp.d] = __uint_as_float(i);
-    for (int j = cp.d + 1; j < rs; ++j) r[j] = 0.0f;
+    write_rec32(pts, A, k, cp, rs, rec);
 }
 
 __global__ void __launch_bounds__(kThreads) rec64_kernel(const double *__restrict__ pts,
@@ -218,12 +127,7 @@ __global__ void __launch_bounds__(kThreads) rec64_kernel(const double *__restric
                                                          int d, int rs, double *__restrict__ rec) {
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    uint32_t i = A[k];
-    const double *p = pts + (uint64_t)i * d;
-    double *r = rec + k * rs;
-    for (int j = 0; j < d; ++j) r[j] = p[j];
-    r[d] = __longlong_as_double((long long)i);
-    for (int j = d + 1; j < rs; ++j) r[j] = 0.0;
+    write_rec64(pts, A, k, d, rs, rec);
 }
 
 __global__ void __launch_bounds__(kThreads) item_count_kernel(const uint32_t *__restrict__ G,
@@ -250,6 +154,37 @@ __global__ void __launch_bounds__(kThreads) item_fill_kernel(const uint32_t *__r
 inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
+
+// Geometry of Section IV-B from the per-dimension bounds (order keys,
+// mm[2j] = min, mm[2j+1] = max): g_min = min - eps, g_max = max + eps, cell
+// side w = eps (1 + 2^-16), |g_j| = floor((g_max_j - g_min_j) / w) + 1,
+// strides with dimension 1 fastest, and the FP32 margin.
+sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, uint64_t n,
+                               double eps, Geometry &g) {
+    g = Geometry();
+    g.d = d;
+    g.n = n;
+    g.eps = eps;
+    g.E2 = eps * eps;
+    g.w = eps * (1.0 + std::ldexp(1.0, -16));
+    double total = 1.0;
+    uint64_t stride = 1;
+    for (int j = 0; j < d; ++j) {
+        const double mn = from_order_key(mm[2 * j]), mx = from_order_key(mm[2 * j + 1]);
+        g.gmin[j] = mn - eps;
+        g.gmax[j] = mx + eps;
+        const double cells = std::floor((g.gmax[j] - g.gmin[j]) / g.w) + 1.0;
+        if (!(cells < 2147483648.0)) return fail(err, SJ_ERANGE, "a dimension needs 2^31 or more cells");
+        g.ng[j] = (int64_t)cells;
+        total *= cells;
+        if (!(total < 9.2e18)) return fail(err, SJ_ERANGE, "grid has 2^63 or more cells");
+        g.stride[j] = stride;
+        stride *= (uint64_t)g.ng[j];
+    }
+    g.grid_cells = stride;
+    fp32_margin(g);  // margin.cu
+    return SJ_OK;
+}
 
 void free_index(Index &ix, cudaStream_t s) {
     DevBuf *all[] = {&ix.pts, &ix.rec32, &ix.rec64, &ix.A, &ix.B, &ix.G,
@@ -302,25 +237,10 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     if (h_counts[0] & 1u) { dev_free(scratch, s); return fail(err, SJ_EINVAL, "non-finite coordinate"); }
 
     // geometry (Section IV-B)
-    double total = 1.0;
-    uint64_t stride = 1;
-    for (int j = 0; j < d; ++j) {
-        double mn = from_order_key(h_mm[2 * j]), mx = from_order_key(h_mm[2 * j + 1]);
-        g.gmin[j] = mn - eps;
-        g.gmax[j] = mx + eps;
-        double cells = std::floor((g.gmax[j] - g.gmin[j]) / g.w) + 1.0;
-        if (!(cells < 2147483648.0)) {
-            dev_free(scratch, s);
-            return fail(err, SJ_ERANGE, "a dimension needs 2^31 or more cells");
-        }
-        g.ng[j] = (int64_t)cells;
-        total *= cells;
-        if (!(total < 9.2e18)) { dev_free(scratch, s); return fail(err, SJ_ERANGE, "grid has 2^63 or more cells"); }
-        g.stride[j] = stride;
-        stride *= (uint64_t)g.ng[j];
+    {
+        const sj_status gst = geometry_from_bounds(err, h_mm, d, n, eps, g);
+        if (gst != SJ_OK) { dev_free(scratch, s); return gst; }
     }
-    g.grid_cells = stride;
-    fp32_margin(g);  // margin.cu
 
     // 2-3. cell ids and the sort by cell
     uint64_t dense_limit = (uint64_t)16 * n;

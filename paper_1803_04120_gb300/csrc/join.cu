@@ -39,6 +39,7 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "sj_internal.cuh"
@@ -63,6 +64,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -728,16 +733,18 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
 
 // ---------------------------------------------------------------- the kernel
 
+// One join's pipelined loop for this warp: takes work items of the join
+// until none is left, then flushes its staged pairs and adds its counters.
+// The warp's mbarriers are initialised on entry and invalidated on a normal
+// exit, so a warp can run several joins one after another in the same
+// shared-memory area.  Returns false when a bounded wait expired.
 template <int D, bool F32, bool UNI>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1) join_kernel(const JoinArgs a,
-                                                                     const uint32_t *counts) {
+__device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *counts,
+                                          unsigned char *smem, int warp, int lane) {
     constexpr int CPL = cpl_for(D, F32);
     constexpr int CB = 32 * CPL;
     constexpr int kNBuf = nbuf_for(D, F32);
     typedef typename std::conditional<F32, float, double>::type T;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     const WarpSmem ws = carve(smem, a, warp, kNBuf);
     const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
@@ -818,6 +825,52 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 1) join_kernel(const Join
     if (lane == 0) {
         if (evals) atomicAdd(&a.counter[1], evals);
         if (rechecks) atomicAdd(&a.counter[2], rechecks);
+        // every copy issued has been waited for: the barriers are idle
+        if (!failed)
+            for (int i = 0; i < kNBuf; ++i) mbar_inval(&ws.bar[i]);
+    }
+    __syncwarp();
+    return !failed;
+}
+
+template <int D, bool F32, bool UNI>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1) join_kernel(const JoinArgs a,
+                                                                     const uint32_t *counts) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    (void)join_body<D, F32, UNI>(a, counts, smem, threadIdx.x >> 5, threadIdx.x & 31);
+}
+
+// Many joins in one persistent launch: every warp takes part in the joins in
+// the order given, moving on to the next join as soon as the current one
+// has no work item left for it (no barrier between joins, so the tail of one
+// join overlaps the start of the next).  Each join has its own work cursor,
+// counters, output and error word; its dimension and precision select the
+// specialised loop.  The job table lives in the kernel parameters (constant
+// bank), read with warp-uniform indices.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1)
+    multi_join_kernel(const __grid_constant__ MultiJobs m) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    for (uint32_t j = 0; j < m.n; ++j) {
+        const JoinArgs &a = m.job[j];
+        bool ok = true;
+        switch (a.d * 2 + (a.f32 ? 1 : 0)) {
+#define SJ_MJ_CASE(DD)                                                                  \
+    case 2 * DD: ok = join_body<DD, false, true>(a, a.dcounts, smem, warp, lane); break; \
+    case 2 * DD + 1: ok = join_body<DD, true, true>(a, a.dcounts, smem, warp, lane); break;
+            SJ_MJ_CASE(1)
+            SJ_MJ_CASE(2)
+            SJ_MJ_CASE(3)
+            SJ_MJ_CASE(4)
+            SJ_MJ_CASE(5)
+            SJ_MJ_CASE(6)
+            SJ_MJ_CASE(7)
+            SJ_MJ_CASE(8)
+#undef SJ_MJ_CASE
+            default: break;
+        }
+        if (!ok) return;
     }
 }
 
@@ -853,16 +906,54 @@ int n_templates(int d, bool uni) {
     return uni ? p + 2 : p;
 }
 
-sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
-                      uint32_t item_end, uint2 *out, uint64_t cap,
-                      unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
-                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+// Warps per block of a join launch: the block size (8, 4, 2 or 1 warps)
+// that keeps the most warps resident per SM under the shared-memory and
+// register limits, or force_wpb when given and it fits.
+sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb_out,
+                      int *per_sm_out) {
+    int smem_optin = 0;
+    SJ_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    {
+        // the limit is only ever raised, so that a launch prepared by another
+        // thread never finds it lowered under its shared-memory size
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lk(mu);
+        cudaFuncAttributes fa;
+        SJ_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+        const int want = std::min(smem_optin, sm_warp * kWarpsPerBlock);
+        if (fa.maxDynamicSharedSizeBytes < want)
+            SJ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, want));
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        int wpb = 0, per_sm = 0, best = 0;
+        for (int w = kWarpsPerBlock; w >= 1; w /= 2) {
+            if (pass == 0 && force_wpb > 0 && w != force_wpb) continue;
+            if ((size_t)sm_warp * w > (size_t)smem_optin) continue;
+            int b = 0;
+            SJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, w * 32, (size_t)sm_warp * w));
+            if (b * w > best) { best = b * w; wpb = w; per_sm = b; }
+        }
+        if (best > 0) {
+            *wpb_out = wpb;
+            *per_sm_out = per_sm;
+            return SJ_OK;
+        }
+        if (force_wpb <= 0) break;
+    }
+    return fail(err, SJ_EINVAL, "join kernel does not fit on an SM");
+}
+
+const void *multi_join_fn() { return reinterpret_cast<const void *>(multi_join_kernel); }
+
+sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
+                         uint32_t item_end, uint2 *out, uint64_t cap,
+                         unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
+                         int count_only, JoinArgs &a) {
     const Geometry &g = ix.g;
     const int d = g.d;
     const bool f32 = cfg.prec_fp32 && g.fp32_ok;
     const bool uni = cfg.unicomp != 0;
     if (!f32 && !ix.rec64.p) return fail(err, SJ_EINVAL, "FP64 records missing");
-    JoinArgs a;
     memset(&a, 0, sizeof(a));
     a.rec32 = static_cast<const float *>(ix.rec32.p);
     a.rec64 = static_cast<const double *>(ix.rec64.p);
@@ -909,28 +1000,30 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     a.sm_warp = 64 + round16(2 * (int)sizeof(ItemHdr)) + 2 * a.sm_ranges + 2 * a.sm_queries +
                 nbuf_for(d, f32) * a.sm_chunk + a.sm_emit;
     a.timeout_ns = 2000000000ull;
+    a.d = d;
+    a.f32 = f32 ? 1 : 0;
+    a.dcounts = n_items_dev(ix) - 1;
+    return SJ_OK;
+}
+
+sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
+                      uint32_t item_end, uint2 *out, uint64_t cap,
+                      unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
+                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+    JoinArgs a;
+    SJ_TRY(fill_join_args(err, ix, cfg, item_begin, item_end, out, cap, d_counter, d_work, d_error,
+                          count_only, a));
+    const int d = a.d;
+    const bool f32 = a.f32 != 0;
+    const bool uni = cfg.unicomp != 0;
 
     KernelFn fn = pick_kernel(d, f32, uni);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
     int dev = 0;
     SJ_CUDA_TRY(cudaGetDevice(&dev));
-    int smem_optin = 0, smem_sm = 0;
-    SJ_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    SJ_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    // warps per block: the block size (8, 4, 2 or 1 warps) that keeps the most
-    // warps resident per SM under the shared-memory and register limits
-    SJ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     std::min(smem_optin, (int)a.sm_warp * kWarpsPerBlock)));
-    int wpb = 0, per_sm = 0, best = 0;
-    for (int w = kWarpsPerBlock; w >= 1; w /= 2) {
-        if ((size_t)a.sm_warp * w > (size_t)smem_optin) continue;
-        int b = 0;
-        SJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, w * 32, (size_t)a.sm_warp * w));
-        if (b * w > best) { best = b * w; wpb = w; per_sm = b; }
-    }
-    if (best < 1) return fail(err, SJ_EINVAL, "join kernel does not fit on an SM");
+    int wpb = 0, per_sm = 0;
+    SJ_TRY(block_shape(err, reinterpret_cast<const void *>(fn), a.sm_warp, cfg.wpb, dev, &wpb, &per_sm));
     const size_t smem = (size_t)a.sm_warp * wpb;
-    (void)smem_sm;
     int blocks = cfg.blocks > 0 ? cfg.blocks : per_sm * sm_count(dev);
     if (item_end <= item_begin) blocks = 1;
     SJ_CUDA_TRY(cudaMemsetAsync(d_work, 0, sizeof(uint32_t), s));

@@ -155,6 +155,11 @@ struct JoinArgs {
     int cb;                         // candidates per chunk
     int eb;                         // emission staging entries
     uint64_t timeout_ns;
+    // multi-join launches: the dimension and precision of this job and its
+    // device counters (|G|, work items) in place of the kernel argument
+    int d;
+    int f32;
+    const uint32_t *dcounts;
 };
 
 struct JoinLaunch {
@@ -163,7 +168,29 @@ struct JoinLaunch {
     int blocks = 0;                 // 0: derive from occupancy
     int grab = 0;
     uint32_t item_stride = 1;
+    int wpb = 0;                    // warps per block; 0: occupancy picks
 };
+
+// Job table of a multi-join launch, passed in the kernel parameters.
+constexpr int kMultiJobs = 64;
+struct MultiJobs {
+    uint32_t n;
+    uint32_t pad;
+    JoinArgs job[kMultiJobs];
+};
+static_assert(sizeof(MultiJobs) <= 32000, "multi-join table exceeds the kernel parameter limit");
+
+sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
+                         uint32_t item_end, uint2 *out, uint64_t cap,
+                         unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
+                         int count_only, JoinArgs &a);
+sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb,
+                      int *per_sm);
+// The multi-join kernel (join.cu): void(const MultiJobs).
+const void *multi_join_fn();
+// Geometry of Section IV-B from per-dimension bounds (index.cu).
+sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, uint64_t n,
+                               double eps, Geometry &g);
 int n_templates(int d, bool uni);
 
 sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
@@ -192,4 +219,47 @@ void note_launch();
 uint64_t launches_so_far();
 int sm_count(int device);
 
+// Pinned host memory shared by all contexts (api.cu).
+void *pinned_get(size_t bytes, size_t *got);
+void pinned_put(void *p, size_t bytes);
+
+}  // namespace sj
+
+// ---------------------------------------------------------------- opaque types
+
+struct sj_result {
+    uint32_t *pairs = nullptr;
+    uint64_t count = 0;
+    size_t bytes = 0;     // capacity of the pinned buffer
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+struct sj_index {
+    sj::Index ix;
+    int device = 0;
+};
+
+struct sj_ctx {
+    sj_config cfg;
+    int device = 0;
+    cudaStream_t s_main = nullptr, s_copy = nullptr;
+    sj::DevBuf misc;                         // join counters, work cursor, error word
+    unsigned long long *h_misc = nullptr;    // pinned read-back
+    std::string last_err;
+    sj_stats stats;
+    double t0 = 0;
+    // profiling
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
+    size_t prof_used = 0;
+    double prof_ms = 0;
+    uint64_t prof_launches = 0;
+    // serving scheduler (serve.cu) and the multi-join engine of
+    // sj_selfjoin_multi (engine.cu)
+    void *serve = nullptr;
+    void *engine = nullptr;
+};
+
+namespace sj {
+// Sorts a host result ascending by (i << 32) | j (api.cu).
+void sort_result(sj_result *r);
 }  // namespace sj

@@ -32,7 +32,8 @@ ABI_FUNCTIONS = (
     "sj_selfjoin", "sj_selfjoin_index", "sj_selfjoin_device", "sj_selfjoin_index_device",
     "sj_selfjoin_count", "sj_selfjoin_stream", "sj_result_count", "sj_result_pairs",
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
-    "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc",
+    "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
+    "sj_serve_stats",
 )
 
 
@@ -67,6 +68,21 @@ class sj_stats(ctypes.Structure):
                 ("estimate", ctypes.c_uint64), ("ms_index", ctypes.c_double),
                 ("ms_join", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64)]
+
+
+class sj_job(ctypes.Structure):
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_uint64), ("d", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("eps", ctypes.c_double)]
+
+
+class sj_serve_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("waves", ctypes.c_uint64), ("max_wave", ctypes.c_uint64),
+                ("overflow_reruns", ctypes.c_uint64), ("standalone", ctypes.c_uint64),
+                ("graph_launches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("mem_in_use", ctypes.c_uint64), ("inflight", ctypes.c_int32),
+                ("lanes", ctypes.c_int32), ("max_concurrent_waves", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
@@ -124,6 +140,8 @@ def load(build: bool = True):
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
             "sj_selfjoin_noalloc": (i32, [P, u64, i32, f64, P, u64, ctypes.POINTER(ctypes.c_uint64),
                                           P, ctypes.c_char_p, ctypes.c_size_t]),
+            "sj_selfjoin_multi": (i32, [P, ctypes.POINTER(sj_job), u64, PP, ctypes.POINTER(ctypes.c_int)]),
+            "sj_serve_stats": (i32, [P, ctypes.POINTER(sj_serve_info)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -326,6 +344,37 @@ class Context:
             return _result_to_numpy(self._lib, r), tuple(x.value for x in ts)
         finally:
             self._lib.sj_result_free(r)
+
+    def sj_selfjoin_multi(self, jobs, raise_errors: bool = True):
+        """Joins [(points, eps), ...] together; returns a list with one
+        (count, 2) uint32 pair array per job (None for a failed job when
+        raise_errors is False)."""
+        keep = []
+        arr = (sj_job * max(1, len(jobs)))()
+        for k, (pts, eps) in enumerate(jobs):
+            p, n, d, kp = _points_ptr(pts)
+            keep.append(kp)
+            arr[k].pts, arr[k].n, arr[k].d, arr[k].eps = p, n, d, float(eps)
+        outs = (ctypes.c_void_p * max(1, len(jobs)))()
+        stat = (ctypes.c_int * max(1, len(jobs)))()
+        st = self._lib.sj_selfjoin_multi(self._h, arr, len(jobs), outs, stat)
+        res = []
+        try:
+            for k in range(len(jobs)):
+                res.append(_result_to_numpy(self._lib, ctypes.c_void_p(outs[k])) if outs[k] else None)
+        finally:
+            for k in range(len(jobs)):
+                if outs[k]:
+                    self._lib.sj_result_free(ctypes.c_void_p(outs[k]))
+        if raise_errors:
+            self._check(st, "sj_selfjoin_multi")
+        self.last_multi_status = [int(stat[k]) for k in range(len(jobs))]
+        return res
+
+    def sj_serve_stats(self) -> dict:
+        s = sj_serve_info()
+        self._check(self._lib.sj_serve_stats(self._h, ctypes.byref(s)), "sj_serve_stats")
+        return {k: getattr(s, k) for k, _ in sj_serve_info._fields_ if k != "reserved"}
 
     # -- diagnostics
     def sj_last_stats(self) -> dict:
