@@ -16,6 +16,13 @@ Printed JSON line (rank 0):
   roofline     the search-and-refine kernel of the dominant launch against
                max(FLOPs / FP32 peak, bytes / HBM bandwidth)
   cpu_baseline the CPU oracle on the host cores, on a bounded sample
+  skew         clustered 5,000,000 points (d = 2, 3, eps = 0.5): device join
+               with the tuned launch parameters against the fixed defaults
+  serving      a stream of join requests (n log-uniform in [1e3, 1e6],
+               d in 2..6, 8..128 mean neighbours) through sj_submit/sj_poll,
+               all at once (saturated) and with Poisson arrivals at half the
+               saturated rate: p50/p99 latency and pairs/s, against the same
+               requests joined one at a time through sj_selfjoin
 --impl reference times the CPU oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -147,6 +154,141 @@ def cpu_oracle_sample(data, budget_s: float):
     return tot_pairs / tot_time, cores, "; ".join(desc) + " (grid build included)"
 
 
+# ---------------------------------------------------------------- skew
+
+def skew_bench(dev: int, reps: int):
+    """Clustered 5,000,000-point workload (d = 2, 3, eps = 0.5), pairs in
+    device memory: tuned launch parameters against the fixed defaults."""
+    import torch
+    from paper_1803_04120_gb300 import sj
+
+    stream = torch.cuda.Stream()
+    out = []
+    for d in (2, 3):
+        cfg = datagen.config4(d)
+        pts = torch.from_numpy(datagen.make_points(cfg)).cuda()
+        c0 = sj.Context(autotune=False, profile=True, device=dev)
+        c1 = sj.Context(autotune=True, profile=True, device=dev)
+        cnt = c0.sj_selfjoin_count(pts, cfg["eps"])
+        buf = torch.empty((cnt, 2), dtype=torch.int32, device="cuda")
+        res = {}
+        for name, c in (("default", c0), ("tuned", c1)):
+            c.sj_selfjoin_device(pts, cfg["eps"], buf, stream=stream)   # warm-up (tunes c1)
+            torch.cuda.synchronize()
+            c.sj_profile_read()
+            ts = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                n = c.sj_selfjoin_device(pts, cfg["eps"], buf, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                assert n == cnt
+                ts.append(e0.elapsed_time(e1))
+            kms, nl = c.sj_profile_read()
+            st = c.sj_last_stats()
+            res[name] = dict(ms=round(statistics.mean(ts), 3), kernel_ms=round(kms / max(nl, 1), 3),
+                             grab=st["grab"], nbuf=st["nbuf"], wpb=st["wpb"], tuned=st["tuned"])
+        out.append(dict(d=d, n=cfg["n"], eps=cfg["eps"], pairs=cnt,
+                        default=res["default"], tuned=res["tuned"],
+                        pairs_per_s_tuned=round(cnt / (res["tuned"]["ms"] / 1e3), 1),
+                        speedup=round(res["default"]["ms"] / res["tuned"]["ms"], 3)))
+        del buf, pts
+        c0.close()
+        c1.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------- serving
+
+def _pct(v, q):
+    return round(float(np.percentile(np.asarray(v) * 1e3, q)), 3)
+
+
+def serving_bench(dev: int, n_req: int, seed: int = 5):
+    """The request stream through the serving loop, saturated and Poisson,
+    against one-at-a-time joins of the same requests."""
+    import threading
+    from paper_1803_04120_gb300 import sj
+
+    reqs = datagen.serving_requests(n_req, seed, rate_hz=1.0)
+    pts = [datagen.uniform(r["n"], r["d"], r["seed"]) for r in reqs]
+
+    def one_at_a_time(prec):
+        with sj.Context(prec=prec, device=dev) as c:
+            r = c.sj_selfjoin_raw(pts[0], reqs[0]["eps"])
+            c.sj_result_free(r)
+            lat, tot = [], 0
+            t0 = time.perf_counter()
+            for p, q in zip(pts, reqs):
+                t = time.perf_counter()
+                r = c.sj_selfjoin_raw(p, q["eps"])
+                tot += c.sj_result_count(r)
+                c.sj_result_free(r)
+                lat.append(time.perf_counter() - t)
+            return tot, time.perf_counter() - t0, lat
+
+    tot64, wall64, lat64 = one_at_a_time(sj.SJ_PREC_FP64)
+    tot32, wall32, lat32 = one_at_a_time(sj.SJ_PREC_FP32_RECHECK)
+    assert tot64 == tot32
+    ctx = sj.Context(device=dev, max_inflight=64, serve_mem_bytes=64 << 30)
+    for k in range(min(8, n_req)):        # engines, graphs, pinned buffers
+        ctx.sj_poll(ctx.sj_submit(pts[k], reqs[k]["eps"]), wait_ms=60000, copy=False)
+
+    def run(arrivals):
+        n = len(arrivals)
+        tickets, got = [None] * n, [None] * n
+        ready = threading.Semaphore(0)
+
+        def poller():
+            for k in range(n):
+                ready.acquire()
+                while got[k] is None:
+                    got[k] = ctx.sj_poll(tickets[k], wait_ms=1000, copy=False)
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for k in range(n):
+            dt = arrivals[k] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[k] = ctx.sj_submit(pts[k], reqs[k]["eps"])
+            ready.release()
+        th.join()
+        lat = [td - ts for _, (ts, ta, td) in got]
+        wall = max(td for _, (ts, ta, td) in got) - min(ts for _, (ts, ta, td) in got)
+        return sum(c for c, _ in got), wall, lat
+
+    p_sat, wall_sat, lat_sat = run([0.0] * n_req)
+    assert p_sat == tot64
+    rate = 0.5 * n_req / wall_sat
+    arrivals = [r["arrival_s"] for r in datagen.serving_requests(n_req, seed, rate_hz=rate)]
+    p_poi, wall_poi, lat_poi = run(arrivals)
+    assert p_poi == tot64
+    info = ctx.sj_serve_stats()
+    ctx.close()
+    return {
+        "requests": n_req, "pairs": tot64,
+        "request_mix": "n log-uniform [1e3,1e6], d uniform {2..6}, eps for U[8,128] mean neighbours, "
+                       "uniform [0,100]^d (seeded)",
+        "saturated": {"pairs_per_s": round(p_sat / wall_sat, 1), "req_per_s": round(n_req / wall_sat, 1),
+                      "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99)},
+        "poisson": {"rate_hz": round(rate, 1), "pairs_per_s": round(p_poi / wall_poi, 1),
+                    "p50_ms": _pct(lat_poi, 50), "p99_ms": _pct(lat_poi, 99)},
+        "one_at_a_time_fp64": {"pairs_per_s": round(tot64 / wall64, 1), "p50_ms": _pct(lat64, 50),
+                               "p99_ms": _pct(lat64, 99)},
+        "one_at_a_time_fp32": {"pairs_per_s": round(tot32 / wall32, 1), "p50_ms": _pct(lat32, 50),
+                               "p99_ms": _pct(lat32, 99)},
+        "speedup_vs_plain_one_at_a_time": round((p_sat / wall_sat) / (tot64 / wall64), 2),
+        "waves": info["waves"], "max_wave": info["max_wave"],
+        "max_concurrent_waves": info["max_concurrent_waves"], "overflow_reruns": info["overflow_reruns"],
+        "standalone": info["standalone"],
+    }
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -272,13 +414,19 @@ def run_gpu(args):
         "roofline_all": roof_all,
         "clocks": clocks,
     }
+    for c in ctx32:
+        c.close()
+    ctx64.close()
+    del outs
+    torch.cuda.empty_cache()
+    if args.serve_requests > 0:
+        line["serving"] = serving_bench(dev, args.serve_requests)
+    if not args.no_skew:
+        line["skew"] = skew_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_cpu:
         v, cores, desc = cpu_oracle_sample(data, args.cpu_budget)
         line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc}
-    for c in ctx32:
-        c.close()
-    ctx64.close()
     return line
 
 
@@ -319,6 +467,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of the serving stream (0: skip)")
+    ap.add_argument("--no-skew", action="store_true", help="skip the clustered workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -330,6 +481,8 @@ def main():
     if world > 1:
         # replicas: each rank runs the same workload on its own GPU; the
         # whole-job value is the sum over ranks of pairs over the max time
+        # (the serving and clustered sections are single-GPU measurements)
+        args.serve_requests, args.no_skew = 0, True
         import torch
         import torch.distributed as dist
         dist.init_process_group("nccl")

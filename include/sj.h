@@ -101,7 +101,14 @@ typedef struct {
     int32_t min_batches;     /* minimum result batches for host results
                                 (Section V-A uses 3); default 3 */
     int32_t sorted;          /* 1: host results sorted by (i << 32) | j */
-    int32_t autotune;        /* 1 (default): launch parameters from the tuner */
+    int32_t autotune;        /* 1 (default): the search-and-refine launch
+                                parameters (grab, chunk ring depth, warps per
+                                block) come from the tuner, which times
+                                sampled count-only launches the first time a
+                                (d, precision, UNICOMP, points-per-cell
+                                bucket) key is met in the process and reuses
+                                the choice after; 0: fixed defaults.  Never
+                                changes the result. */
     int32_t device;          /* CUDA device ordinal; default 0 */
     int32_t lookup;          /* sj_lookup; default SJ_LOOKUP_AUTO */
     int32_t profile;         /* 1: time every join-kernel launch with CUDA
@@ -319,6 +326,11 @@ typedef struct {
     double ms_join;          /* host wall time of the join after the index */
     double ms_total;
     uint64_t kernel_launches;/* CUDA kernels the library launched for the call */
+    /* launch parameters of the search-and-refine kernel for the call */
+    int32_t grab;            /* work items per cursor bump */
+    int32_t nbuf;            /* candidate-chunk ring depth (0: by dimension) */
+    int32_t wpb;             /* warps per block (0: by occupancy) */
+    int32_t tuned;           /* 0 defaults, 1 from the tuner's cache, 2 tuned by this call */
 } sj_stats;
 
 SJ_API sj_status sj_last_stats(const sj_ctx *ctx, sj_stats *out);

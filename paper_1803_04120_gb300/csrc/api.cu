@@ -193,12 +193,32 @@ sj_status profile_events(Error &err, sj_ctx *ctx, cudaEvent_t *e0, cudaEvent_t *
     return SJ_OK;
 }
 
-JoinLaunch launch_cfg(const sj_ctx *ctx) {
+JoinLaunch default_launch(const sj_ctx *ctx) {
     JoinLaunch l;
     l.prec_fp32 = ctx->cfg.prec == SJ_PREC_FP32_RECHECK;
     l.unicomp = ctx->cfg.unicomp;
     l.grab = ctx->cfg.grab > 0 ? ctx->cfg.grab : 1;
     return l;
+}
+
+JoinLaunch launch_cfg(const sj_ctx *ctx) { return ctx->launch; }
+
+// Launch parameters of the join on ix: the defaults, or with autotune = 1
+// (and no grab forced in the configuration) the tuner's choice for the
+// index's key (one host read of |G| and the work-item count first).
+sj_status prepare_launch(Error &err, sj_ctx *ctx, Index &ix, cudaStream_t s) {
+    ctx->launch = default_launch(ctx);
+    ctx->launch_tuned = 0;
+    if (!ctx->cfg.autotune || ctx->cfg.grab > 0) return SJ_OK;
+    SJ_TRY(read_counts(err, ix, s));
+    return tune_launch(err, ix, ctx->launch, s, &ctx->launch_tuned);
+}
+
+void record_launch(sj_ctx *ctx) {
+    ctx->stats.grab = ctx->launch.grab;
+    ctx->stats.nbuf = ctx->launch.nbuf;
+    ctx->stats.wpb = ctx->launch.wpb;
+    ctx->stats.tuned = ctx->launch_tuned;
 }
 
 // Runs one join launch over items [ib, ie) into out (cap pairs) and reads
@@ -496,7 +516,9 @@ namespace {
 sj_status host_join(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     if (!(ctx->cfg.prec == SJ_PREC_FP32_RECHECK && ix.g.fp32_ok))
         SJ_TRY(ensure_rec64(err, ix, ctx->s_main));
+    SJ_TRY(prepare_launch(err, ctx, ix, ctx->s_main));
     SJ_TRY(run_batches(err, ctx, ix, sink));
+    record_launch(ctx);
     if (sink.res && ctx->cfg.sorted) sort_result(sink.res);
     return SJ_OK;
 }
@@ -562,6 +584,7 @@ sj_status sj_create(const sj_config *cfg, sj_ctx **out) {
     ctx->device = c.device;
     ctx->t0 = now_ms();
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->launch = sj::default_launch(ctx);
     Error err;
     // keep freed pool memory cached across calls
     cudaMemPool_t pool;
@@ -673,10 +696,12 @@ sj_status sj_index_export(const sj_index *ix, uint64_t *B, uint32_t *G, uint32_t
 static sj_status device_join_on(sj_ctx *ctx, Error &err, Index &ix, uint32_t *d_pairs,
                                 uint64_t cap, uint64_t *count, cudaStream_t s, int count_only) {
     if (!(ctx->cfg.prec == SJ_PREC_FP32_RECHECK && ix.g.fp32_ok)) SJ_TRY(ensure_rec64(err, ix, s));
+    SJ_TRY(prepare_launch(err, ctx, ix, s));
     unsigned long long r[3];
     SJ_TRY(join_once(err, ctx, ix, 0, 0xffffffffu, 1, reinterpret_cast<uint2 *>(d_pairs), cap,
                      count_only, s, r));
     *count = r[0];
+    record_launch(ctx);
     ctx->stats.pairs = r[0];
     ctx->stats.evaluations = r[1];
     ctx->stats.rechecks = r[2];

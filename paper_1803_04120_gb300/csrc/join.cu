@@ -743,15 +743,15 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                                           unsigned char *smem, int warp, int lane) {
     constexpr int CPL = cpl_for(D, F32);
     constexpr int CB = 32 * CPL;
-    constexpr int kNBuf = nbuf_for(D, F32);
+    const uint32_t nbuf = (uint32_t)a.nbuf;   // chunk ring depth (launch parameter)
     typedef typename std::conditional<F32, float, double>::type T;
-    const WarpSmem ws = carve(smem, a, warp, kNBuf);
+    const WarpSmem ws = carve(smem, a, warp, nbuf);
     const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
                                    : reinterpret_cast<const unsigned char *>(a.rec64);
 
     if (lane == 0)
-        for (int i = 0; i < kNBuf; ++i) mbar_init(&ws.bar[i], 1);
+        for (uint32_t i = 0; i < nbuf; ++i) mbar_init(&ws.bar[i], 1);
     fence_proxy_async_smem();
     __syncwarp();
 
@@ -776,9 +776,9 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     if (fetch_item(st, a, item_end, lane, it)) {
         prepare_item<D, F32, UNI>(ws, 0, it, a, n_cells, lane, evals);
         for (;;) {
-            // producer: keep up to kNBuf chunks in flight, crossing into the
+            // producer: keep up to nbuf chunks in flight, crossing into the
             // next item (at most one item ahead of the consumer)
-            while (st.issued - st.consumed < (uint32_t)kNBuf) {
+            while (st.issued - st.consumed < nbuf) {
                 const int ps = st.prod_seq & 1;
                 if (st.p_chunk == ws.hdr[ps].nchunks) {
                     // the other item slot is free once the consumer has
@@ -794,20 +794,20 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                     st.rcur = 0;
                     continue;
                 }
-                issue_chunk<CB>(ws, ps, st.p_chunk, st.issued % kNBuf, st.rcur, rec, rsb, lane,
+                issue_chunk<CB>(ws, ps, st.p_chunk, st.issued % nbuf, st.rcur, rec, rsb, lane,
                                 a.sm_chunk);
                 ++st.issued;
                 ++st.p_chunk;
             }
             if (st.consumed == st.issued) break;
             // consumer
-            const int r = st.consumed % kNBuf;
-            if (!mbar_wait_bounded(&ws.bar[r], (st.consumed / kNBuf) & 1u, a.timeout_ns)) {
+            const int r = st.consumed % nbuf;
+            if (!mbar_wait_bounded(&ws.bar[r], (st.consumed / nbuf) & 1u, a.timeout_ns)) {
                 failed = true;
                 if (lane == 0) atomicOr(a.error, kErrTimeout);
                 // let the other copies in flight land before leaving
                 for (uint32_t k = st.consumed + 1; k < st.issued; ++k)
-                    (void)mbar_wait_bounded(&ws.bar[k % kNBuf], (k / kNBuf) & 1u, a.timeout_ns);
+                    (void)mbar_wait_bounded(&ws.bar[k % nbuf], (k / nbuf) & 1u, a.timeout_ns);
                 break;
             }
             consume_chunk<D, F32, UNI>(st, ws, st.cons_seq & 1, st.c_chunk, r, a, lane, rechecks);
@@ -827,7 +827,7 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
         if (rechecks) atomicAdd(&a.counter[2], rechecks);
         // every copy issued has been waited for: the barriers are idle
         if (!failed)
-            for (int i = 0; i < kNBuf; ++i) mbar_inval(&ws.bar[i]);
+            for (uint32_t i = 0; i < nbuf; ++i) mbar_inval(&ws.bar[i]);
     }
     __syncwarp();
     return !failed;
@@ -997,8 +997,10 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.sm_chunk = round16(a.cb * rsb);
     a.eb = kEmit;
     a.sm_emit = round16(kEmit * (int)sizeof(uint2));
+    // ring depth: the launch's choice (2..8 chunks; the warp has 8 mbarriers)
+    a.nbuf = (cfg.nbuf >= 2 && cfg.nbuf <= 8) ? cfg.nbuf : nbuf_for(d, f32);
     a.sm_warp = 64 + round16(2 * (int)sizeof(ItemHdr)) + 2 * a.sm_ranges + 2 * a.sm_queries +
-                nbuf_for(d, f32) * a.sm_chunk + a.sm_emit;
+                a.nbuf * a.sm_chunk + a.sm_emit;
     a.timeout_ns = 2000000000ull;
     a.d = d;
     a.f32 = f32 ? 1 : 0;

@@ -154,6 +154,7 @@ struct JoinArgs {
     int sm_ranges, sm_queries, sm_chunk, sm_emit, sm_warp;
     int cb;                         // candidates per chunk
     int eb;                         // emission staging entries
+    int nbuf;                       // chunk ring depth (2..8)
     uint64_t timeout_ns;
     // multi-join launches: the dimension and precision of this job and its
     // device counters (|G|, work items) in place of the kernel argument
@@ -169,6 +170,7 @@ struct JoinLaunch {
     int grab = 0;
     uint32_t item_stride = 1;
     int wpb = 0;                    // warps per block; 0: occupancy picks
+    int nbuf = 0;                   // chunk ring depth; 0: by dimension and precision
 };
 
 // Job table of a multi-join launch, passed in the kernel parameters.
@@ -186,6 +188,14 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
                          int count_only, JoinArgs &a);
 sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb,
                       int *per_sm);
+// Launch tuner (tune.cu): on a miss times sampled count-only launches of ix
+// and stores the fastest (grab, ring depth, warps per block) for the key
+// (d, precision, UNICOMP, points-per-cell bucket); *tuned = 0 defaults kept,
+// 1 taken from the cache, 2 tuned now.  ix.n_items and ix.n_cells must be
+// known on the host.
+int tune_bucket(const Index &ix);
+sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned);
+void tune_clear();
 // The multi-join kernel (join.cu): void(const MultiJobs).
 const void *multi_join_fn();
 // Geometry of Section IV-B from per-dimension bounds (index.cu).
@@ -253,6 +263,9 @@ struct sj_ctx {
     size_t prof_used = 0;
     double prof_ms = 0;
     uint64_t prof_launches = 0;
+    // launch parameters of the current join (defaults or the tuner's)
+    sj::JoinLaunch launch;
+    int launch_tuned = 0;
     // serving scheduler (serve.cu) and the multi-join engine of
     // sj_selfjoin_multi (engine.cu)
     void *serve = nullptr;

@@ -1,0 +1,156 @@
+// tune.cu -- launch tuner of the search-and-refine kernel.
+//
+// Three launch parameters change the speed of the join but never its
+// result: grab (the work items a warp takes from the cursor at a time: how
+// many (cell, query block) items it owns before it returns for more), the
+// depth of the per-warp ring of staged candidate chunks, and the warps per
+// block (which trades shared memory per block against blocks per SM).  Their
+// best values depend on the dimension, the precision and how many points a
+// non-empty cell holds (few per cell: short candidate lists, latency-bound
+// copies; many per cell, as in clustered data: long lists, skew between
+// items).  The tuner keys its choices on (d, precision, UNICOMP, bucket)
+// with bucket = round(log2(mean points per non-empty cell)), and on a miss
+// times count-only launches of the join at hand over a fixed systematic
+// sample of its work items (the same items for every candidate), one
+// parameter after the other, keeping a change only when it is at least 3%
+// faster.  Choices are kept for the life of the process.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+
+namespace {
+
+struct TuneVal {
+    int grab = 1, nbuf = 0, wpb = 0;
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, TuneVal> g_tune;
+
+constexpr uint32_t kTuneMinItems = 4096;      // smaller joins keep the defaults
+constexpr uint32_t kTuneSampleItems = 24576;  // items per timed launch
+
+}  // namespace
+
+int tune_bucket(const Index &ix) {
+    const double per = ix.n_cells ? (double)ix.g.n / (double)ix.n_cells : 1.0;
+    return (int)std::lround(std::log2(std::max(1.0, per)));
+}
+
+sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned) {
+    *tuned = 0;
+    const bool f32 = l.prec_fp32 && ix.g.fp32_ok;
+    const auto key = std::make_tuple(ix.g.d, f32 ? 1 : 0, l.unicomp ? 1 : 0, tune_bucket(ix));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            l.grab = it->second.grab;
+            l.nbuf = it->second.nbuf;
+            l.wpb = it->second.wpb;
+            *tuned = 1;
+            return SJ_OK;
+        }
+    }
+    if (ix.n_items < kTuneMinItems) return SJ_OK;
+    DevBuf misc;
+    SJ_TRY(dev_alloc(err, misc, 64, s));
+    unsigned long long *m = static_cast<unsigned long long *>(misc.p);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sj_status st = SJ_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(err, SJ_ECUDA, "cudaEventCreate failed");
+    }
+    const uint32_t stride = std::max<uint32_t>(1, ix.n_items / kTuneSampleItems);
+    auto time_it = [&](const JoinLaunch &c, double *ms) -> sj_status {
+        JoinLaunch x = c;
+        x.item_stride = stride;
+        double best = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            SJ_CUDA_TRY(cudaMemsetAsync(m, 0, 64, s));
+            SJ_TRY(launch_join(err, ix, x, 0, ix.n_items, nullptr, 0, m,
+                               reinterpret_cast<uint32_t *>(m + 4), reinterpret_cast<uint32_t *>(m + 5),
+                               1, s, e0, e1));
+            SJ_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0;
+            SJ_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            best = std::min(best, (double)t);
+        }
+        unsigned long long h[8];
+        SJ_CUDA_TRY(cudaMemcpy(h, m, sizeof(h), cudaMemcpyDeviceToHost));
+        if ((uint32_t)h[5] & kErrTimeout) return fail(err, SJ_ETIMEOUT, "a bounded device wait expired while tuning");
+        *ms = best;
+        return SJ_OK;
+    };
+    JoinLaunch cur = l;
+    if (cur.grab <= 0) cur.grab = 1;
+    double t_cur = 0;
+    if (st == SJ_OK) st = time_it(cur, &t_cur);
+    const int grabs[] = {2, 4, 8, 16};
+    const int nbufs[] = {2, 3, 4, 6};
+    const int wpbs[] = {8, 4, 2};
+    for (int g : grabs) {
+        if (st != SJ_OK) break;
+        JoinLaunch c = cur;
+        c.grab = g;
+        double t = 0;
+        st = time_it(c, &t);
+        if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
+    }
+    for (int nb : nbufs) {
+        if (st != SJ_OK) break;
+        JoinLaunch c = cur;
+        c.nbuf = nb;
+        double t = 0;
+        st = time_it(c, &t);
+        if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
+    }
+    for (int w : wpbs) {
+        if (st != SJ_OK) break;
+        JoinLaunch c = cur;
+        c.wpb = w;
+        double t = 0;
+        st = time_it(c, &t);
+        if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(misc, s);
+    if (st != SJ_OK) return st;
+    TuneVal v;
+    v.grab = cur.grab;
+    v.nbuf = cur.nbuf;
+    v.wpb = cur.wpb;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = v;
+    }
+    l.grab = v.grab;
+    l.nbuf = v.nbuf;
+    l.wpb = v.wpb;
+    *tuned = 2;
+    return SJ_OK;
+}
+
+void tune_lookup(const Index &ix, JoinLaunch &l) {
+    const bool f32 = l.prec_fp32 && ix.g.fp32_ok;
+    const auto key = std::make_tuple(ix.g.d, f32 ? 1 : 0, l.unicomp ? 1 : 0, tune_bucket(ix));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return;
+    l.grab = it->second.grab;
+    l.nbuf = it->second.nbuf;
+}
+
+void tune_clear() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+}  // namespace sj

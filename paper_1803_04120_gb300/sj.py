@@ -67,7 +67,8 @@ class sj_stats(ctypes.Structure):
                 ("batches", ctypes.c_uint32), ("retries", ctypes.c_uint32),
                 ("estimate", ctypes.c_uint64), ("ms_index", ctypes.c_double),
                 ("ms_join", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64), ("grab", ctypes.c_int32),
+                ("nbuf", ctypes.c_int32), ("wpb", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
 
 class sj_job(ctypes.Structure):
@@ -331,8 +332,10 @@ class Context:
         self._check(self._lib.sj_submit(self._h, p, n, d, float(eps), ctypes.byref(t)), "sj_submit")
         return int(t.value)
 
-    def sj_poll(self, ticket: int, wait_ms: int = 0):
-        """None while pending, else (pairs array, (t_submit, t_admit, t_done))."""
+    def sj_poll(self, ticket: int, wait_ms: int = 0, copy: bool = True):
+        """None while pending, else (pairs, (t_submit, t_admit, t_done)) where
+        pairs is the (count, 2) uint32 array, or only the count when copy is
+        False."""
         r = ctypes.c_void_p()
         st = self._lib.sj_poll(self._h, ticket, int(wait_ms), ctypes.byref(r))
         if st == SJ_PENDING:
@@ -341,7 +344,8 @@ class Context:
         try:
             ts = [ctypes.c_double() for _ in range(3)]
             self._lib.sj_result_times(r, *[ctypes.byref(x) for x in ts])
-            return _result_to_numpy(self._lib, r), tuple(x.value for x in ts)
+            pairs = _result_to_numpy(self._lib, r) if copy else int(self._lib.sj_result_count(r))
+            return pairs, tuple(x.value for x in ts)
         finally:
             self._lib.sj_result_free(r)
 

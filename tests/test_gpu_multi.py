@@ -69,7 +69,7 @@ def test_multi_overflow_rerun_and_standalone():
     blob = np.concatenate([rng.normal(50.0, 0.3, size=(20000, 2)),
                            np.array([[0.0, 0.0], [100.0, 100.0]])])
     sparse = rng.uniform(0, 1e6, size=(3000, 8))
-    jobs = [(blob, 0.05), (sparse, 2e5), (datagen.uniform(5000, 2, seed=7), 1.0)]
+    jobs = [(blob, 0.05), (sparse, 1e5), (datagen.uniform(5000, 2, seed=7), 1.0)]
     with sj.Context() as ctx:
         res = ctx.sj_selfjoin_multi(jobs)
         st = ctx.sj_last_stats()
@@ -175,3 +175,18 @@ def test_serving_shutdown_with_pending_requests():
     for k in range(10):
         ctx.sj_submit(datagen.uniform(50000, 3, seed=20 + k), 2.0)
     ctx.close()   # cancels what is queued, waits for what runs
+
+
+def test_tuner_keeps_results():
+    pts = datagen.clustered(200000, 2, seed=3)
+    with sj.Context(autotune=False) as c0, sj.Context(autotune=True) as c1:
+        r1 = c1.sj_selfjoin(pts, 0.5)
+        s1 = c1.sj_last_stats()
+        assert s1["tuned"] in (1, 2)
+        assert s1["grab"] >= 1
+        r0 = c0.sj_selfjoin(pts, 0.5)
+        assert c0.sj_last_stats()["tuned"] == 0
+        assert np.array_equal(keys(r0), keys(r1))
+        n = c1.sj_selfjoin_count(pts, 0.5)
+        assert c1.sj_last_stats()["tuned"] == 1
+        assert n == len(r0)
