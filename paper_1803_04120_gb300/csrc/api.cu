@@ -393,6 +393,7 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
             return SJ_OK;
         }
         SJ_CUDA_TRY(cudaStreamWaitEvent(sc, ev_k[b], 0));
+        ctx->stats.pairs += cnt;
         if (sink.cb) {
             if (cb_count[k]) SJ_TRY(deliver_cb(k));
             SJ_CUDA_TRY(cudaMemcpyAsync(stage[k], dbuf[k].p, cnt * 8, cudaMemcpyDeviceToHost, sc));
@@ -463,6 +464,7 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
         }
         ctx->stats.evaluations += r3[1];
         ctx->stats.rechecks += r3[2];
+        ctx->stats.pairs += cnt;
         if (sink.cb) {
             SJ_RC(cudaMemcpyAsync(stage[0], dbuf[0].p, cnt * 8, cudaMemcpyDeviceToHost, s));
             SJ_RC(cudaStreamSynchronize(s));

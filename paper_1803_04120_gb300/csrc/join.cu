@@ -24,16 +24,22 @@
 //        FP32 mode: coordinates relative to the home cell's centre,
 //        z = fl32(y - o), and s = |z_p|^2 + |z_q|^2 - 2 z_p . z_q evaluated
 //        as one add and d fused multiply-adds on packed f32x2 pairs (two
-//        candidates per instruction).  s is classified against the proven
-//        margin [lo32, hi32] computed on the host (index.cu); only values
-//        inside the margin are recomputed with the exact FP64 predicate, in a
-//        warp-uniform branch around a non-inlined function so that the slow
-//        FP64 pipe of GB300 sees only the real rechecks.
+//        candidates per instruction).  s is compared with the proven margin
+//        [lo32, hi32] computed on the host (margin.cu): per candidate slot
+//        each lane keeps a 32-bit mask of the queries within hi32.  Hits
+//        above lo32 (the band) are recomputed with the exact FP64
+//        predicate, in a warp-uniform branch around a non-inlined function
+//        so that the slow FP64 pipe of GB300 sees only the real rechecks.
 //        FP64 mode: the exact predicate for every candidate.
-//   5. emits: under UNICOMP each hit (p, q) gives (p, q) and (q, p); in the
-//      home cell only q >= p is compared and the self-pair is emitted once.
-//      Pairs are staged per warp in shared memory (ballot + popc offsets) and
-//      written out in coalesced blocks after one atomic reservation per flush.
+//   5. emits: FP32 mode under UNICOMP: the self-pair of every query once
+//      per item, then each hit (p, q) gives (p, q) and (q, p), and in the
+//      home cell only candidates after the query's own position count (the
+//      masks are cleared with bit operations); without UNICOMP each hit
+//      gives (p, q), the self-pair included.  Pairs are staged per warp in
+//      shared memory in a few rounds per chunk, one warp scan each.  FP64
+//      mode: per query, ballot + popc offsets, the self-pair once.  Staged
+//      pairs are written out in coalesced blocks after one atomic
+//      reservation per flush.
 // Waits on mbarriers are bounded by a time limit; on expiry the warp records
 // an error bit, waits (bounded) for its copies in flight and leaves.
 #include <cmath>
@@ -396,63 +402,6 @@ __device__ __forceinline__ void eval_query(const float *qd, const f2_t (*z)[D], 
     for (int cp = 0; cp < NP; ++cp) f2_unpack(acc[cp], sv[2 * cp], sv[2 * cp + 1]);
 }
 
-// Decides the candidates of one query per lane (hb: values <= hi32) and
-// stages their pairs.  Values above lo32 are recomputed with the exact FP64
-// predicate; in the home cell only candidates at or after the query's own
-// position count, and the self-pair is emitted once.  Every lane may hold a
-// different query (qd, ql).  The caller guarantees room for 2 * 32 * CPL
-// pairs in the staging buffer.
-template <int D, int CPL, bool UNI>
-__device__ __forceinline__ void refine_emit(Pipe &st, const WarpSmem &ws, const JoinArgs &a,
-                                            int lane, const float *qd, const float *sv, uint32_t hb,
-                                            const uint32_t *cid, bool home_chunk, uint32_t kb,
-                                            uint32_t home_len, uint32_t ql,
-                                            unsigned long long &rechecks) {
-    uint32_t selfb = 0, needb = 0;
-#pragma unroll
-    for (int s = 0; s < CPL; ++s) {
-        if (home_chunk) {
-            const uint32_t k = kb + lane + 32 * s;
-            if (k < home_len) {
-                if (k < ql) hb &= ~(1u << s);
-                if (k == ql) selfb |= 1u << s;
-            }
-        }
-        if (((hb >> s) & 1u) && !((selfb >> s) & 1u) && sv[s] > a.lo32) needb |= 1u << s;
-    }
-    const uint32_t qid = __float_as_uint(qd[2 * D + 2]);
-    if (__any_sync(0xffffffffu, needb)) {
-#pragma unroll
-        for (int s = 0; s < CPL; ++s) {
-            if ((needb >> s) & 1u) {
-                ++rechecks;
-                if (!exact_member_ni(a.pts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
-                    hb &= ~(1u << s);
-            }
-        }
-    }
-    selfb &= hb;
-    const uint32_t n = UNI ? 2u * __popc(hb) - __popc(selfb) : (uint32_t)__popc(hb);
-    uint32_t incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (n && !a.count_only) {
-        uint32_t pos = st.fill + incl - n;
-#pragma unroll
-        for (int s = 0; s < CPL; ++s) {
-            if ((hb >> s) & 1u) {
-                ws.emit[pos++] = make_uint2(qid, cid[s]);
-                if (UNI && !((selfb >> s) & 1u)) ws.emit[pos++] = make_uint2(cid[s], qid);
-            }
-        }
-    }
-    st.fill += total;
-}
-
 // Takes the next work item for this warp; false when none is left.
 __device__ __forceinline__ bool fetch_item(Pipe &st, const JoinArgs &a, uint32_t item_end,
                                            int lane, uint2 &it) {
@@ -634,54 +583,122 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
 
     if (F32) {
         constexpr int NP = CPL / 2;
-        const float hi32 = a.hi32;
+        const float hi32 = a.hi32, lo32 = a.lo32;
         f2_t z[NP][D], qq2[NP];
         uint32_t cid[CPL];
         load_candidates<D, CPL>(buf, a.rs, clen, lane, hd->o, z, qq2, cid);
         const float *qbase = reinterpret_cast<const float *>(ws.q[sl]);
-        if (D <= 3) {
-            // frequent hits: decide and emit per query
-            for (uint32_t qi = 0; qi < nq; ++qi) {
-                const float *qd = qbase + (size_t)qi * a.qrs;
-                float sv[CPL];
-                eval_query<D, NP>(qd, z, qq2, sv);
-                uint32_t hb = 0;
-#pragma unroll
-                for (int s = 0; s < CPL; ++s) hb |= (sv[s] <= hi32 ? 1u : 0u) << s;
-                if (!__any_sync(0xffffffffu, hb)) continue;
-                if (st.fill + 2 * 32 * CPL > (uint32_t)a.eb) flush(st, ws, a, lane);
-                refine_emit<D, CPL, UNI>(st, ws, a, lane, qd, sv, hb, cid, home_chunk, kb, home_len,
-                                         ql_base + qi, rechecks);
+        if (UNI && ch == 0) {
+            // UNICOMP: the item's self-pairs, one per query point; every
+            // other hit then stands for both (p, q) and (q, p).  (The full
+            // search meets the query itself as an ordinary hit.)
+            if (st.fill + nq > (uint32_t)a.eb) flush(st, ws, a, lane);
+            if (!a.count_only && lane < (int)nq) {
+                const uint32_t qid = __float_as_uint(qbase[(size_t)lane * a.qrs + 2 * D + 2]);
+                ws.emit[st.fill + lane] = make_uint2(qid, qid);
             }
-        } else {
-            // rare hits: flag the queries whose value may be a member, one
-            // vote per chunk, then re-evaluate only the flagged queries
-            uint32_t flags = 0;
-            for (uint32_t qi = 0; qi < nq; ++qi) {
-                float sv[CPL];
-                eval_query<D, NP>(qbase + (size_t)qi * a.qrs, z, qq2, sv);
-                float mn = sv[0];
+            st.fill += nq;
+        }
+        // 1. comparison: bit qi of m[s] = candidate slot s is within hi32 of
+        //    query qi; at low d also the band bits (above lo32) on the way
+        uint32_t m[CPL], b[CPL];
 #pragma unroll
-                for (int s = 1; s < CPL; ++s) mn = fminf(mn, sv[s]);
-                flags |= (mn <= hi32 ? 1u : 0u) << qi;
+        for (int s = 0; s < CPL; ++s) m[s] = b[s] = 0u;
+        for (uint32_t qi = 0; qi < nq; ++qi) {
+            float sv[CPL];
+            eval_query<D, NP>(qbase + (size_t)qi * a.qrs, z, qq2, sv);
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                m[s] |= (sv[s] <= hi32 ? 1u : 0u) << qi;
+                if (D <= 3) b[s] |= (sv[s] > lo32 ? 1u : 0u) << qi;
             }
-            while (__any_sync(0xffffffffu, flags)) {
-                // one flagged query per lane per round: at most 2 * CPL pairs each
-                if (st.fill + 2 * 32 * CPL > (uint32_t)a.eb) flush(st, ws, a, lane);
-                uint32_t hb = 0, qi = 0;
-                float sv[CPL];
-                const float *qd = qbase;
-                if (flags) {
-                    qi = __ffs(flags) - 1;
-                    flags &= flags - 1;
-                    qd = qbase + (size_t)qi * a.qrs;
-                    eval_query<D, NP>(qd, z, qq2, sv);
+        }
+        uint32_t any = 0;
 #pragma unroll
-                    for (int s = 0; s < CPL; ++s) hb |= (sv[s] <= hi32 ? 1u : 0u) << s;
+        for (int s = 0; s < CPL; ++s) any |= m[s];
+        if (!__any_sync(0xffffffffu, any)) return;
+        // 2. UNICOMP home cell (range 0): only candidates after the query's
+        //    own position count
+        if (home_chunk) {
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                const uint32_t k = kb + lane + 32 * s;
+                if (k < home_len) {
+                    const uint32_t r = k > ql_base ? k - ql_base : 0u;
+                    m[s] &= r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
                 }
-                refine_emit<D, CPL, UNI>(st, ws, a, lane, qd, sv, hb, cid, home_chunk, kb, home_len,
-                                         ql_base + qi, rechecks);
             }
+        }
+        // 3. band: values above lo32 are decided by the exact FP64
+        //    predicate (at high d the rare hits are re-evaluated to find them)
+        if (D > 3) {
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                uint32_t w = m[s];
+                while (w) {
+                    const uint32_t q = __ffs(w) - 1;
+                    w &= w - 1;
+                    float sv2[2];
+                    eval_query<D, 1>(qbase + (size_t)q * a.qrs, &z[s >> 1], &qq2[s >> 1], sv2);
+                    if (sv2[s & 1] > lo32) b[s] |= 1u << q;
+                }
+            }
+        }
+        uint32_t band = 0;
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            b[s] &= m[s];
+            band |= b[s];
+        }
+        if (__any_sync(0xffffffffu, band)) {
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                uint32_t w = b[s];
+                while (w) {
+                    const uint32_t q = __ffs(w) - 1;
+                    w &= w - 1;
+                    ++rechecks;
+                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + 2 * D + 2]);
+                    if (!exact_member_ni(a.pts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
+                        m[s] &= ~(1u << q);
+                }
+            }
+        }
+        // 4. emission in rounds of at most kPer hits per lane, one warp scan
+        //    and one staging-area check per round
+        constexpr uint32_t kPP = UNI ? 2u : 1u;
+        constexpr uint32_t kPer = (uint32_t)kEmit / (32u * kPP);
+        uint32_t left = 0;
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) left += __popc(m[s]);
+        while (__any_sync(0xffffffffu, left)) {
+            const uint32_t c = left < kPer ? left : kPer;
+            const uint32_t n = c * kPP;
+            uint32_t incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (st.fill + total > (uint32_t)a.eb) flush(st, ws, a, lane);
+            uint32_t pos = st.fill + incl - n;
+            uint32_t t = c;
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                while (t && m[s]) {
+                    const uint32_t q = __ffs(m[s]) - 1;
+                    m[s] &= m[s] - 1;
+                    --t;
+                    if (!a.count_only) {
+                        const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + 2 * D + 2]);
+                        ws.emit[pos++] = make_uint2(qid, cid[s]);
+                        if (UNI) ws.emit[pos++] = make_uint2(cid[s], qid);
+                    }
+                }
+            }
+            left -= c;
+            st.fill += total;
         }
     } else {
         double y[CPL][D];

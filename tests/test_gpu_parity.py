@@ -324,3 +324,33 @@ def test_config2_full_size_sampled(d):
     # degree sum statistics: realised mean within 10% of 64 (boundary effects)
     mean = (cnt - n) / n
     assert 0.7 * 64 < mean < 1.02 * 64
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("d", [2])
+def test_config3_full_size_streamed_digest(d):
+    """10,000,000 points, 128 mean neighbours, result device buffers capped at
+    2 GB: the pairs stream to the host in batches (Section V-A); count,
+    per-point degree and the order-independent pair hash must equal the
+    oracle's."""
+    cfg = datagen.config3(d)
+    pts = datagen.make_points(cfg)
+    n, eps = cfg["n"], cfg["eps"]
+    deg = np.zeros(n, dtype=np.int64)
+    acc = {"count": 0, "hash": 0}
+
+    def cb(pairs):
+        keys = (pairs[:, 0].astype(np.uint64) << np.uint64(32)) | pairs[:, 1].astype(np.uint64)
+        acc["hash"] = (acc["hash"] + orc.pair_hash(keys)) % (1 << 64)
+        acc["count"] += len(pairs)
+        deg[:] += np.bincount(pairs[:, 0], minlength=n)
+        return False
+
+    with sj.Context(out_cap_bytes=2 << 30) as ctx:
+        ctx.sj_selfjoin_stream(pts, eps, cb)
+        st = ctx.sj_last_stats()
+    assert st["batches"] >= 6
+    o_count, o_deg, o_hash = orc.grid_digest(pts, eps)
+    assert acc["count"] == o_count == st["pairs"]
+    assert acc["hash"] == o_hash
+    assert np.array_equal(deg, o_deg.astype(np.int64))
