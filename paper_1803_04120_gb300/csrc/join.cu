@@ -54,12 +54,18 @@ namespace sj {
 
 namespace {
 
-constexpr int kEmit = 512;                 // staged pairs per warp
-
+// The kernel is latency-bound (dependent shared-memory loads and ALU chains
+// per warp), so the per-warp shared memory and registers are sized for
+// resident warps: measured on GB300 with 2,000,000 uniform points.
 // Candidates per lane by dimension and precision (chunk = 32 * CPL).
 __host__ __device__ constexpr int cpl_for(int d, bool f32) { return f32 ? (d <= 3 ? 2 : 4) : 2; }
-// Depth of the chunk ring (smaller chunks need more of them in flight).
-__host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >= 4) ? 3 : 4; }
+// Default depth of the chunk ring (a launch may choose another).
+__host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >= 4) ? 2 : 4; }
+// Staged pairs per warp: many pairs per chunk at low d want a large staging
+// area (fewer flushes); at higher d a smaller one leaves room for warps.
+__host__ __device__ constexpr int emit_for(int d, bool f32) { return (f32 && d >= 3) ? 256 : 512; }
+// Minimum resident blocks of 256 threads the compiler sizes registers for.
+__host__ __device__ constexpr int minb_for(int d, bool f32) { return f32 ? (d <= 2 ? 1 : (d == 3 ? 3 : 2)) : 1; }
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -667,7 +673,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         // 4. emission in rounds of at most kPer hits per lane, one warp scan
         //    and one staging-area check per round
         constexpr uint32_t kPP = UNI ? 2u : 1u;
-        constexpr uint32_t kPer = (uint32_t)kEmit / (32u * kPP);
+        constexpr uint32_t kPer = (uint32_t)emit_for(D, true) / (32u * kPP);
         uint32_t left = 0;
 #pragma unroll
         for (int s = 0; s < CPL; ++s) left += __popc(m[s]);
@@ -851,8 +857,8 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
 }
 
 template <int D, bool F32, bool UNI>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1) join_kernel(const JoinArgs a,
-                                                                     const uint32_t *counts) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, minb_for(D, F32))
+    join_kernel(const JoinArgs a, const uint32_t *counts) {
     extern __shared__ __align__(128) unsigned char smem[];
     (void)join_body<D, F32, UNI>(a, counts, smem, threadIdx.x >> 5, threadIdx.x & 31);
 }
@@ -1012,8 +1018,8 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.sm_ranges = round16(a.n_templates * (int)sizeof(uint2));
     a.sm_queries = round16(kQueryBlock * a.qrs * esz);
     a.sm_chunk = round16(a.cb * rsb);
-    a.eb = kEmit;
-    a.sm_emit = round16(kEmit * (int)sizeof(uint2));
+    a.eb = emit_for(d, f32);
+    a.sm_emit = round16(a.eb * (int)sizeof(uint2));
     // ring depth: the launch's choice (2..8 chunks; the warp has 8 mbarriers)
     a.nbuf = (cfg.nbuf >= 2 && cfg.nbuf <= 8) ? cfg.nbuf : nbuf_for(d, f32);
     a.sm_warp = 64 + round16(2 * (int)sizeof(ItemHdr)) + 2 * a.sm_ranges + 2 * a.sm_queries +
