@@ -670,38 +670,53 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                 }
             }
         }
-        // 4. emission in rounds of at most kPer hits per lane, one warp scan
-        //    and one staging-area check per round
+        // 4. emission in rounds of at most kPer hits per lane.  Within a
+        //    round the t-th hit of every lane that has one goes to
+        //    consecutive staging slots (order by (t, lane)), so the stores of
+        //    one instruction hit consecutive words (no bank conflicts); the
+        //    order of pairs in the output is free.
         constexpr uint32_t kPP = UNI ? 2u : 1u;
         constexpr uint32_t kPer = (uint32_t)emit_for(D, true) / (32u * kPP);
+        const unsigned lt = (1u << lane) - 1u;
         uint32_t left = 0;
 #pragma unroll
         for (int s = 0; s < CPL; ++s) left += __popc(m[s]);
         while (__any_sync(0xffffffffu, left)) {
             const uint32_t c = left < kPer ? left : kPer;
-            const uint32_t n = c * kPP;
-            uint32_t incl = n;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t total = __reduce_add_sync(0xffffffffu, c) * kPP;
             if (st.fill + total > (uint32_t)a.eb) flush(st, ws, a, lane);
-            uint32_t pos = st.fill + incl - n;
-            uint32_t t = c;
+            uint32_t base = st.fill;
+            int s_cur = 0;
+            for (uint32_t t = 0;; ++t) {
+                const bool act = t < c;
+                const unsigned bm = __ballot_sync(0xffffffffu, act);
+                if (!bm) break;
+                const uint32_t nb = __popc(bm);
+                if (act) {
+                    // this lane's next hit: lowest query bit of the first
+                    // non-empty slot
+                    uint32_t q = 0, cand = 0;
 #pragma unroll
-            for (int s = 0; s < CPL; ++s) {
-                while (t && m[s]) {
-                    const uint32_t q = __ffs(m[s]) - 1;
-                    m[s] &= m[s] - 1;
-                    --t;
+                    for (int s = 0; s < CPL; ++s) {
+                        if (s == s_cur && m[s] == 0) ++s_cur;
+                    }
+#pragma unroll
+                    for (int s = 0; s < CPL; ++s) {
+                        if (s == s_cur) {
+                            q = __ffs(m[s]) - 1;
+                            m[s] &= m[s] - 1;
+                            cand = cid[s];
+                        }
+                    }
                     if (!a.count_only) {
+                        // (p, q) of all active lanes, then their (q, p)
                         const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + 2 * D + 2]);
-                        ws.emit[pos++] = make_uint2(qid, cid[s]);
-                        if (UNI) ws.emit[pos++] = make_uint2(cid[s], qid);
+                        const uint32_t pos = base + __popc(bm & lt);
+                        ws.emit[pos] = make_uint2(qid, cand);
+                        if (UNI) ws.emit[pos + nb] = make_uint2(cand, qid);
                     }
                 }
+                base += kPP * nb;
             }
             left -= c;
             st.fill += total;
