@@ -48,6 +48,26 @@ UNIT = "pairs/s"
 WORKLOAD = "uniform 2,000,000 points in [0,100]^d for d=2..6, eps for 64 mean neighbours"
 
 
+def profiled_traffic(d: int):
+    """DRAM bytes per launch of the d-dimensional join kernel from the ncu
+    summary in profiles/, or None when the kernel source has changed since
+    that capture (or d was not captured)."""
+    import hashlib
+    import re
+    summ = os.path.join(ROOT, "profiles", "join_kernel_uniform2M.md")
+    src = os.path.join(ROOT, "paper_1803_04120_gb300", "csrc", "join.cu")
+    try:
+        text = open(summ).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch\[d=%d\]:\s*(\d+)" % d, text)
+    if not m or not t or m.group(1) != h:
+        return None
+    return int(t.group(1))
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm, src = 6800.0, "fallback"
@@ -390,7 +410,10 @@ def run_gpu(args):
                              evaluations=st["evaluations"], pairs=cnt, rechecks=st["rechecks"]))
     dom = max(roof_all, key=lambda r: r["kernel_ms"])
     roofline = dict(bound=dom["bound"], achieved=dom["achieved"], peak=dom["peak"], unit=dom["unit"],
-                    frac=dom["frac"], traffic=None, kernel=f"join_kernel d={dom['d']}",
+                    frac=dom["frac"], traffic=profiled_traffic(dom["d"]),
+                    traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                   "(profiles/join_kernel_uniform2M.md); null when the kernel changed",
+                    kernel=f"join_kernel d={dom['d']}",
                     peak_source=("fp32: 152 SMs x 128 lanes x 2 x max SM clock" if dom["bound"] == "alu"
                                  else f"hbm_gbs {psrc}"),
                     all_launches_frac=round(sum(r["roofline_ms"] for r in roof_all)
