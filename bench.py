@@ -209,7 +209,8 @@ def skew_bench(dev: int, reps: int):
             kms, nl = c.sj_profile_read()
             st = c.sj_last_stats()
             res[name] = dict(ms=round(statistics.mean(ts), 3), kernel_ms=round(kms / max(nl, 1), 3),
-                             grab=st["grab"], nbuf=st["nbuf"], wpb=st["wpb"], tuned=st["tuned"])
+                             grab=st["grab"], nbuf=st["nbuf"], wpb=st["wpb"], staging=st["staging"],
+                             tuned=st["tuned"])
         out.append(dict(d=d, n=cfg["n"], eps=cfg["eps"], pairs=cnt,
                         default=res["default"], tuned=res["tuned"],
                         pairs_per_s_tuned=round(cnt / (res["tuned"]["ms"] / 1e3), 1),
@@ -282,6 +283,7 @@ def serving_bench(dev: int, n_req: int, seed: int = 5):
         wall = max(td for _, (ts, ta, td) in got) - min(ts for _, (ts, ta, td) in got)
         return sum(c for c, _ in got), wall, lat
 
+    run([0.0] * n_req)                    # untimed pass: pinned result buffers, pool
     p_sat, wall_sat, lat_sat = run([0.0] * n_req)
     assert p_sat == tot64
     rate = 0.5 * n_req / wall_sat
@@ -306,6 +308,8 @@ def serving_bench(dev: int, n_req: int, seed: int = 5):
         "waves": info["waves"], "max_wave": info["max_wave"],
         "max_concurrent_waves": info["max_concurrent_waves"], "overflow_reruns": info["overflow_reruns"],
         "standalone": info["standalone"],
+        "lane_ms": {"bounds": round(info["ms_bounds"], 1), "graph": round(info["ms_graph"], 1),
+                    "output": round(info["ms_output"], 1)},
     }
 
 
@@ -453,6 +457,17 @@ def run_gpu(args):
     return line
 
 
+def replica_value(ms_local: float, pairs_per_step: int, device: str):
+    """Replicas: the slowest rank's step time and the whole-job pairs/s
+    (every rank processes pairs_per_step per step)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, dist.get_world_size() * pairs_per_step / (ms / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -506,18 +521,15 @@ def main():
         # whole-job value is the sum over ranks of pairs over the max time
         # (the serving and clustered sections are single-GPU measurements)
         args.serve_requests, args.no_skew = 0, True
-        import torch
         import torch.distributed as dist
         dist.init_process_group("nccl")
         args.no_cpu = args.no_cpu or rank != 0
         line = run_gpu(args)
-        t = torch.tensor([line["ms_per_step"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, value = replica_value(line["ms_per_step"], line["config"]["pairs_per_step"], "cuda")
         if rank == 0:
-            ms = float(t.item())
             line["n_gpus"] = world
             line["ms_per_step"] = round(ms, 4)
-            line["value"] = round(world * line["config"]["pairs_per_step"] / (ms / 1e3), 1)
+            line["value"] = round(value, 1)
             line["config"]["parallelism"] = f"replicas x{world}"
             print(json.dumps(line))
         dist.destroy_process_group()

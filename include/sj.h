@@ -32,7 +32,7 @@
  *   - `pts` is n x d row-major FP64.  It may be a host or a device pointer;
  *     the library detects which.  The caller keeps ownership; the library
  *     copies what it needs and does not hold the pointer after the call
- *     returns (sj_submit: until the request completes, see there).
+ *     returns (sj_submit copies the points before it returns).
  *   - A pair is two consecutive uint32 values (i, j).  Results returned in
  *     sj_result are library-owned host memory, valid until sj_result_free.
  *   - Pair order is unspecified unless sj_config.sorted = 1, which orders
@@ -102,8 +102,9 @@ typedef struct {
                                 (Section V-A uses 3); default 3 */
     int32_t sorted;          /* 1: host results sorted by (i << 32) | j */
     int32_t autotune;        /* 1 (default): the search-and-refine launch
-                                parameters (grab, chunk ring depth, warps per
-                                block) come from the tuner, which times
+                                parameters (grab, chunk ring depth, pair
+                                staging size, warps per block) come from
+                                the tuner, which times
                                 sampled count-only launches the first time a
                                 (d, precision, UNICOMP, points-per-cell
                                 bucket) key is met in the process and reuses
@@ -119,7 +120,10 @@ typedef struct {
     /* launch tuning of the search-and-refine kernel; -1 (default) lets the
      * library (or the tuner, with autotune = 1) choose */
     int32_t grab;            /* work items a warp takes per cursor bump */
-    int32_t reserved[7];
+    int32_t nbuf;            /* candidate-chunk ring depth (2..8) */
+    int32_t staging;         /* staged pairs per warp (256, 512 or 1024) */
+    int32_t wpb;             /* warps per block (1, 2, 4 or 8) */
+    int32_t reserved[4];
 } sj_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -275,6 +279,31 @@ SJ_API const uint32_t *sj_result_pairs(const sj_result *r);   /* 2 * count uint3
 SJ_API void sj_result_free(sj_result *r);                     /* NULL is ignored */
 
 /* ------------------------------------------------------------------ */
+/* One join split over several ranks (one process per GPU).           */
+/* ------------------------------------------------------------------ */
+
+/* The share of rank `rank` of `world` in one join: the rank builds the grid
+ * index of all points (Section IV-B/C, the same on every rank) and
+ * searches only the query cells of its shard, emitting the pairs whose
+ * home cell (under UNICOMP, the cell that visits the cell pair, Section V-B)
+ * is one of them.  The ranks' outputs are disjoint and their union is the
+ * full result; summing the counts (one all-reduce) is the only exchange.
+ * Shards are contiguous ranges of work items (cell, block of 32 points)
+ * cut at cell starts, balanced by query blocks (see sj_shard_bounds).
+ * Arguments and errors as sj_selfjoin_device, plus SJ_EINVAL unless
+ * 0 <= rank < world. */
+SJ_API sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                                          double eps, int rank, int world, uint32_t *d_pairs,
+                                          uint64_t cap_pairs, uint64_t *count, void *stream);
+
+/* The shard rule on a host array, needing no device: item_block[k] is the
+ * block index within its cell of work item k (0 at a cell start; items in
+ * cell order).  [*lo, *hi) is [n r / w, n (r + 1) / w) with each bound moved
+ * forward to the next cell start (or n).  The ranks' ranges tile [0, n). */
+SJ_API sj_status sj_shard_bounds(const uint32_t *item_block, uint64_t n_items, int rank,
+                                 int world, uint64_t *lo, uint64_t *hi);
+
+/* ------------------------------------------------------------------ */
 /* Many joins at once.                                                */
 /* ------------------------------------------------------------------ */
 
@@ -331,6 +360,8 @@ typedef struct {
     int32_t nbuf;            /* candidate-chunk ring depth (0: by dimension) */
     int32_t wpb;             /* warps per block (0: by occupancy) */
     int32_t tuned;           /* 0 defaults, 1 from the tuner's cache, 2 tuned by this call */
+    int32_t staging;         /* staged pairs per warp (0: by dimension) */
+    int32_t reserved_;
 } sj_stats;
 
 SJ_API sj_status sj_last_stats(const sj_ctx *ctx, sj_stats *out);
@@ -350,7 +381,8 @@ SJ_API sj_status sj_profile_read(sj_ctx *ctx, double *kernel_ms, uint64_t *launc
  * estimated device memory fits in serve_mem_bytes; admitted requests share
  * persistent multi-join kernel launches, so requests that arrive while
  * others run overlap with them on the device.  Errors: as sj_selfjoin for
- * the arguments, SJ_ENOMEM if the request alone exceeds serve_mem_bytes. */
+ * the arguments, SJ_ENOMEM if the request alone exceeds serve_mem_bytes;
+ * a NaN or infinite coordinate is reported by sj_poll (SJ_EINVAL). */
 SJ_API sj_status sj_submit(sj_ctx *ctx, const double *pts, uint64_t n, int d,
                     double eps, uint64_t *ticket);
 
@@ -374,6 +406,10 @@ typedef struct {
     int32_t lanes;             /* waves that may run at the same time */
     int32_t max_concurrent_waves; /* most waves seen running at once */
     int32_t reserved;
+    /* host wall time summed over the lanes' waves (ms): points to the device
+     * and the bounds pass, the graph replay (index build + join), the result
+     * copies to the host */
+    double ms_bounds, ms_graph, ms_output;
 } sj_serve_info;
 
 SJ_API sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out);

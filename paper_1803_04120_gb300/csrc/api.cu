@@ -94,7 +94,19 @@ struct PinnedCache {
     size_t cached = 0;
     static constexpr size_t kLimit = (size_t)32 << 30;
 
+    // Buffers are allocated in size classes (eight per power of two, at
+    // least 64 KiB) so that a freed buffer serves later requests of about
+    // the same size: pinning fresh memory costs far more than the slack.
+    static size_t size_class(size_t bytes) {
+        size_t c = (size_t)64 << 10;
+        if (bytes <= c) return c;
+        size_t p = 1;
+        while (p <= bytes / 2) p <<= 1;      // largest power of two <= bytes
+        const size_t step = p / 8;
+        return (bytes + step - 1) / step * step;
+    }
     void *get(size_t bytes, size_t *got) {
+        bytes = size_class(bytes);
         {
             std::lock_guard<std::mutex> lk(mu);
             auto it = free_list.lower_bound(bytes);
@@ -198,18 +210,23 @@ JoinLaunch default_launch(const sj_ctx *ctx) {
     l.prec_fp32 = ctx->cfg.prec == SJ_PREC_FP32_RECHECK;
     l.unicomp = ctx->cfg.unicomp;
     l.grab = ctx->cfg.grab > 0 ? ctx->cfg.grab : 1;
+    l.nbuf = ctx->cfg.nbuf > 0 ? ctx->cfg.nbuf : 0;
+    l.eb = ctx->cfg.staging > 0 ? ctx->cfg.staging : 0;
+    l.wpb = ctx->cfg.wpb > 0 ? ctx->cfg.wpb : 0;
     return l;
 }
+
+bool launch_forced(const sj_config &c) { return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.wpb > 0; }
 
 JoinLaunch launch_cfg(const sj_ctx *ctx) { return ctx->launch; }
 
 // Launch parameters of the join on ix: the defaults, or with autotune = 1
-// (and no grab forced in the configuration) the tuner's choice for the
+// (and no launch parameter forced in the configuration) the tuner's choice for the
 // index's key (one host read of |G| and the work-item count first).
 sj_status prepare_launch(Error &err, sj_ctx *ctx, Index &ix, cudaStream_t s) {
     ctx->launch = default_launch(ctx);
     ctx->launch_tuned = 0;
-    if (!ctx->cfg.autotune || ctx->cfg.grab > 0) return SJ_OK;
+    if (!ctx->cfg.autotune || launch_forced(ctx->cfg)) return SJ_OK;
     SJ_TRY(read_counts(err, ix, s));
     return tune_launch(err, ix, ctx->launch, s, &ctx->launch_tuned);
 }
@@ -218,6 +235,7 @@ void record_launch(sj_ctx *ctx) {
     ctx->stats.grab = ctx->launch.grab;
     ctx->stats.nbuf = ctx->launch.nbuf;
     ctx->stats.wpb = ctx->launch.wpb;
+    ctx->stats.staging = ctx->launch.eb;
     ctx->stats.tuned = ctx->launch_tuned;
 }
 
@@ -549,6 +567,9 @@ void sj_config_default(sj_config *cfg) {
     cfg->max_inflight = 64;
     cfg->serve_mem_bytes = 8ull << 30;
     cfg->grab = -1;
+    cfg->nbuf = -1;
+    cfg->staging = -1;
+    cfg->wpb = -1;
 }
 
 const char *sj_status_str(sj_status st) {
@@ -696,11 +717,12 @@ sj_status sj_index_export(const sj_index *ix, uint64_t *B, uint32_t *G, uint32_t
 }
 
 static sj_status device_join_on(sj_ctx *ctx, Error &err, Index &ix, uint32_t *d_pairs,
-                                uint64_t cap, uint64_t *count, cudaStream_t s, int count_only) {
+                                uint64_t cap, uint64_t *count, cudaStream_t s, int count_only,
+                                uint32_t item_begin = 0, uint32_t item_end = 0xffffffffu) {
     if (!(ctx->cfg.prec == SJ_PREC_FP32_RECHECK && ix.g.fp32_ok)) SJ_TRY(ensure_rec64(err, ix, s));
     SJ_TRY(prepare_launch(err, ctx, ix, s));
     unsigned long long r[3];
-    SJ_TRY(join_once(err, ctx, ix, 0, 0xffffffffu, 1, reinterpret_cast<uint2 *>(d_pairs), cap,
+    SJ_TRY(join_once(err, ctx, ix, item_begin, item_end, 1, reinterpret_cast<uint2 *>(d_pairs), cap,
                      count_only, s, r));
     *count = r[0];
     record_launch(ctx);
@@ -728,6 +750,33 @@ sj_status sj_selfjoin_device(sj_ctx *ctx, const double *pts, uint64_t n, int d, 
     st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, s, ix);
     double t1 = now_ms();
     if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, d_pairs, cap_pairs, count, s, 0);
+    free_index(ix, s);
+    ctx->stats.ms_index = t1 - t0;
+    ctx->stats.ms_join = now_ms() - t1;
+    ctx->stats.ms_total = now_ms() - t0;
+    return sc.done(st);
+}
+
+sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, int d, double eps,
+                                   int rank, int world, uint32_t *d_pairs, uint64_t cap_pairs,
+                                   uint64_t *count, void *stream) {
+    if (!ctx || !count) return SJ_EINVAL;
+    Scoped sc(ctx);
+    reset_stats(ctx);
+    sj_status st = check_args(sc.err, pts, n, d, eps);
+    if (st != SJ_OK) return sc.done(st);
+    if (world < 1 || rank < 0 || rank >= world)
+        return sc.done(fail(sc.err, SJ_EINVAL, "rank must be in [0, world)"));
+    if (!d_pairs && cap_pairs) return sc.done(fail(sc.err, SJ_EINVAL, "d_pairs is NULL"));
+    if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double t0 = now_ms();
+    Index ix;
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, s, ix);
+    double t1 = now_ms();
+    uint32_t lo = 0, hi = 0;
+    if (st == SJ_OK) st = shard_items(sc.err, ix, rank, world, s, &lo, &hi);
+    if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, d_pairs, cap_pairs, count, s, 0, lo, hi);
     free_index(ix, s);
     ctx->stats.ms_index = t1 - t0;
     ctx->stats.ms_join = now_ms() - t1;

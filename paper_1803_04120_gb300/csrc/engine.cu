@@ -376,6 +376,7 @@ public:
     int build_blocks = 0;
     int sms = 0;
     sj_ctx *fallback = nullptr;
+    cudaEvent_t ev[kMultiJobs] = {};   // per-job completion of the result copies
     EngStats stats;
 };
 
@@ -442,6 +443,8 @@ struct JobMem {
     uint64_t lut_len = 0;
     double est = 0;
     int row = 0;                 // bounds / counter row
+    const uint2 *src = nullptr;  // pairs to copy out
+    uint64_t count = 0;
 };
 
 }  // namespace
@@ -471,6 +474,11 @@ sj_status engine_create(Error &err, int device, const sj_config &cfg, Engine **o
         set_cuda_error(err, ce, "engine allocation", __FILE__, __LINE__);
         return bad(SJ_ENOMEM);
     }
+    for (int q = 0; q < kMultiJobs; ++q)
+        if ((ce = cudaEventCreateWithFlags(&e->ev[q], cudaEventDisableTiming)) != cudaSuccess) {
+            set_cuda_error(err, ce, "cudaEventCreate", __FILE__, __LINE__);
+            return bad(err.st);
+        }
     e->h_mj = static_cast<MultiJobs *>(std::calloc(1, sizeof(MultiJobs)));
     if (!e->h_mj) return bad(fail(err, SJ_ENOMEM, "host allocation failed"));
     std::memset(e->h_table, 0, sizeof(EngTable));
@@ -497,6 +505,8 @@ void engine_destroy(Engine *e) {
     if (e->h_mm) cudaFreeHost(e->h_mm);
     if (e->h_misc) cudaFreeHost(e->h_misc);
     std::free(e->h_mj);
+    for (int q = 0; q < kMultiJobs; ++q)
+        if (e->ev[q]) cudaEventDestroy(e->ev[q]);
     if (e->fallback) sj_destroy(e->fallback);
     if (e->st) cudaStreamDestroy(e->st);
     cudaGetLastError();
@@ -531,13 +541,14 @@ uint64_t engine_estimate(const double *pts, uint64_t n, int d, double eps, uint6
     return (uint64_t)(per_point * n + lut + 8.0 * (1.25 * p + 4096) + (1 << 20));
 }
 
-sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
-    if (k <= 0) return SJ_OK;
-    if (k > kMultiJobs) return fail(err, SJ_EINVAL, "too many jobs for one wave");
+namespace {
+
+sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
+                          void (*on_done)(void *user, int job), void *user,
+                          std::vector<JobMem> &mem) {
     SJ_CUDA_TRY(cudaSetDevice(e->device));
     cudaStream_t s = e->st;
     const double t0 = now_ms();
-    std::vector<JobMem> mem(k);
     std::vector<int> standalone;
     for (int i = 0; i < k; ++i) {
         jobs[i]->st = SJ_OK;
@@ -546,13 +557,6 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
         jobs[i]->evaluations = jobs[i]->rechecks = 0;
         jobs[i]->path = 0;
     }
-    auto release = [&]() {
-        for (JobMem &m : mem) {
-            dev_free(m.pts, s);
-            dev_free(m.region, s);
-            dev_free(m.out2, s);
-        }
-    };
     auto job_fail = [&](int i, sj_status st, const std::string &msg) {
         jobs[i]->st = st;
         jobs[i]->msg = msg;
@@ -732,6 +736,8 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
         l.prec_fp32 = e->cfg.prec == SJ_PREC_FP32_RECHECK;
         l.unicomp = 1;
         l.grab = e->cfg.grab > 0 ? e->cfg.grab : 1;
+        l.nbuf = e->cfg.nbuf > 0 ? e->cfg.nbuf : 0;
+        l.eb = e->cfg.staging > 0 ? e->cfg.staging : 0;
         JoinArgs &a = MJ->job[slot];
         if (fill_join_args(e2, v, l, 0, 0xffffffffu, m.out, m.cap, sl.misc,
                            reinterpret_cast<uint32_t *>(sl.misc + 4),
@@ -773,6 +779,7 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
     const double t3 = now_ms();
 
     // 3. counts, reruns after overflow, pairs to the host
+    std::vector<int> ready;
     for (int i : order) {
         EngJob &J = *jobs[i];
         JobMem &m = mem[i];
@@ -794,6 +801,8 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
             l.prec_fp32 = e->cfg.prec == SJ_PREC_FP32_RECHECK;
             l.unicomp = 1;
             l.grab = e->cfg.grab > 0 ? e->cfg.grab : 1;
+            l.nbuf = e->cfg.nbuf > 0 ? e->cfg.nbuf : 0;
+            l.eb = e->cfg.staging > 0 ? e->cfg.staging : 0;
             if (cudaMemsetAsync(dm, 0, kMiscWords * 8, s) != cudaSuccess ||
                 launch_join(e2, m.view, l, 0, 0xffffffffu, static_cast<uint2 *>(m.out2.p), count, dm,
                             reinterpret_cast<uint32_t *>(dm + 4), reinterpret_cast<uint32_t *>(dm + 5), 0,
@@ -813,13 +822,24 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
             J.path = 2;
             e->stats.overflow_reruns++;
         }
+        m.src = src;
+        m.count = count;
+        ready.push_back(i);
+    }
+    // pairs to the host, smallest result first, each completing on its own
+    // event so that the caller can hand it out before the larger ones land
+    std::stable_sort(ready.begin(), ready.end(),
+                     [&](int x, int y) { return mem[x].count < mem[y].count; });
+    std::vector<int> copied;
+    for (int i : ready) {
         sj_result *r = new sj_result();
         size_t got = 0;
-        r->pairs = static_cast<uint32_t *>(pinned_get(std::max<size_t>(count * 8, 64), &got));
+        r->pairs = static_cast<uint32_t *>(pinned_get(std::max<size_t>(mem[i].count * 8, 64), &got));
         if (!r->pairs) { delete r; job_fail(i, SJ_ENOMEM, "pinned host allocation failed"); continue; }
         r->bytes = got;
-        r->count = count;
-        const cudaError_t ce = cudaMemcpyAsync(r->pairs, src, count * 8, cudaMemcpyDeviceToHost, s);
+        r->count = mem[i].count;
+        cudaError_t ce = cudaMemcpyAsync(r->pairs, mem[i].src, mem[i].count * 8, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e->ev[copied.size()], s);
         if (ce != cudaSuccess) {
             cudaGetLastError();
             pinned_put(r->pairs, r->bytes);
@@ -827,14 +847,24 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
             job_fail(i, SJ_ECUDA, cudaGetErrorString(ce));
             continue;
         }
-        J.res = r;
+        jobs[i]->res = r;
+        copied.push_back(i);
     }
-    SJ_CUDA_TRY(cudaStreamSynchronize(s));
-    release();
-    SJ_CUDA_TRY(cudaStreamSynchronize(s));
-    if (e->cfg.sorted)
-        for (int i : order)
-            if (jobs[i]->res) sort_result(jobs[i]->res);
+    std::vector<char> signalled(k, 0);
+    for (size_t q = 0; q < copied.size(); ++q) {
+        const int i = copied[q];
+        const cudaError_t ce = cudaEventSynchronize(e->ev[q]);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            sj_result_free(jobs[i]->res);
+            jobs[i]->res = nullptr;
+            job_fail(i, SJ_ECUDA, cudaGetErrorString(ce));
+        } else if (e->cfg.sorted) {
+            sort_result(jobs[i]->res);
+        }
+        if (on_done) on_done(user, i);
+        signalled[i] = 1;
+    }
     const double t4 = now_ms();
 
     // jobs the engine does not take: the stand-alone path
@@ -854,12 +884,33 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k) {
         J.path = 1;
         e->stats.standalone++;
     }
+    if (on_done)
+        for (int i = 0; i < k; ++i)
+            if (!signalled[i]) on_done(user, i);
     e->stats.waves++;
     e->stats.jobs += (uint64_t)k;
     e->stats.ms_bounds += t1 - t0;
     e->stats.ms_graph += t3 - t2;
     e->stats.ms_output += t4 - t3;
     return SJ_OK;
+}
+
+}  // namespace
+
+sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k,
+                     void (*on_done)(void *user, int job), void *user) {
+    if (k <= 0) return SJ_OK;
+    if (k > kMultiJobs) return fail(err, SJ_EINVAL, "too many jobs for one wave");
+    std::vector<JobMem> mem(k);
+    const sj_status st = engine_run_impl(err, e, jobs, k, on_done, user, mem);
+    // device memory of the wave goes back to the pool on every path
+    for (JobMem &m : mem) {
+        dev_free(m.pts, e->st);
+        dev_free(m.region, e->st);
+        dev_free(m.out2, e->st);
+    }
+    if (cudaStreamSynchronize(e->st) != cudaSuccess) cudaGetLastError();
+    return st;
 }
 
 }  // namespace sj

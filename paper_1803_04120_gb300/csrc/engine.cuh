@@ -40,8 +40,11 @@ void engine_destroy(Engine *e);
 // replay of the engine's CUDA graph (batched index build of every job and
 // one persistent multi-join launch), then the results to pinned host memory.
 // Per-job failures are reported in the job; the return value is SJ_OK unless
-// the engine itself failed.
-sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k);
+// the engine itself failed.  on_done (optional) is called once per job, from
+// the calling thread, as soon as that job's result is on the host (or the
+// job failed): smaller results first.
+sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k,
+                     void (*on_done)(void *user, int job) = nullptr, void *user = nullptr);
 EngStats engine_stats(const Engine *e);
 
 // Device bytes a job is expected to hold in the engine (points, index,

@@ -5,15 +5,19 @@
 // Scheduler.  sj_submit copies the request's points into pinned host memory,
 // estimates the device bytes the request will hold (points, index, result
 // buffer; engine.cu) and queues it.  Each of kLanes lane threads owns a
-// multi-join engine (its own stream, job tables and CUDA graph).  A lane
-// that is idle admits queued requests in arrival order while fewer than
-// max_inflight requests are admitted over all lanes and their estimated
-// bytes fit in serve_mem_bytes (at most kMultiJobs per wave), then runs them
-// as one wave.  So requests that arrive while a wave runs are admitted by
-// the other lane as soon as slots and memory allow, and the two waves
-// overlap on the device; memory and slots are returned when a wave's
-// results are on the host.  A request's result does not depend on the wave
-// it ran in: every job has its own index, cursor, counters and output.
+// multi-join engine (its own stream, job tables and CUDA graph).  An idle
+// lane admits queued requests in arrival order and runs them as one wave,
+// while all of these hold:
+//   - fewer than max_inflight requests are admitted over all lanes;
+//   - the admitted estimated bytes fit in serve_mem_bytes;
+//   - the wave has at most kMultiJobs requests, and no more estimated
+//     pairs than kWavePairs beyond its first request.
+// Each request is handed out as soon as its own pairs are on the host,
+// smaller results first; its memory estimate and slot are returned then.
+// So requests that arrive while a wave runs are admitted by the other lane
+// as soon as slots and memory allow, and the two waves overlap on the
+// device.  A request's result does not depend on the wave it ran in: every
+// job has its own index, cursor, counters and output.
 #include <algorithm>
 #include <cmath>
 #include <condition_variable>
@@ -40,8 +44,14 @@ struct Request {
     int d = 0;
     double eps = 0;
     uint64_t est_bytes = 0;
+    uint64_t est_pairs = 0;
     double t_submit = 0, t_admit = 0;
 };
+
+// Estimated pairs one wave may hold beyond its first request: a very large
+// request then runs in a wave of its own while the other lane keeps
+// serving the small ones.
+constexpr uint64_t kWavePairs = 250000000ull;
 
 struct Finished {
     sj_status st = SJ_OK;
@@ -80,6 +90,49 @@ bool admissible(const Server *S) {
     return S->inflight == 0 || S->mem_in_use + S->queue.front().est_bytes <= mem_budget(S->ctx);
 }
 
+// Hands out a finished request: its result (or error) becomes visible to
+// sj_poll and its memory estimate and slot are returned.
+void finish(Server *S, Request &r, EngJob &J, sj_status st, double t_done) {
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        Finished f;
+        f.st = st;
+        f.r = st == SJ_OK ? J.res : nullptr;
+        if (st != SJ_OK && J.res) sj_result_free(J.res);
+        J.res = nullptr;
+        if (f.r) {
+            f.r->t_submit = r.t_submit;
+            f.r->t_admit = r.t_admit;
+            f.r->t_done = t_done;
+        }
+        S->done[r.ticket] = f;
+        S->pending.erase(r.ticket);
+        S->mem_in_use -= r.est_bytes;
+        S->inflight--;
+        S->info.completed++;
+        if (J.path == 2) S->info.overflow_reruns++;
+        if (J.path == 1) S->info.standalone++;
+        pinned_put(r.pts, r.pts_bytes);
+        r.pts = nullptr;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+}
+
+struct WaveState {
+    Server *S;
+    std::vector<Request> *wave;
+    std::vector<EngJob> *jobs;
+    std::vector<char> done;
+};
+
+void on_job_done(void *user, int q) {
+    WaveState *w = static_cast<WaveState *>(user);
+    if (w->done[q]) return;
+    w->done[q] = 1;
+    finish(w->S, (*w->wave)[q], (*w->jobs)[q], (*w->jobs)[q].st, secs(w->S->ctx));
+}
+
 void lane_main(Server *S, int lane) {
     cudaSetDevice(S->ctx->device);
     Engine *E = S->engines[lane];
@@ -90,10 +143,13 @@ void lane_main(Server *S, int lane) {
             S->cv_work.wait(lk, [&] { return S->stop || admissible(S); });
             if (S->stop) break;
             const double t = secs(S->ctx);
-            while (admissible(S) && (int)wave.size() < kMultiJobs) {
+            uint64_t pairs = 0;
+            while (admissible(S) && (int)wave.size() < kMultiJobs &&
+                   (wave.empty() || pairs + S->queue.front().est_pairs <= kWavePairs)) {
                 Request r = std::move(S->queue.front());
                 S->queue.pop_front();
                 r.t_admit = t;
+                pairs += r.est_pairs;
                 S->mem_in_use += r.est_bytes;
                 S->inflight++;
                 wave.push_back(std::move(r));
@@ -114,35 +170,19 @@ void lane_main(Server *S, int lane) {
             jobs[q].eps = wave[q].eps;
             ptrs.push_back(&jobs[q]);
         }
+        WaveState ws{S, &wave, &jobs, std::vector<char>(wave.size(), 0)};
         Error err;
-        const sj_status st = engine_run(err, E, ptrs.data(), (int)ptrs.size());
-        const double t_done = secs(S->ctx);
-        const EngStats es = engine_stats(E);
+        const sj_status st = engine_run(err, E, ptrs.data(), (int)ptrs.size(), on_job_done, &ws);
+        // requests the engine did not hand out (it stopped on an error)
+        for (size_t q = 0; q < wave.size(); ++q)
+            if (!ws.done[q]) {
+                ws.done[q] = 1;
+                finish(S, wave[q], jobs[q], st != SJ_OK ? st : jobs[q].st, secs(S->ctx));
+            }
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            for (size_t q = 0; q < wave.size(); ++q) {
-                Finished f;
-                f.st = st != SJ_OK ? st : jobs[q].st;
-                f.r = f.st == SJ_OK ? jobs[q].res : nullptr;
-                if (f.st != SJ_OK && jobs[q].res) sj_result_free(jobs[q].res);
-                if (f.r) {
-                    f.r->t_submit = wave[q].t_submit;
-                    f.r->t_admit = wave[q].t_admit;
-                    f.r->t_done = t_done;
-                }
-                S->done[wave[q].ticket] = f;
-                S->pending.erase(wave[q].ticket);
-                S->mem_in_use -= wave[q].est_bytes;
-                S->inflight--;
-                S->info.completed++;
-                if (jobs[q].path == 2) S->info.overflow_reruns++;
-                if (jobs[q].path == 1) S->info.standalone++;
-                pinned_put(wave[q].pts, wave[q].pts_bytes);
-            }
             S->running_waves--;
-            (void)es;
         }
-        S->cv_done.notify_all();
         S->cv_work.notify_all();
     }
 }
@@ -242,12 +282,9 @@ sj_status sj_submit(sj_ctx *ctx, const double *pts, uint64_t n, int d, double ep
     } else {
         std::memcpy(r.pts, pts, bytes);
     }
-    for (size_t i = 0; i < (size_t)n * d; ++i)
-        if (!std::isfinite(r.pts[i])) {
-            pinned_put(r.pts, r.pts_bytes);
-            return SJ_EINVAL;
-        }
-    r.est_bytes = engine_estimate(r.pts, n, d, eps, nullptr);
+    // non-finite coordinates are found by the device bounds pass; the
+    // request then finishes with SJ_EINVAL
+    r.est_bytes = engine_estimate(r.pts, n, d, eps, &r.est_pairs);
     if (r.est_bytes > mem_budget(ctx)) {
         pinned_put(r.pts, r.pts_bytes);
         return SJ_ENOMEM;
@@ -313,7 +350,13 @@ sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out) {
     out->inflight = S->inflight;
     out->mem_in_use = S->mem_in_use;
     uint64_t g = 0;
-    for (Engine *E : S->engines) g += engine_stats(E).graph_launches;
+    for (Engine *E : S->engines) {
+        const EngStats es = engine_stats(E);
+        g += es.graph_launches;
+        out->ms_bounds += es.ms_bounds;
+        out->ms_graph += es.ms_graph;
+        out->ms_output += es.ms_output;
+    }
     out->graph_launches = g;
     return SJ_OK;
 }

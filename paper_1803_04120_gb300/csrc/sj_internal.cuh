@@ -171,6 +171,7 @@ struct JoinLaunch {
     uint32_t item_stride = 1;
     int wpb = 0;                    // warps per block; 0: occupancy picks
     int nbuf = 0;                   // chunk ring depth; 0: by dimension and precision
+    int eb = 0;                     // staged pairs per warp (256/512/1024); 0: by dimension
 };
 
 // Job table of a multi-join launch, passed in the kernel parameters.
@@ -188,6 +189,10 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
                          int count_only, JoinArgs &a);
 sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb,
                       int *per_sm);
+// Work-item range [lo, hi) of shard `rank` of `world` (shard.cu): the
+// nominal split of the items moved forward to cell starts.  Synchronises s.
+sj_status shard_items(Error &err, const Index &ix, int rank, int world, cudaStream_t s,
+                      uint32_t *lo, uint32_t *hi);
 // Launch tuner (tune.cu): on a miss times sampled count-only launches of ix
 // and stores the fastest (grab, ring depth, warps per block) for the key
 // (d, precision, UNICOMP, points-per-cell bucket); *tuned = 0 defaults kept,

@@ -1,19 +1,22 @@
 // tune.cu -- launch tuner of the search-and-refine kernel.
 //
-// Three launch parameters change the speed of the join but never its
+// Four launch parameters change the speed of the join but never its
 // result: grab (the work items a warp takes from the cursor at a time: how
 // many (cell, query block) items it owns before it returns for more), the
-// depth of the per-warp ring of staged candidate chunks, and the warps per
-// block (which trades shared memory per block against blocks per SM).  Their
+// depth of the per-warp ring of staged candidate chunks, the size of the
+// per-warp pair staging area (few large flushes when hits are dense, as in
+// clustered data, against more resident warps), and the warps per block
+// (which trades shared memory per block against blocks per SM).  Their
 // best values depend on the dimension, the precision and how many points a
 // non-empty cell holds (few per cell: short candidate lists, latency-bound
 // copies; many per cell, as in clustered data: long lists, skew between
 // items).  The tuner keys its choices on (d, precision, UNICOMP, bucket)
 // with bucket = round(log2(mean points per non-empty cell)), and on a miss
-// times count-only launches of the join at hand over a fixed systematic
-// sample of its work items (the same items for every candidate), one
-// parameter after the other, keeping a change only when it is at least 3%
-// faster.  Choices are kept for the life of the process.
+// times launches of the join at hand over a fixed systematic sample of its
+// work items (the same items for every candidate; the sample's pairs are
+// written to a scratch buffer when it fits in 512 MB, else counted only),
+// one parameter after the other, keeping a change only when it is at least
+// 3% faster.  Choices are kept for the life of the process.
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -26,7 +29,7 @@ namespace sj {
 namespace {
 
 struct TuneVal {
-    int grab = 1, nbuf = 0, wpb = 0;
+    int grab = 1, nbuf = 0, wpb = 0, eb = 0;
 };
 
 std::mutex g_tune_mu;
@@ -34,6 +37,7 @@ std::map<std::tuple<int, int, int, int>, TuneVal> g_tune;
 
 constexpr uint32_t kTuneMinItems = 4096;      // smaller joins keep the defaults
 constexpr uint32_t kTuneSampleItems = 24576;  // items per timed launch
+constexpr uint64_t kTuneMaxOutBytes = 512ull << 20;  // above: time count-only launches
 
 }  // namespace
 
@@ -53,6 +57,7 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
             l.grab = it->second.grab;
             l.nbuf = it->second.nbuf;
             l.wpb = it->second.wpb;
+            l.eb = it->second.eb;
             *tuned = 1;
             return SJ_OK;
         }
@@ -67,16 +72,48 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
         cudaGetLastError();
         st = fail(err, SJ_ECUDA, "cudaEventCreate failed");
     }
-    const uint32_t stride = std::max<uint32_t>(1, ix.n_items / kTuneSampleItems);
+    uint32_t stride = std::max<uint32_t>(1, ix.n_items / kTuneSampleItems);
+    // the sample's pair count, so that the timed launches can write their
+    // pairs (the staging size only matters with the stores); a sample whose
+    // pairs exceed kTuneMaxOutBytes is thinned until they fit
+    DevBuf outb;
+    uint64_t sample_pairs = 0;
+    auto count_sample = [&](uint32_t str, uint64_t *pairs) -> sj_status {
+        JoinLaunch x = l;
+        x.item_stride = str;
+        unsigned long long h[8] = {0};
+        if (cudaMemsetAsync(m, 0, 64, s) != cudaSuccess ||
+            launch_join(err, ix, x, 0, ix.n_items, nullptr, 0, m, reinterpret_cast<uint32_t *>(m + 4),
+                        reinterpret_cast<uint32_t *>(m + 5), 1, s, nullptr, nullptr) != SJ_OK ||
+            cudaMemcpyAsync(h, m, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return err.st != SJ_OK ? err.st : fail(err, SJ_ECUDA, "tuner sample count failed");
+        }
+        *pairs = h[0];
+        return SJ_OK;
+    };
+    if (st == SJ_OK) st = count_sample(stride, &sample_pairs);
+    for (int tries = 0; st == SJ_OK && sample_pairs * 8 > kTuneMaxOutBytes && tries < 4; ++tries) {
+        const uint64_t f = (sample_pairs * 8 + kTuneMaxOutBytes - 1) / kTuneMaxOutBytes;
+        if ((uint64_t)stride * f * 64 > ix.n_items) break;   // keep at least 64 items
+        stride = (uint32_t)(stride * f);
+        st = count_sample(stride, &sample_pairs);
+    }
+    if (st == SJ_OK && sample_pairs * 8 <= kTuneMaxOutBytes) {
+        Error e2;
+        if (dev_alloc(e2, outb, std::max<uint64_t>(sample_pairs, 1) * 8, s) != SJ_OK) outb = DevBuf();
+    }
+    const int count_only = outb.p ? 0 : 1;
     auto time_it = [&](const JoinLaunch &c, double *ms) -> sj_status {
         JoinLaunch x = c;
         x.item_stride = stride;
         double best = 1e30;
         for (int rep = 0; rep < 2; ++rep) {
             SJ_CUDA_TRY(cudaMemsetAsync(m, 0, 64, s));
-            SJ_TRY(launch_join(err, ix, x, 0, ix.n_items, nullptr, 0, m,
-                               reinterpret_cast<uint32_t *>(m + 4), reinterpret_cast<uint32_t *>(m + 5),
-                               1, s, e0, e1));
+            SJ_TRY(launch_join(err, ix, x, 0, ix.n_items, static_cast<uint2 *>(outb.p),
+                               outb.p ? sample_pairs : 0, m, reinterpret_cast<uint32_t *>(m + 4),
+                               reinterpret_cast<uint32_t *>(m + 5), count_only, s, e0, e1));
             SJ_CUDA_TRY(cudaEventSynchronize(e1));
             float t = 0;
             SJ_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
@@ -111,6 +148,15 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
         st = time_it(c, &t);
         if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
     }
+    const int ebs[] = {256, 512, 1024};
+    for (int eb : ebs) {
+        if (st != SJ_OK) break;
+        JoinLaunch c = cur;
+        c.eb = eb;
+        double t = 0;
+        st = time_it(c, &t);
+        if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
+    }
     for (int w : wpbs) {
         if (st != SJ_OK) break;
         JoinLaunch c = cur;
@@ -121,12 +167,14 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    dev_free(outb, s);
     dev_free(misc, s);
     if (st != SJ_OK) return st;
     TuneVal v;
     v.grab = cur.grab;
     v.nbuf = cur.nbuf;
     v.wpb = cur.wpb;
+    v.eb = cur.eb;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = v;
@@ -134,18 +182,9 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
     l.grab = v.grab;
     l.nbuf = v.nbuf;
     l.wpb = v.wpb;
+    l.eb = v.eb;
     *tuned = 2;
     return SJ_OK;
-}
-
-void tune_lookup(const Index &ix, JoinLaunch &l) {
-    const bool f32 = l.prec_fp32 && ix.g.fp32_ok;
-    const auto key = std::make_tuple(ix.g.d, f32 ? 1 : 0, l.unicomp ? 1 : 0, tune_bucket(ix));
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(key);
-    if (it == g_tune.end()) return;
-    l.grab = it->second.grab;
-    l.nbuf = it->second.nbuf;
 }
 
 void tune_clear() {

@@ -48,7 +48,8 @@ def main(argv=None):
             ms, launches = ctx.sj_profile_read()
             st = ctx.sj_last_stats()
         print(json.dumps(dict(d=d, eps=eps, pairs=n, kernel_ms=round(ms / max(launches, 1), 4),
-                              grab=st["grab"], nbuf=st["nbuf"], wpb=st["wpb"], tuned=st["tuned"],
+                              grab=st["grab"], nbuf=st["nbuf"], wpb=st["wpb"], staging=st["staging"],
+                              tuned=st["tuned"],
                               evaluations=st["evaluations"], rechecks=st["rechecks"],
                               index_ms=round(st["ms_index"], 3))))
 

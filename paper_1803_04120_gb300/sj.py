@@ -33,7 +33,7 @@ ABI_FUNCTIONS = (
     "sj_selfjoin_count", "sj_selfjoin_stream", "sj_result_count", "sj_result_pairs",
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
-    "sj_serve_stats",
+    "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
 )
 
 
@@ -50,7 +50,8 @@ class sj_config(ctypes.Structure):
                 ("device", ctypes.c_int32), ("lookup", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("serve_mem_bytes", ctypes.c_uint64), ("grab", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("nbuf", ctypes.c_int32), ("staging", ctypes.c_int32), ("wpb", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class sj_index_desc(ctypes.Structure):
@@ -68,7 +69,8 @@ class sj_stats(ctypes.Structure):
                 ("estimate", ctypes.c_uint64), ("ms_index", ctypes.c_double),
                 ("ms_join", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64), ("grab", ctypes.c_int32),
-                ("nbuf", ctypes.c_int32), ("wpb", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+                ("nbuf", ctypes.c_int32), ("wpb", ctypes.c_int32), ("tuned", ctypes.c_int32),
+                ("staging", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class sj_job(ctypes.Structure):
@@ -83,7 +85,8 @@ class sj_serve_info(ctypes.Structure):
                 ("graph_launches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
                 ("mem_in_use", ctypes.c_uint64), ("inflight", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("max_concurrent_waves", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("ms_bounds", ctypes.c_double),
+                ("ms_graph", ctypes.c_double), ("ms_output", ctypes.c_double)]
 
 
 CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
@@ -143,6 +146,10 @@ def load(build: bool = True):
                                           P, ctypes.c_char_p, ctypes.c_size_t]),
             "sj_selfjoin_multi": (i32, [P, ctypes.POINTER(sj_job), u64, PP, ctypes.POINTER(ctypes.c_int)]),
             "sj_serve_stats": (i32, [P, ctypes.POINTER(sj_serve_info)]),
+            "sj_selfjoin_shard_device": (i32, [P, P, u64, i32, f64, i32, i32, P, u64,
+                                               ctypes.POINTER(ctypes.c_uint64), P]),
+            "sj_shard_bounds": (i32, [P, u64, i32, i32, ctypes.POINTER(ctypes.c_uint64),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -203,7 +210,7 @@ class Context:
                  out_cap_bytes: int = 2 << 30, min_batches: int = 3, sorted: bool = False,
                  device: int = 0, lookup: int = SJ_LOOKUP_AUTO, profile: bool = False,
                  max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True,
-                 grab: int = -1):
+                 grab: int = -1, nbuf: int = -1, staging: int = -1, wpb: int = -1):
         lib = load()
         cfg = sj_config()
         lib.sj_config_default(ctypes.byref(cfg))
@@ -211,7 +218,7 @@ class Context:
         cfg.out_cap_bytes, cfg.min_batches, cfg.sorted = out_cap_bytes, min_batches, int(sorted)
         cfg.device, cfg.lookup, cfg.profile = device, lookup, int(profile)
         cfg.max_inflight, cfg.serve_mem_bytes, cfg.autotune = max_inflight, serve_mem_bytes, int(autotune)
-        cfg.grab = grab
+        cfg.grab, cfg.nbuf, cfg.staging, cfg.wpb = grab, nbuf, staging, wpb
         h = ctypes.c_void_p()
         st = lib.sj_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != SJ_OK:
@@ -278,6 +285,21 @@ class Context:
         if st == SJ_EOVERFLOW and not raise_overflow:
             return int(cnt.value)
         self._check(st, "sj_selfjoin_device")
+        return int(cnt.value)
+
+    def sj_selfjoin_shard_device(self, points, eps: float, rank: int, world: int, out,
+                                 stream=None, raise_overflow: bool = True) -> int:
+        """Rank `rank` of `world`'s share of the join into a device buffer;
+        returns its pair count."""
+        p, n, d, keep = _points_ptr(points)
+        cap = 0 if out is None else out.shape[0]
+        optr = ctypes.c_void_p(out.data_ptr()) if out is not None and cap else None
+        cnt = ctypes.c_uint64(0)
+        st = self._lib.sj_selfjoin_shard_device(self._h, p, n, d, float(eps), int(rank), int(world),
+                                                optr, cap, ctypes.byref(cnt), _stream_ptr(stream))
+        if st == SJ_EOVERFLOW and not raise_overflow:
+            return int(cnt.value)
+        self._check(st, "sj_selfjoin_shard_device")
         return int(cnt.value)
 
     def sj_selfjoin_count(self, points, eps: float) -> int:
@@ -467,6 +489,18 @@ def sj_fp32_margin(d: int, eps: float, gmin, gmax):
     st = lib.sj_fp32_margin(d, float(eps), gmin.ctypes.data, gmax.ctypes.data,
                             ctypes.byref(w), ctypes.byref(lo), ctypes.byref(hi))
     return st, w.value, lo.value, hi.value
+
+
+def sj_shard_bounds(item_block, rank: int, world: int):
+    """(lo, hi) work-item range of a shard from host block indices (no device)."""
+    lib = load()
+    a = np.ascontiguousarray(item_block, dtype=np.uint32)
+    lo, hi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = lib.sj_shard_bounds(ctypes.c_void_p(a.ctypes.data) if a.size else None, a.size, int(rank),
+                             int(world), ctypes.byref(lo), ctypes.byref(hi))
+    if st != SJ_OK:
+        raise SJError(st, "sj_shard_bounds")
+    return int(lo.value), int(hi.value)
 
 
 def pairs_to_keys(pairs: np.ndarray) -> np.ndarray:

@@ -168,6 +168,15 @@ def test_serving_admission_and_errors():
         with pytest.raises(sj.SJError) as ei:
             ctx.sj_poll(987654321)
         assert ei.value.status == sj.SJ_ENOTFOUND
+        # a non-finite coordinate fails that request only, at poll time
+        bad = datagen.uniform(3000, 3, seed=44)
+        bad[5, 2] = np.inf
+        tb = ctx.sj_submit(bad, 2.0)
+        tg = ctx.sj_submit(datagen.uniform(3000, 3, seed=45), 2.0)
+        with pytest.raises(sj.SJError) as ei:
+            ctx.sj_poll(tb, wait_ms=60000)
+        assert ei.value.status == sj.SJ_EINVAL
+        assert ctx.sj_poll(tg, wait_ms=60000) is not None
 
 
 def test_serving_shutdown_with_pending_requests():
@@ -190,3 +199,33 @@ def test_tuner_keeps_results():
         n = c1.sj_selfjoin_count(pts, 0.5)
         assert c1.sj_last_stats()["tuned"] == 1
         assert n == len(r0)
+
+
+@pytest.mark.parametrize("world", [2, 3, 5])
+def test_shards_partition_the_join(world):
+    """One join split over `world` ranks (run one after another on this GPU;
+    no rank waits on another): the shards are disjoint and their union is
+    the full pair set."""
+    torch = pytest.importorskip("torch")
+    cases = [(datagen.uniform(60000, 3, seed=41), 2.5),
+             (datagen.clustered(80000, 2, seed=42), 0.3),
+             (datagen.uniform(30000, 5, seed=43), 12.0)]
+    with sj.Context() as ctx:
+        for pts_np, eps in cases:
+            pts = torch.from_numpy(pts_np).cuda()
+            n_full = ctx.sj_selfjoin_count(pts, eps)
+            full = torch.empty((n_full, 2), dtype=torch.int32, device="cuda")
+            ctx.sj_selfjoin_device(pts, eps, full)
+            parts, total = [], 0
+            for r in range(world):
+                cnt = ctx.sj_selfjoin_shard_device(pts, eps, r, world, None, raise_overflow=False)
+                out = torch.empty((max(cnt, 1), 2), dtype=torch.int32, device="cuda")
+                assert ctx.sj_selfjoin_shard_device(pts, eps, r, world, out) == cnt
+                parts.append(keys(out[:cnt].cpu().numpy()))
+                total += cnt
+            assert total == n_full
+            got = np.sort(np.concatenate(parts))
+            assert np.array_equal(got, keys(full.cpu().numpy()))
+        with pytest.raises(sj.SJError) as ei:
+            ctx.sj_selfjoin_shard_device(pts, eps, world, world, None)
+        assert ei.value.status == sj.SJ_EINVAL
