@@ -573,6 +573,59 @@ __device__ __forceinline__ void issue_chunk(const WarpSmem &ws, int sl, uint32_t
     }
 }
 
+// Chunks with at least this many pairs write them straight to the output.
+constexpr uint32_t kDirectPairs = 128;
+
+// Writes up to c hits of this lane (the lowest query bits of the first
+// non-empty candidate slots, cleared as they go) at dst[base ...] in
+// (t, lane) order: at step t the pairs (p, q) of the active lanes, then
+// their (q, p) under UNICOMP.  Global destinations are bounded by cap.
+template <int CPL, bool UNI, bool GLOBAL>
+__device__ __forceinline__ void put_hits(uint32_t (&m)[CPL], const uint32_t (&cid)[CPL],
+                                         const float *qbase, int qrs, int id_at, uint32_t c,
+                                         uint64_t base, uint2 *dst, uint64_t cap, int lane) {
+    constexpr uint32_t kPP = UNI ? 2u : 1u;
+    const unsigned lt = (1u << lane) - 1u;
+    int s_cur = 0;
+    for (uint32_t t = 0;; ++t) {
+        const bool act = t < c;
+        const unsigned bm = __ballot_sync(0xffffffffu, act);
+        if (!bm) break;
+        const uint32_t nb = __popc(bm);
+        if (act) {
+            uint32_t q = 0, cand = 0;
+#pragma unroll
+            for (int s = 0; s < CPL; ++s)
+                if (s == s_cur && m[s] == 0) ++s_cur;
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                if (s == s_cur) {
+                    q = __ffs(m[s]) - 1;
+                    m[s] &= m[s] - 1;
+                    cand = cid[s];
+                }
+            }
+            const uint32_t qid = __float_as_uint(qbase[(size_t)q * qrs + id_at]);
+            const uint64_t pos = base + __popc(bm & lt);
+            if (!GLOBAL || pos < cap) dst[pos] = make_uint2(qid, cand);
+            if (UNI && (!GLOBAL || pos + nb < cap)) dst[pos + nb] = make_uint2(cand, qid);
+        }
+        base += kPP * nb;
+    }
+}
+
+// Clears up to c hits of this lane, in the order put_hits takes them.
+template <int CPL>
+__device__ __forceinline__ void drop_hits(uint32_t (&m)[CPL], uint32_t c) {
+#pragma unroll
+    for (int s = 0; s < CPL; ++s) {
+        while (c && m[s]) {
+            m[s] &= m[s] - 1;
+            --c;
+        }
+    }
+}
+
 // Compares chunk `ch` (in ring slot r) of the item in slot `sl` with the
 // item's queries and stages the pairs found.
 template <int D, bool F32, bool UNI>
@@ -672,54 +725,36 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                 }
             }
         }
-        // 4. emission in rounds of at most kPer hits per lane.  Within a
-        //    round the t-th hit of every lane that has one goes to
-        //    consecutive staging slots (order by (t, lane)), so the stores of
-        //    one instruction hit consecutive words (no bank conflicts); the
-        //    order of pairs in the output is free.
+        // 4. emission.  The hits go out in (t, lane) order: the t-th hit of
+        //    every lane that has one goes to consecutive slots, so one store
+        //    instruction writes consecutive words (no shared-memory bank
+        //    conflicts, coalesced global stores); the order of pairs in the
+        //    output is free.  A chunk with many pairs reserves its output
+        //    once and writes it straight to global memory; a chunk with few
+        //    is staged, so the same-address reservations stay rare.
         constexpr uint32_t kPP = UNI ? 2u : 1u;
-        const uint32_t kPer = (uint32_t)a.eb / (32u * kPP);
-        const unsigned lt = (1u << lane) - 1u;
         uint32_t left = 0;
 #pragma unroll
         for (int s = 0; s < CPL; ++s) left += __popc(m[s]);
+        const uint32_t hits = __reduce_add_sync(0xffffffffu, left);
+        if (hits == 0) return;
+        if (hits * kPP >= kDirectPairs) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)hits * kPP);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (!a.count_only)
+                put_hits<CPL, UNI, true>(m, cid, qbase, a.qrs, 2 * D + 2, left, base, a.out, a.cap, lane);
+            return;
+        }
+        const uint32_t kPer = (uint32_t)a.eb / (32u * kPP);
         while (__any_sync(0xffffffffu, left)) {
             const uint32_t c = left < kPer ? left : kPer;
             const uint32_t total = __reduce_add_sync(0xffffffffu, c) * kPP;
             if (st.fill + total > (uint32_t)a.eb) flush(st, ws, a, lane);
-            uint32_t base = st.fill;
-            int s_cur = 0;
-            for (uint32_t t = 0;; ++t) {
-                const bool act = t < c;
-                const unsigned bm = __ballot_sync(0xffffffffu, act);
-                if (!bm) break;
-                const uint32_t nb = __popc(bm);
-                if (act) {
-                    // this lane's next hit: lowest query bit of the first
-                    // non-empty slot
-                    uint32_t q = 0, cand = 0;
-#pragma unroll
-                    for (int s = 0; s < CPL; ++s) {
-                        if (s == s_cur && m[s] == 0) ++s_cur;
-                    }
-#pragma unroll
-                    for (int s = 0; s < CPL; ++s) {
-                        if (s == s_cur) {
-                            q = __ffs(m[s]) - 1;
-                            m[s] &= m[s] - 1;
-                            cand = cid[s];
-                        }
-                    }
-                    if (!a.count_only) {
-                        // (p, q) of all active lanes, then their (q, p)
-                        const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + 2 * D + 2]);
-                        const uint32_t pos = base + __popc(bm & lt);
-                        ws.emit[pos] = make_uint2(qid, cand);
-                        if (UNI) ws.emit[pos + nb] = make_uint2(cand, qid);
-                    }
-                }
-                base += kPP * nb;
-            }
+            if (!a.count_only)
+                put_hits<CPL, UNI, false>(m, cid, qbase, a.qrs, 2 * D + 2, c, st.fill, ws.emit, 0, lane);
+            else
+                drop_hits<CPL>(m, c);
             left -= c;
             st.fill += total;
         }
