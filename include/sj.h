@@ -121,9 +121,10 @@ typedef struct {
      * library (or the tuner, with autotune = 1) choose */
     int32_t grab;            /* work items a warp takes per cursor bump */
     int32_t nbuf;            /* candidate-chunk ring depth (2..8) */
-    int32_t staging;         /* staged pairs per warp (256, 512 or 1024) */
+    int32_t staging;         /* staged pairs per warp (128, 256, 512 or 1024) */
     int32_t wpb;             /* warps per block (1, 2, 4 or 8) */
-    int32_t reserved[4];
+    int32_t slots;           /* work items a warp holds at once (1 or 2) */
+    int32_t reserved[3];
 } sj_config;
 
 /* Fills *cfg with the defaults listed above. */

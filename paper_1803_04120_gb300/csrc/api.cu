@@ -213,10 +213,13 @@ JoinLaunch default_launch(const sj_ctx *ctx) {
     l.nbuf = ctx->cfg.nbuf > 0 ? ctx->cfg.nbuf : 0;
     l.eb = ctx->cfg.staging > 0 ? ctx->cfg.staging : 0;
     l.wpb = ctx->cfg.wpb > 0 ? ctx->cfg.wpb : 0;
+    l.slots = ctx->cfg.slots > 0 ? ctx->cfg.slots : 0;
     return l;
 }
 
-bool launch_forced(const sj_config &c) { return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.wpb > 0; }
+bool launch_forced(const sj_config &c) {
+    return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.wpb > 0 || c.slots > 0;
+}
 
 JoinLaunch launch_cfg(const sj_ctx *ctx) { return ctx->launch; }
 
@@ -570,6 +573,7 @@ void sj_config_default(sj_config *cfg) {
     cfg->nbuf = -1;
     cfg->staging = -1;
     cfg->wpb = -1;
+    cfg->slots = -1;
 }
 
 const char *sj_status_str(sj_status st) {

@@ -66,6 +66,10 @@ __host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >
 // data: 27.7 ms with 256 against 13.1 ms with 512); at higher d a smaller
 // one leaves room for warps (the tuner may still choose more).
 __host__ __device__ constexpr int emit_for(int d, bool f32) { return (f32 && d >= 4) ? 256 : 512; }
+// Item slots per warp: at d >= 4 an item spans tens of chunks, so
+// preparing the next item ahead buys little and its shared memory is worth
+// more as resident warps.
+__host__ __device__ constexpr int slots_for(int d, bool f32) { return (f32 && d >= 4) ? 1 : 2; }
 // Minimum resident blocks of 256 threads the compiler sizes registers for.
 __host__ __device__ constexpr int minb_for(int d, bool f32) { return f32 ? (d <= 2 ? 1 : (d == 3 ? 3 : 2)) : 1; }
 
@@ -276,16 +280,19 @@ __device__ __forceinline__ WarpSmem carve(unsigned char *base, const JoinArgs &a
     unsigned char *p = base + (size_t)warp * a.sm_warp;
     w.bar = reinterpret_cast<uint64_t *>(p);
     p += 64;
+    // one or two item slots (the second lets the producer prepare the next
+    // item while the consumer still works on the current one)
+    const int two = a.slots > 1 ? 1 : 0;
     w.hdr = reinterpret_cast<ItemHdr *>(p);
-    p += 2 * sizeof(ItemHdr);
+    p += (1 + two) * sizeof(ItemHdr);
     w.ranges[0] = reinterpret_cast<uint2 *>(p);
     p += a.sm_ranges;
-    w.ranges[1] = reinterpret_cast<uint2 *>(p);
-    p += a.sm_ranges;
+    w.ranges[1] = reinterpret_cast<uint2 *>(p - (two ? 0 : a.sm_ranges));
+    p += two * a.sm_ranges;
     w.q[0] = p;
     p += a.sm_queries;
-    w.q[1] = p;
-    p += a.sm_queries;
+    w.q[1] = p - (two ? 0 : a.sm_queries);
+    p += two * a.sm_queries;
     w.ring = p;
     p += (size_t)nbuf * a.sm_chunk;
     w.emit = reinterpret_cast<uint2 *>(p);
@@ -296,7 +303,7 @@ __device__ __forceinline__ WarpSmem carve(unsigned char *base, const JoinArgs &a
 struct Pipe {
     uint32_t grab_pos, grab_end;   // work-cursor positions taken by this warp
     uint32_t issued, consumed;     // chunks
-    uint32_t prod_seq, cons_seq;   // item sequence numbers (slot = seq & 1)
+    uint32_t prod_seq, cons_seq;   // item sequence numbers (slot = seq & smask)
     uint32_t p_chunk, c_chunk;
     uint32_t rcur;                 // producer's range cursor
     uint32_t fill;                 // staged pairs
@@ -819,6 +826,7 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     constexpr int CPL = cpl_for(D, F32);
     constexpr int CB = 32 * CPL;
     const uint32_t nbuf = (uint32_t)a.nbuf;   // chunk ring depth (launch parameter)
+    const uint32_t smask = a.slots > 1 ? 1u : 0u;   // item slot of a sequence number
     typedef typename std::conditional<F32, float, double>::type T;
     const WarpSmem ws = carve(smem, a, warp, nbuf);
     const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
@@ -854,17 +862,18 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
             // producer: keep up to nbuf chunks in flight, crossing into the
             // next item (at most one item ahead of the consumer)
             while (st.issued - st.consumed < nbuf) {
-                const int ps = st.prod_seq & 1;
+                const int ps = st.prod_seq & smask;
                 if (st.p_chunk == ws.hdr[ps].nchunks) {
-                    // the other item slot is free once the consumer has
-                    // reached the producer's item
-                    if (st.prod_done || st.prod_seq > st.cons_seq) break;
+                    // a slot is free once the consumer has left its item:
+                    // with two slots the producer runs one item ahead,
+                    // with one it waits for the consumer to finish
+                    if (st.prod_done || st.prod_seq + 1 >= st.cons_seq + (uint32_t)a.slots) break;
                     if (!fetch_item(st, a, item_end, lane, it)) {
                         st.prod_done = true;
                         break;
                     }
                     ++st.prod_seq;
-                    prepare_item<D, F32, UNI>(ws, st.prod_seq & 1, it, a, n_cells, lane, evals);
+                    prepare_item<D, F32, UNI>(ws, st.prod_seq & smask, it, a, n_cells, lane, evals);
                     st.p_chunk = 0;
                     st.rcur = 0;
                     continue;
@@ -885,10 +894,10 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                     (void)mbar_wait_bounded(&ws.bar[k % nbuf], (k / nbuf) & 1u, a.timeout_ns);
                 break;
             }
-            consume_chunk<D, F32, UNI>(st, ws, st.cons_seq & 1, st.c_chunk, r, a, lane, rechecks);
+            consume_chunk<D, F32, UNI>(st, ws, st.cons_seq & smask, st.c_chunk, r, a, lane, rechecks);
             ++st.consumed;
             ++st.c_chunk;
-            if (st.c_chunk == ws.hdr[st.cons_seq & 1].nchunks) {
+            if (st.c_chunk == ws.hdr[st.cons_seq & smask].nchunks) {
                 ++st.cons_seq;
                 st.c_chunk = 0;
             }
@@ -1070,13 +1079,14 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.sm_ranges = round16(a.n_templates * (int)sizeof(uint2));
     a.sm_queries = round16(kQueryBlock * a.qrs * esz);
     a.sm_chunk = round16(a.cb * rsb);
-    // staging area: the launch's choice (256, 512 or 1024 pairs) or by d
-    a.eb = (cfg.eb == 256 || cfg.eb == 512 || cfg.eb == 1024) ? cfg.eb : emit_for(d, f32);
+    // staging area: the launch's choice (128 .. 1024 pairs) or by d
+    a.eb = (cfg.eb == 128 || cfg.eb == 256 || cfg.eb == 512 || cfg.eb == 1024) ? cfg.eb : emit_for(d, f32);
     a.sm_emit = round16(a.eb * (int)sizeof(uint2));
     // ring depth: the launch's choice (2..8 chunks; the warp has 8 mbarriers)
     a.nbuf = (cfg.nbuf >= 2 && cfg.nbuf <= 8) ? cfg.nbuf : nbuf_for(d, f32);
-    a.sm_warp = 64 + round16(2 * (int)sizeof(ItemHdr)) + 2 * a.sm_ranges + 2 * a.sm_queries +
-                a.nbuf * a.sm_chunk + a.sm_emit;
+    a.slots = (cfg.slots == 1 || cfg.slots == 2) ? cfg.slots : slots_for(d, f32);
+    a.sm_warp = 64 + round16(a.slots * (int)sizeof(ItemHdr)) + a.slots * a.sm_ranges +
+                a.slots * a.sm_queries + a.nbuf * a.sm_chunk + a.sm_emit;
     a.timeout_ns = 2000000000ull;
     a.d = d;
     a.f32 = f32 ? 1 : 0;

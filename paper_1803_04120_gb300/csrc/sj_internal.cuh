@@ -155,6 +155,7 @@ struct JoinArgs {
     int cb;                         // candidates per chunk
     int eb;                         // emission staging entries
     int nbuf;                       // chunk ring depth (2..8)
+    int slots;                      // item slots per warp (1 or 2)
     uint64_t timeout_ns;
     // multi-join launches: the dimension and precision of this job and its
     // device counters (|G|, work items) in place of the kernel argument
@@ -171,7 +172,8 @@ struct JoinLaunch {
     uint32_t item_stride = 1;
     int wpb = 0;                    // warps per block; 0: occupancy picks
     int nbuf = 0;                   // chunk ring depth; 0: by dimension and precision
-    int eb = 0;                     // staged pairs per warp (256/512/1024); 0: by dimension
+    int eb = 0;                     // staged pairs per warp (128..1024); 0: by dimension
+    int slots = 0;                  // item slots per warp (1 or 2); 0: by dimension
 };
 
 // Job table of a multi-join launch, passed in the kernel parameters.

@@ -1,11 +1,12 @@
 // tune.cu -- launch tuner of the search-and-refine kernel.
 //
-// Four launch parameters change the speed of the join but never its
+// Five launch parameters change the speed of the join but never its
 // result: grab (the work items a warp takes from the cursor at a time: how
 // many (cell, query block) items it owns before it returns for more), the
-// depth of the per-warp ring of staged candidate chunks, the size of the
-// per-warp pair staging area (few large flushes when hits are dense, as in
-// clustered data, against more resident warps), and the warps per block
+// depth of the per-warp ring of staged candidate chunks, the item slots per
+// warp (preparing the next item ahead against shared memory), the size of
+// the per-warp pair staging area (few large flushes when hits are dense, as
+// in clustered data, against more resident warps), and the warps per block
 // (which trades shared memory per block against blocks per SM).  Their
 // best values depend on the dimension, the precision and how many points a
 // non-empty cell holds (few per cell: short candidate lists, latency-bound
@@ -29,7 +30,7 @@ namespace sj {
 namespace {
 
 struct TuneVal {
-    int grab = 1, nbuf = 0, wpb = 0, eb = 0;
+    int grab = 1, nbuf = 0, wpb = 0, eb = 0, slots = 0;
 };
 
 std::mutex g_tune_mu;
@@ -58,6 +59,7 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
             l.nbuf = it->second.nbuf;
             l.wpb = it->second.wpb;
             l.eb = it->second.eb;
+            l.slots = it->second.slots;
             *tuned = 1;
             return SJ_OK;
         }
@@ -148,6 +150,15 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
         st = time_it(c, &t);
         if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
     }
+    const int slotss[] = {1, 2};
+    for (int sl : slotss) {
+        if (st != SJ_OK) break;
+        JoinLaunch c = cur;
+        c.slots = sl;
+        double t = 0;
+        st = time_it(c, &t);
+        if (st == SJ_OK && t < 0.97 * t_cur) { cur = c; t_cur = t; }
+    }
     const int ebs[] = {256, 512, 1024};
     for (int eb : ebs) {
         if (st != SJ_OK) break;
@@ -175,6 +186,7 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
     v.nbuf = cur.nbuf;
     v.wpb = cur.wpb;
     v.eb = cur.eb;
+    v.slots = cur.slots;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = v;
@@ -183,6 +195,7 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
     l.nbuf = v.nbuf;
     l.wpb = v.wpb;
     l.eb = v.eb;
+    l.slots = v.slots;
     *tuned = 2;
     return SJ_OK;
 }

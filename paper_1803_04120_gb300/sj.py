@@ -51,7 +51,7 @@ class sj_config(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("serve_mem_bytes", ctypes.c_uint64), ("grab", ctypes.c_int32),
                 ("nbuf", ctypes.c_int32), ("staging", ctypes.c_int32), ("wpb", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class sj_index_desc(ctypes.Structure):
@@ -210,7 +210,8 @@ class Context:
                  out_cap_bytes: int = 2 << 30, min_batches: int = 3, sorted: bool = False,
                  device: int = 0, lookup: int = SJ_LOOKUP_AUTO, profile: bool = False,
                  max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True,
-                 grab: int = -1, nbuf: int = -1, staging: int = -1, wpb: int = -1):
+                 grab: int = -1, nbuf: int = -1, staging: int = -1, wpb: int = -1,
+                 slots: int = -1):
         lib = load()
         cfg = sj_config()
         lib.sj_config_default(ctypes.byref(cfg))
@@ -218,7 +219,7 @@ class Context:
         cfg.out_cap_bytes, cfg.min_batches, cfg.sorted = out_cap_bytes, min_batches, int(sorted)
         cfg.device, cfg.lookup, cfg.profile = device, lookup, int(profile)
         cfg.max_inflight, cfg.serve_mem_bytes, cfg.autotune = max_inflight, serve_mem_bytes, int(autotune)
-        cfg.grab, cfg.nbuf, cfg.staging, cfg.wpb = grab, nbuf, staging, wpb
+        cfg.grab, cfg.nbuf, cfg.staging, cfg.wpb, cfg.slots = grab, nbuf, staging, wpb, slots
         h = ctypes.c_void_p()
         st = lib.sj_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != SJ_OK:
