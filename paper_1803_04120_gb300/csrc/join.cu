@@ -47,6 +47,7 @@
 #include <algorithm>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "sj_internal.cuh"
 
@@ -182,59 +183,33 @@ __device__ __forceinline__ bool exact_member(const double *__restrict__ a,
     return s <= E2;
 }
 
-// Powers of three for decoding row templates.
-__constant__ uint32_t c_pow3[kMaxDim + 1] = {1, 3, 9, 27, 81, 243, 729, 2187, 6561};
-
-// Row template t of the search, for a query cell with coordinates c:
-// outputs the x range [xlo, xhi] and the coordinates b of dimensions
-// 1..D-1, or false when the template is inactive or leaves the grid.
+// Row templates of the search, precomputed on the host per (d, UNICOMP)
+// and read with one load per template.  Entry t describes template t
+// relative to the query cell c:
+//   bits 0-1  x range: 0 the home cell only, 1 x - 1 only, 2 x + 1 only,
+//             3 x - 1 .. x + 1;
+//   bits 2-5  gate: the template is active when bit `gate` of the cell's
+//             odd-coordinate mask is set (gate < 8), always (gate = 8);
+//   bits 6-19 offset + 1 of dimensions 2..d (2 bits each).
 //   UNICOMP: t = 0 home cell; t = 1, 2 stage 0 (x - 1, x + 1); then, for
-//   stage k = 1..D-1, 2 * 3^(k-1) rows with dimension k at c_k -+ 1,
+//   stage k = 1..d-1, 2 * 3^(k-1) rows with dimension k at c_k -+ 1,
 //   dimensions 1..k-1 anywhere in c -+ 1, dimensions above k equal to c.
 //   Stage k is active when c_k is odd (Section V-B, generalised to n
-//   dimensions).  Full search: t in [0, 3^(D-1)) enumerates all rows.
+//   dimensions).  Full search: t in [0, 3^(d-1)) enumerates all rows.
+constexpr int kTemplateEntries = 6576;   // sum over d = 1..8 of both tables
+__device__ uint32_t g_templates[kTemplateEntries];
+
 template <int D, bool UNI>
 __device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, const JoinArgs &a,
                                        int32_t &xlo, int32_t &xhi, int32_t *b) {
+    const uint32_t e = __ldg(&a.tmpl[t]);
+    const uint32_t gate = (e >> 2) & 15u;
+    if (gate < 8 && !((odd >> gate) & 1u)) return false;
+    const uint32_t xm = e & 3u;
+    xlo = c[0] + (xm == 2 ? 1 : (xm == 0 ? 0 : -1));
+    xhi = c[0] + (xm == 1 ? -1 : (xm == 0 ? 0 : 1));
 #pragma unroll
-    for (int j = 1; j < D; ++j) b[j] = c[j];
-    xlo = c[0] - 1;
-    xhi = c[0] + 1;
-    if (UNI) {
-        if (t == 0) {
-            xlo = xhi = c[0];
-        } else if (t <= 2) {
-            if (!(odd & 1u)) return false;
-            xlo = xhi = (t == 1) ? c[0] - 1 : c[0] + 1;
-        } else {
-            const uint32_t u = (uint32_t)t - 3;
-            int k = 1;
-#pragma unroll
-            for (int kk = 1; kk < D; ++kk)
-                if (u >= c_pow3[kk] - 1) k = kk + 1;
-            if (k >= D) return false;
-            if (!((odd >> k) & 1u)) return false;
-            const uint32_t p = c_pow3[k - 1];
-            const uint32_t v = u - (p - 1);
-            uint32_t rem = v % p;
-#pragma unroll
-            for (int j = 1; j < D; ++j) {
-                if (j < k) {
-                    b[j] = c[j] + (int32_t)(rem % 3) - 1;
-                    rem /= 3;
-                } else if (j == k) {
-                    b[j] = c[j] + ((v / p) ? 1 : -1);
-                }
-            }
-        }
-    } else {
-        uint32_t rem = (uint32_t)t;
-#pragma unroll
-        for (int j = 1; j < D; ++j) {
-            b[j] = c[j] + (int32_t)(rem % 3) - 1;
-            rem /= 3;
-        }
-    }
+    for (int j = 1; j < D; ++j) b[j] = c[j] + (int32_t)((e >> (6 + 2 * (j - 1))) & 3u) - 1;
     if (xlo < 0) xlo = 0;
     if (xhi > a.ng[0] - 1) xhi = a.ng[0] - 1;
     if (xlo > xhi) return false;
@@ -1029,6 +1004,86 @@ sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, in
 
 const void *multi_join_fn() { return reinterpret_cast<const void *>(multi_join_kernel); }
 
+namespace {
+
+// Entry t of the template table of (d, UNICOMP); see g_templates.
+uint32_t template_entry(int d, bool uni, uint32_t t) {
+    uint32_t pow3[kMaxDim + 1];
+    pow3[0] = 1;
+    for (int j = 1; j <= kMaxDim; ++j) pow3[j] = 3 * pow3[j - 1];
+    int dy[kMaxDim] = {0};
+    uint32_t xm = 3, gate = 8;
+    if (uni) {
+        if (t == 0) {
+            xm = 0;
+        } else if (t <= 2) {
+            xm = t;            // 1: x - 1, 2: x + 1
+            gate = 0;
+        } else {
+            const uint32_t u = t - 3;
+            int k = 1;
+            for (int kk = 1; kk < d; ++kk)
+                if (u >= pow3[kk] - 1) k = kk + 1;
+            gate = (uint32_t)k;
+            const uint32_t p = pow3[k - 1];
+            const uint32_t v = u - (p - 1);
+            uint32_t rem = v % p;
+            for (int j = 1; j < k; ++j) {
+                dy[j] = (int)(rem % 3) - 1;
+                rem /= 3;
+            }
+            dy[k] = (v / p) ? 1 : -1;
+        }
+    } else {
+        uint32_t rem = t;
+        for (int j = 1; j < d; ++j) {
+            dy[j] = (int)(rem % 3) - 1;
+            rem /= 3;
+        }
+    }
+    uint32_t e = xm | (gate << 2);
+    for (int j = 1; j < d; ++j) e |= (uint32_t)(dy[j] + 1) << (6 + 2 * (j - 1));
+    return e;
+}
+
+uint32_t template_offset(int d, bool uni) {
+    uint32_t off = 0;
+    for (int dd = 1; dd <= kMaxDim; ++dd)
+        for (int u = 0; u < 2; ++u) {
+            if (dd == d && (u == 1) == uni) return off;
+            off += (uint32_t)n_templates(dd, u == 1);
+        }
+    return off;
+}
+
+std::mutex g_tmpl_mu;
+const uint32_t *g_tmpl_dev[64] = {nullptr};
+
+// Device address of the template table of (d, UNICOMP) on the current
+// device; the tables are written on the first use on each device.
+sj_status template_table(Error &err, int d, bool uni, const uint32_t **out) {
+    int dev = 0;
+    SJ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(err, SJ_ECUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_tmpl_mu);
+    if (!g_tmpl_dev[dev]) {
+        std::vector<uint32_t> h;
+        h.reserve(kTemplateEntries);
+        for (int dd = 1; dd <= kMaxDim; ++dd)
+            for (int u = 0; u < 2; ++u)
+                for (int t = 0; t < n_templates(dd, u == 1); ++t) h.push_back(template_entry(dd, u == 1, t));
+        if (h.size() != (size_t)kTemplateEntries) return fail(err, SJ_ECUDA, "template table size");
+        SJ_CUDA_TRY(cudaMemcpyToSymbol(g_templates, h.data(), h.size() * sizeof(uint32_t)));
+        void *p = nullptr;
+        SJ_CUDA_TRY(cudaGetSymbolAddress(&p, g_templates));
+        g_tmpl_dev[dev] = static_cast<const uint32_t *>(p);
+    }
+    *out = g_tmpl_dev[dev] + template_offset(d, uni);
+    return SJ_OK;
+}
+
+}  // namespace
+
 sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                          uint32_t item_end, uint2 *out, uint64_t cap,
                          unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
@@ -1055,6 +1110,7 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.dense = ix.dense;
     a.rs = f32 ? ix.rs32 : ix.rs64;
     a.n_templates = n_templates(d, uni);
+    SJ_TRY(template_table(err, d, uni, &a.tmpl));
     for (int j = 0; j < d; ++j) {
         a.ng[j] = (int32_t)g.ng[j];
         a.stride[j] = g.stride[j];

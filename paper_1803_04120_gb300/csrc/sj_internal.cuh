@@ -136,6 +136,7 @@ struct JoinArgs {
     int dense;
     int rs;                         // record stride in elements of the mode's type
     int n_templates;
+    const uint32_t *tmpl;           // row templates of (d, UNICOMP), device memory
     int32_t ng[kMaxDim];
     uint64_t stride[kMaxDim];
     float lo32, hi32;
