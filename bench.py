@@ -18,6 +18,8 @@ Printed JSON line (rank 0):
   cpu_baseline the CPU oracle on the host cores, on a bounded sample
   skew         clustered 5,000,000 points (d = 2, 3, eps = 0.5): device join
                with the tuned launch parameters against the fixed defaults
+  ablation     the join kernel with and without UNICOMP, and the indexed
+               join against the index-free brute-force comparator
   serving      a stream of join requests (n log-uniform in [1e3, 1e6],
                d in 2..6, 8..128 mean neighbours) through sj_submit/sj_poll,
                all at once (saturated) and with Poisson arrivals at half the
@@ -220,6 +222,71 @@ def skew_bench(dev: int, reps: int):
         c1.close()
         torch.cuda.empty_cache()
     return out
+
+
+# ---------------------------------------------------------------- ablation
+
+def ablation_bench(dev: int, reps: int):
+    """What the index and UNICOMP save: the join kernel with and without
+    UNICOMP on the 2,000,000-point workload, and the indexed join against
+    the index-free brute-force comparator on config 1 and on 100,000-point
+    uniform sets."""
+    import torch
+    from paper_1803_04120_gb300 import sj
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    uni = []
+    for d in DIMS:
+        cfg = datagen.config2(d)
+        pts = torch.from_numpy(datagen.make_points(cfg)).cuda()
+        row = {"d": d}
+        for flag in (1, 0):
+            with sj.Context(unicomp=bool(flag), profile=True, device=dev) as c:
+                n = c.sj_selfjoin_count(pts, cfg["eps"])
+                out = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+                c.sj_selfjoin_device(pts, cfg["eps"], out)
+                c.sj_profile_read()
+                for _ in range(reps):
+                    c.sj_selfjoin_device(pts, cfg["eps"], out)
+                ms, nl = c.sj_profile_read()
+                st = c.sj_last_stats()
+                key = "unicomp" if flag else "full_search"
+                row[key] = {"kernel_ms": round(ms / max(nl, 1), 3), "evaluations": st["evaluations"]}
+                del out
+        row["time_ratio"] = round(row["full_search"]["kernel_ms"] / row["unicomp"]["kernel_ms"], 3)
+        row["evaluation_ratio"] = round(row["full_search"]["evaluations"] / row["unicomp"]["evaluations"], 3)
+        uni.append(row)
+    brute = []
+    cases = [("config 1: 20,000 points, d=2, eps=2", datagen.make_points(datagen.CONFIG1),
+              datagen.CONFIG1["eps"])]
+    for d in (2, 4, 6):
+        cases.append((f"100,000 uniform points, d={d}, 64 neighbours", datagen.uniform(100000, d, 70 + d),
+                      datagen.eps_for_neighbors(100000, d, 64)))
+    with sj.Context(device=dev) as c:
+        for name, pts_np, eps in cases:
+            pts = torch.from_numpy(pts_np).cuda()
+            n = c.sj_selfjoin_count(pts, eps)
+            out = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+            t_idx = timed(lambda: c.sj_selfjoin_device(pts, eps, out))
+            t_bf = timed(lambda: c.sj_selfjoin_bruteforce_device(pts, eps, out))
+            brute.append({"workload": name, "pairs": n, "indexed_ms": round(t_idx, 3),
+                          "bruteforce_ms": round(t_bf, 3), "speedup": round(t_bf / t_idx, 1)})
+    return {"unicomp_vs_full_search": uni, "index_vs_bruteforce": brute,
+            "note": "join kernel only for UNICOMP; whole device call (index build included) "
+                    "for the brute-force comparison"}
 
 
 # ---------------------------------------------------------------- serving
@@ -450,6 +517,8 @@ def run_gpu(args):
         line["serving"] = serving_bench(dev, args.serve_requests)
     if not args.no_skew:
         line["skew"] = skew_bench(dev, max(1, min(args.steps, 3)))
+    if not args.no_ablation:
+        line["ablation"] = ablation_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_cpu:
         v, cores, desc = cpu_oracle_sample(data, args.cpu_budget)
         line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -508,6 +577,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving stream (0: skip)")
     ap.add_argument("--no-skew", action="store_true", help="skip the clustered workload")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the UNICOMP and brute-force comparisons")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -520,7 +591,7 @@ def main():
         # replicas: each rank runs the same workload on its own GPU; the
         # whole-job value is the sum over ranks of pairs over the max time
         # (the serving and clustered sections are single-GPU measurements)
-        args.serve_requests, args.no_skew = 0, True
+        args.serve_requests, args.no_skew, args.no_ablation = 0, True, True
         import torch.distributed as dist
         dist.init_process_group("nccl")
         args.no_cpu = args.no_cpu or rank != 0

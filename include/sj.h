@@ -232,6 +232,17 @@ SJ_API sj_status sj_selfjoin_index_device(sj_ctx *ctx, const sj_index *idx,
                                    uint32_t *d_pairs, uint64_t cap_pairs,
                                    uint64_t *count, void *stream);
 
+/* The index-free comparator: every ordered pair (i, j) is tested with the
+ * exact FP64 predicate (no grid, no UNICOMP, no FP32 filter), O(n^2)
+ * evaluations.  It returns the same pair set as sj_selfjoin_device and
+ * exists to measure what the grid index of Section IV and the
+ * duplicate-search removal of Section V-B save (the paper compares its
+ * indexed GPU join with a brute-force GPU join).  Arguments, output and
+ * errors as sj_selfjoin_device. */
+SJ_API sj_status sj_selfjoin_bruteforce_device(sj_ctx *ctx, const double *pts, uint64_t n, int d,
+                                               double eps, uint32_t *d_pairs, uint64_t cap_pairs,
+                                               uint64_t *count, void *stream);
+
 /* Counts the pairs without writing them. */
 SJ_API sj_status sj_selfjoin_count(sj_ctx *ctx, const double *pts, uint64_t n, int d,
                             double eps, uint64_t *count);

@@ -788,6 +788,44 @@ sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, i
     return sc.done(st);
 }
 
+sj_status sj_selfjoin_bruteforce_device(sj_ctx *ctx, const double *pts, uint64_t n, int d, double eps,
+                                        uint32_t *d_pairs, uint64_t cap_pairs, uint64_t *count,
+                                        void *stream) {
+    if (!ctx || !count) return SJ_EINVAL;
+    Scoped sc(ctx);
+    reset_stats(ctx);
+    sj_status st = check_args(sc.err, pts, n, d, eps);
+    if (st != SJ_OK) return sc.done(st);
+    if (!d_pairs && cap_pairs) return sc.done(fail(sc.err, SJ_EINVAL, "d_pairs is NULL"));
+    if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double t0 = now_ms();
+    Error &err = sc.err;
+    DevBuf dp;
+    auto run = [&]() -> sj_status {
+        SJ_TRY(dev_alloc(err, dp, n * d * sizeof(double), s));
+        SJ_CUDA_TRY(cudaMemcpyAsync(dp.p, pts, n * d * sizeof(double), cudaMemcpyDefault, s));
+        unsigned long long *m = misc_dev(ctx);
+        SJ_CUDA_TRY(cudaMemsetAsync(m, 0, kMiscWords * sizeof(unsigned long long), s));
+        SJ_TRY(brute_join(err, static_cast<const double *>(dp.p), n, d, eps,
+                          reinterpret_cast<uint2 *>(d_pairs), cap_pairs, m + kMiscCounter, s));
+        SJ_CUDA_TRY(cudaMemcpyAsync(ctx->h_misc, m, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        SJ_CUDA_TRY(cudaStreamSynchronize(s));
+        return SJ_OK;
+    };
+    st = run();
+    dev_free(dp, s);
+    if (st == SJ_OK) {
+        *count = ctx->h_misc[0];
+        ctx->stats.pairs = *count;
+        ctx->stats.evaluations = n * n;
+        ctx->stats.batches = 1;
+        ctx->stats.ms_total = now_ms() - t0;
+        if (*count > cap_pairs) st = fail(err, SJ_EOVERFLOW, "output buffer too small for the pair count");
+    }
+    return sc.done(st);
+}
+
 sj_status sj_selfjoin_index_device(sj_ctx *ctx, const sj_index *idx, uint32_t *d_pairs,
                                    uint64_t cap_pairs, uint64_t *count, void *stream) {
     if (!ctx || !idx || !count) return SJ_EINVAL;

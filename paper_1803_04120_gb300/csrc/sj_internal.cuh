@@ -192,6 +192,10 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
                          int count_only, JoinArgs &a);
 sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb,
                       int *per_sm);
+// Index-free comparator (brute.cu): every ordered pair with the exact FP64
+// predicate; *d_counter accumulates the member count.
+sj_status brute_join(Error &err, const double *d_pts, uint64_t n, int d, double eps, uint2 *out,
+                     uint64_t cap, unsigned long long *d_counter, cudaStream_t s);
 // Work-item range [lo, hi) of shard `rank` of `world` (shard.cu): the
 // nominal split of the items moved forward to cell starts.  Synchronises s.
 sj_status shard_items(Error &err, const Index &ix, int rank, int world, cudaStream_t s,

@@ -34,6 +34,7 @@ ABI_FUNCTIONS = (
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
+    "sj_selfjoin_bruteforce_device",
 )
 
 
@@ -150,6 +151,8 @@ def load(build: bool = True):
                                                ctypes.POINTER(ctypes.c_uint64), P]),
             "sj_shard_bounds": (i32, [P, u64, i32, i32, ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_uint64)]),
+            "sj_selfjoin_bruteforce_device": (i32, [P, P, u64, i32, f64, P, u64,
+                                                    ctypes.POINTER(ctypes.c_uint64), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -301,6 +304,20 @@ class Context:
         if st == SJ_EOVERFLOW and not raise_overflow:
             return int(cnt.value)
         self._check(st, "sj_selfjoin_shard_device")
+        return int(cnt.value)
+
+    def sj_selfjoin_bruteforce_device(self, points, eps: float, out, stream=None,
+                                      raise_overflow: bool = True) -> int:
+        """The index-free O(n^2) comparator into a device buffer."""
+        p, n, d, keep = _points_ptr(points)
+        cap = 0 if out is None else out.shape[0]
+        optr = ctypes.c_void_p(out.data_ptr()) if out is not None and cap else None
+        cnt = ctypes.c_uint64(0)
+        st = self._lib.sj_selfjoin_bruteforce_device(self._h, p, n, d, float(eps), optr, cap,
+                                                     ctypes.byref(cnt), _stream_ptr(stream))
+        if st == SJ_EOVERFLOW and not raise_overflow:
+            return int(cnt.value)
+        self._check(st, "sj_selfjoin_bruteforce_device")
         return int(cnt.value)
 
     def sj_selfjoin_count(self, points, eps: float) -> int:

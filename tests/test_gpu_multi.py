@@ -229,3 +229,20 @@ def test_shards_partition_the_join(world):
         with pytest.raises(sj.SJError) as ei:
             ctx.sj_selfjoin_shard_device(pts, eps, world, world, None)
         assert ei.value.status == sj.SJ_EINVAL
+
+
+def test_bruteforce_comparator_matches_oracle():
+    torch = pytest.importorskip("torch")
+    cases = [(datagen.make_points(datagen.CONFIG1), datagen.CONFIG1["eps"])]
+    rng = np.random.default_rng(9)
+    for d in range(1, 9):
+        pts = rng.uniform(0, 10, size=(int(rng.integers(1, 3000)), d))
+        cases.append((pts, float(rng.uniform(0.5, 3.0))))
+    with sj.Context() as ctx:
+        for pts, eps in cases:
+            t = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+            n = ctx.sj_selfjoin_bruteforce_device(t, eps, None, raise_overflow=False)
+            out = torch.empty((max(n, 1), 2), dtype=torch.int32, device="cuda")
+            assert ctx.sj_selfjoin_bruteforce_device(t, eps, out) == n
+            assert ctx.sj_last_stats()["evaluations"] == len(pts) ** 2
+            assert np.array_equal(keys(out[:n].cpu().numpy()), oracle_keys(pts, eps)), pts.shape
