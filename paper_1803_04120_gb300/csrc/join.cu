@@ -561,33 +561,35 @@ constexpr uint32_t kDirectPairs = 128;
 // Writes up to c hits of this lane (the lowest query bits of the first
 // non-empty candidate slots, cleared as they go) at dst[base ...] in
 // (t, lane) order: at step t the pairs (p, q) of the active lanes, then
-// their (q, p) under UNICOMP.  Global destinations are bounded by cap.
+// their (q, p) under UNICOMP.  Lane l holds the id of query l in qid_l; the
+// query id of a hit comes by shuffle.  Global destinations are bounded by
+// cap.
 template <int CPL, bool UNI, bool GLOBAL>
 __device__ __forceinline__ void put_hits(uint32_t (&m)[CPL], const uint32_t (&cid)[CPL],
-                                         const float *qbase, int qrs, int id_at, uint32_t c,
-                                         uint64_t base, uint2 *dst, uint64_t cap, int lane) {
+                                         uint32_t qid_l, uint32_t c, uint64_t base, uint2 *dst,
+                                         uint64_t cap, int lane) {
     constexpr uint32_t kPP = UNI ? 2u : 1u;
     const unsigned lt = (1u << lane) - 1u;
-    int s_cur = 0;
     for (uint32_t t = 0;; ++t) {
         const bool act = t < c;
         const unsigned bm = __ballot_sync(0xffffffffu, act);
         if (!bm) break;
         const uint32_t nb = __popc(bm);
-        if (act) {
-            uint32_t q = 0, cand = 0;
+        // the lane's next hit: first non-empty slot, lowest query bit
+        uint32_t q = 0, cand = 0;
+        bool found = false;
 #pragma unroll
-            for (int s = 0; s < CPL; ++s)
-                if (s == s_cur && m[s] == 0) ++s_cur;
-#pragma unroll
-            for (int s = 0; s < CPL; ++s) {
-                if (s == s_cur) {
-                    q = __ffs(m[s]) - 1;
-                    m[s] &= m[s] - 1;
-                    cand = cid[s];
-                }
+        for (int s = 0; s < CPL; ++s) {
+            const bool take = act && !found && m[s] != 0;
+            if (take) {
+                q = __ffs(m[s]) - 1;
+                m[s] &= m[s] - 1;
+                cand = cid[s];
             }
-            const uint32_t qid = __float_as_uint(qbase[(size_t)q * qrs + id_at]);
+            found |= take;
+        }
+        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, q);
+        if (act) {
             const uint64_t pos = base + __popc(bm & lt);
             if (!GLOBAL || pos < cap) dst[pos] = make_uint2(qid, cand);
             if (UNI && (!GLOBAL || pos + nb < cap)) dst[pos + nb] = make_uint2(cand, qid);
@@ -720,12 +722,14 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         for (int s = 0; s < CPL; ++s) left += __popc(m[s]);
         const uint32_t hits = __reduce_add_sync(0xffffffffu, left);
         if (hits == 0) return;
+        const uint32_t qid_l =
+            lane < (int)nq ? __float_as_uint(qbase[(size_t)lane * a.qrs + 2 * D + 2]) : 0u;
         if (hits * kPP >= kDirectPairs) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)hits * kPP);
             base = __shfl_sync(0xffffffffu, base, 0);
             if (!a.count_only)
-                put_hits<CPL, UNI, true>(m, cid, qbase, a.qrs, 2 * D + 2, left, base, a.out, a.cap, lane);
+                put_hits<CPL, UNI, true>(m, cid, qid_l, left, base, a.out, a.cap, lane);
             return;
         }
         const uint32_t kPer = (uint32_t)a.eb / (32u * kPP);
@@ -734,7 +738,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
             const uint32_t total = __reduce_add_sync(0xffffffffu, c) * kPP;
             if (st.fill + total > (uint32_t)a.eb) flush(st, ws, a, lane);
             if (!a.count_only)
-                put_hits<CPL, UNI, false>(m, cid, qbase, a.qrs, 2 * D + 2, c, st.fill, ws.emit, 0, lane);
+                put_hits<CPL, UNI, false>(m, cid, qid_l, c, st.fill, ws.emit, 0, lane);
             else
                 drop_hits<CPL>(m, c);
             left -= c;
