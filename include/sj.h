@@ -232,6 +232,19 @@ SJ_API sj_status sj_selfjoin_index_device(sj_ctx *ctx, const sj_index *idx,
                                    uint32_t *d_pairs, uint64_t cap_pairs,
                                    uint64_t *count, void *stream);
 
+/* Two-set join R ⋈ S (the paper treats the self-join as a special case of
+ * this join): all pairs (i, j) with point i of R and point j of S within
+ * eps, by the same predicate as the self-join.  One grid (Section IV-B) is
+ * laid over the bounding box of R ∪ S; S is indexed as the candidate set
+ * and the points of R are the queries, grouped by their cells; every query
+ * cell searches all 3^n adjacent cells (UNICOMP does not apply: the pair
+ * (i, j) has one orientation).  A pair is (index in R, index in S).  R and S
+ * may be host or device memory.  Output, count and errors as
+ * sj_selfjoin_device. */
+SJ_API sj_status sj_join2_device(sj_ctx *ctx, const double *R, uint64_t nR, const double *S,
+                                 uint64_t nS, int d, double eps, uint32_t *d_pairs,
+                                 uint64_t cap_pairs, uint64_t *count, void *stream);
+
 /* The index-free comparator: every ordered pair (i, j) is tested with the
  * exact FP64 predicate (no grid, no UNICOMP, no FP32 filter), O(n^2)
  * evaluations.  It returns the same pair set as sj_selfjoin_device and

@@ -67,6 +67,8 @@ def _load():
         lib.sj_oracle_mix64.restype = u64
         lib.sj_oracle_bruteforce.argtypes = [P, u64, i32, f64, P, u64]
         lib.sj_oracle_bruteforce.restype = i64
+        lib.sj_oracle_bruteforce2.argtypes = [P, u64, P, u64, i32, f64, P, u64]
+        lib.sj_oracle_bruteforce2.restype = i64
         lib.sj_oracle_grid_cells.argtypes = [P, u64, i32, f64, P, P]
         lib.sj_oracle_grid_cells.restype = i32
         lib.sj_oracle_grid_join.argtypes = [P, u64, i32, f64, i32, P, u64]
@@ -139,6 +141,21 @@ def bruteforce(points, eps: float) -> np.ndarray:
     got = lib.sj_oracle_bruteforce(_ptr(p), n, d, float(eps), _ptr(out), cnt)
     assert got == cnt
     return out
+
+
+def bruteforce2(R, S, eps: float) -> np.ndarray:
+    """The two-set join R ⋈ S by its O(|R| |S|) definition, as sorted keys
+    i << 32 | j (i indexes R, j indexes S)."""
+    r, s = _pts(R), _pts(S)
+    if r.shape[1] != s.shape[1]:
+        raise ValueError("R and S must have the same dimension")
+    lib = _load()
+    args = (_ptr(r), r.shape[0], _ptr(s), s.shape[0], r.shape[1], float(eps))
+    cnt = _check(lib.sj_oracle_bruteforce2(*args, None, 0), "bruteforce2")
+    out = np.empty(cnt, dtype=np.uint64)
+    got = lib.sj_oracle_bruteforce2(*args, _ptr(out), cnt)
+    assert got == cnt
+    return np.sort(out)
 
 
 def grid_join(points, eps: float, nthreads: int | None = None) -> np.ndarray:

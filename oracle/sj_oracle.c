@@ -108,6 +108,25 @@ int64_t sj_oracle_bruteforce(const double *pts, uint64_t n, int d, double eps,
     return (int64_t)count;
 }
 
+/* The two-set join R ⋈ S by the same definition: every (i, j) with point
+ * i of R and point j of S within eps, keys (i << 32) | j in the order of the
+ * loops (i outer), the first cap of them written to out; returns the count.
+ * The self-join is the case S = R. */
+int64_t sj_oracle_bruteforce2(const double *R, uint64_t nR, const double *S, uint64_t nS, int d,
+                              double eps, uint64_t *out, uint64_t cap)
+{
+    const double E2 = sj_oracle_eps2(eps);
+    uint64_t count = 0;
+    for (uint64_t i = 0; i < nR; ++i)
+        for (uint64_t j = 0; j < nS; ++j)
+            if (within(R + i * d, S + j * d, d, E2)) {
+                if (out && count < cap)
+                    out[count] = (i << 32) | j;
+                ++count;
+            }
+    return (int64_t)count;
+}
+
 /* ------------------------------------------------------------------ */
 /* Grid index (Section IV-B, IV-C).                                   */
 /* ------------------------------------------------------------------ */

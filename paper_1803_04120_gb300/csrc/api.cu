@@ -788,6 +788,78 @@ sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, i
     return sc.done(st);
 }
 
+sj_status sj_join2_device(sj_ctx *ctx, const double *R, uint64_t nR, const double *S, uint64_t nS,
+                          int d, double eps, uint32_t *d_pairs, uint64_t cap_pairs, uint64_t *count,
+                          void *stream) {
+    if (!ctx || !count) return SJ_EINVAL;
+    Scoped sc(ctx);
+    reset_stats(ctx);
+    sj_status st = check_args(sc.err, R, nR, d, eps);
+    if (st == SJ_OK) st = check_args(sc.err, S, nS, d, eps);
+    if (st != SJ_OK) return sc.done(st);
+    if (!d_pairs && cap_pairs) return sc.done(fail(sc.err, SJ_EINVAL, "d_pairs is NULL"));
+    if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Error &err = sc.err;
+    const double t0 = now_ms();
+    DevBuf dR, dS;
+    Index ixR, ixS;
+    auto run = [&]() -> sj_status {
+        // one grid over both sets (Section IV-B on the union bounding box)
+        SJ_TRY(dev_alloc(err, dR, nR * d * sizeof(double), s));
+        SJ_TRY(dev_alloc(err, dS, nS * d * sizeof(double), s));
+        SJ_CUDA_TRY(cudaMemcpyAsync(dR.p, R, nR * d * sizeof(double), cudaMemcpyDefault, s));
+        SJ_CUDA_TRY(cudaMemcpyAsync(dS.p, S, nS * d * sizeof(double), cudaMemcpyDefault, s));
+        unsigned long long mR[2 * kMaxDim], mS[2 * kMaxDim], mm[2 * kMaxDim] = {0};
+        bool badR = false, badS = false;
+        SJ_TRY(bounds_of(err, static_cast<const double *>(dR.p), nR, d, s, mR, &badR));
+        SJ_TRY(bounds_of(err, static_cast<const double *>(dS.p), nS, d, s, mS, &badS));
+        if (badR || badS) return fail(err, SJ_EINVAL, "non-finite coordinate");
+        for (int j = 0; j < d; ++j) {
+            mm[2 * j] = std::min(mR[2 * j], mS[2 * j]);
+            mm[2 * j + 1] = std::max(mR[2 * j + 1], mS[2 * j + 1]);
+        }
+        SJ_TRY(build_index(err, static_cast<const double *>(dS.p), nS, d, eps, ctx->cfg.lookup, s, ixS, mm));
+        SJ_TRY(build_index(err, static_cast<const double *>(dR.p), nR, d, eps, ctx->cfg.lookup, s, ixR, mm));
+        const double t1 = now_ms();
+        ctx->stats.ms_index = t1 - t0;
+        JoinLaunch l = default_launch(ctx);
+        l.unicomp = 0;   // R and S differ: every query searches all adjacent cells
+        if (!(l.prec_fp32 && ixS.g.fp32_ok)) {
+            SJ_TRY(ensure_rec64(err, ixS, s));
+            SJ_TRY(ensure_rec64(err, ixR, s));
+        }
+        unsigned long long *m = misc_dev(ctx);
+        SJ_CUDA_TRY(cudaMemsetAsync(m, 0, kMiscWords * sizeof(unsigned long long), s));
+        cudaEvent_t e0, e1;
+        SJ_TRY(profile_events(err, ctx, &e0, &e1));
+        SJ_TRY(launch_join(err, ixS, l, 0, 0xffffffffu, reinterpret_cast<uint2 *>(d_pairs), cap_pairs,
+                           m + kMiscCounter, reinterpret_cast<uint32_t *>(m + kMiscWork),
+                           reinterpret_cast<uint32_t *>(m + kMiscError), 0, s, e0, e1, &ixR));
+        SJ_CUDA_TRY(cudaMemcpyAsync(ctx->h_misc, m, kMiscWords * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s));
+        SJ_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((uint32_t)ctx->h_misc[kMiscError] & kErrTimeout)
+            return fail(err, SJ_ETIMEOUT, "a bounded device wait expired in the join kernel");
+        *count = ctx->h_misc[0];
+        ctx->stats.pairs = ctx->h_misc[0];
+        ctx->stats.evaluations = ctx->h_misc[1];
+        ctx->stats.rechecks = ctx->h_misc[2];
+        ctx->stats.batches = 1;
+        ctx->stats.ms_join = now_ms() - t1;
+        return SJ_OK;
+    };
+    st = run();
+    free_index(ixR, s);
+    free_index(ixS, s);
+    dev_free(dR, s);
+    dev_free(dS, s);
+    ctx->stats.ms_total = now_ms() - t0;
+    if (st == SJ_OK && *count > cap_pairs)
+        st = fail(err, SJ_EOVERFLOW, "output buffer too small for the pair count");
+    return sc.done(st);
+}
+
 sj_status sj_selfjoin_bruteforce_device(sj_ctx *ctx, const double *pts, uint64_t n, int d, double eps,
                                         uint32_t *d_pairs, uint64_t cap_pairs, uint64_t *count,
                                         void *stream) {

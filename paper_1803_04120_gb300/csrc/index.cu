@@ -197,8 +197,33 @@ struct BuildScratch {
     DevBuf minmax, counts;  // counts: [0] flag, [1] n_cells, [2] n_items, [3] lut total
 };
 
+sj_status bounds_of(Error &err, const double *d_pts, uint64_t n, int d, cudaStream_t s,
+                    unsigned long long *mm, bool *nonfinite) {
+    DevBuf scratch;
+    SJ_TRY(dev_alloc(err, scratch, (2 * kMaxDim) * sizeof(unsigned long long) + 64, s));
+    unsigned long long *d_minmax = static_cast<unsigned long long *>(scratch.p);
+    uint32_t *d_flag = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxDim);
+    init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_flag); note_launch();
+    int blocks = 2 * sm_count(-1);
+    const uint64_t need = (n + kThreads - 1) / kThreads;
+    if ((uint64_t)blocks > need) blocks = (int)need;
+    bounds_kernel<<<blocks, kThreads, 0, s>>>(d_pts, n, d, d_minmax, d_flag); note_launch();
+    unsigned long long h[2 * kMaxDim + 8];
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_minmax, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(scratch, s);
+    if (e != cudaSuccess) {
+        set_cuda_error(err, e, "bounds", __FILE__, __LINE__);
+        return err.st;
+    }
+    for (int k = 0; k < 2 * kMaxDim; ++k) mm[k] = h[k];
+    *nonfinite = (reinterpret_cast<const uint32_t *>(h + 2 * kMaxDim)[0] & 1u) != 0;
+    return SJ_OK;
+}
+
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
-                      int lookup_mode, cudaStream_t s, Index &ix) {
+                      int lookup_mode, cudaStream_t s, Index &ix, const unsigned long long *given_mm) {
     ix = Index();
     ix.owner_stream = s;
     if (pts_any == nullptr || n == 0 || d < 1 || d > kMaxDim || !(eps > 0.0) || !std::isfinite(eps))
@@ -222,19 +247,24 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     unsigned long long *d_minmax = static_cast<unsigned long long *>(scratch.p);
     uint32_t *d_counts = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxDim);
     SJ_CUDA_TRY(cudaMemsetAsync(d_counts, 0, 64, s));
-    init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_counts); note_launch();
-    {
-        int blocks = 2 * sm_count(-1);
-        uint64_t need = (n + kThreads - 1) / kThreads;
-        if ((uint64_t)blocks > need) blocks = (int)need;
-        bounds_kernel<<<blocks, kThreads, 0, s>>>(pts, n, d, d_minmax, d_counts); note_launch();
-    }
-    SJ_CUDA_TRY(cudaGetLastError());
     unsigned long long h_mm[2 * kMaxDim + 8];
-    SJ_CUDA_TRY(cudaMemcpyAsync(h_mm, d_minmax, sizeof(h_mm), cudaMemcpyDeviceToHost, s));
-    SJ_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t *h_counts = reinterpret_cast<const uint32_t *>(h_mm + 2 * kMaxDim);
-    if (h_counts[0] & 1u) { dev_free(scratch, s); return fail(err, SJ_EINVAL, "non-finite coordinate"); }
+    if (given_mm) {
+        // bounds given by the caller (a grid shared with another point set)
+        for (int k = 0; k < 2 * kMaxDim; ++k) h_mm[k] = given_mm[k];
+    } else {
+        init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_counts); note_launch();
+        {
+            int blocks = 2 * sm_count(-1);
+            uint64_t need = (n + kThreads - 1) / kThreads;
+            if ((uint64_t)blocks > need) blocks = (int)need;
+            bounds_kernel<<<blocks, kThreads, 0, s>>>(pts, n, d, d_minmax, d_counts); note_launch();
+        }
+        SJ_CUDA_TRY(cudaGetLastError());
+        SJ_CUDA_TRY(cudaMemcpyAsync(h_mm, d_minmax, sizeof(h_mm), cudaMemcpyDeviceToHost, s));
+        SJ_CUDA_TRY(cudaStreamSynchronize(s));
+        const uint32_t *h_counts = reinterpret_cast<const uint32_t *>(h_mm + 2 * kMaxDim);
+        if (h_counts[0] & 1u) { dev_free(scratch, s); return fail(err, SJ_EINVAL, "non-finite coordinate"); }
+    }
 
     // geometry (Section IV-B)
     {

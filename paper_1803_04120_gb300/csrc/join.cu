@@ -416,10 +416,12 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
                                              unsigned long long &evals) {
     typedef typename std::conditional<F32, float, double>::type T;
     const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
-    const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
-                                   : reinterpret_cast<const unsigned char *>(a.rec64);
+    // the query side: the item's cell and points (the candidate side is
+    // read through a.lut / a.B / a.G and the ranges)
+    const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.qrec32)
+                                   : reinterpret_cast<const unsigned char *>(a.qrec64);
     const uint32_t h = it.x;
-    const uint32_t cbeg = __ldg(&a.G[h]), cend = __ldg(&a.G[h + 1]);
+    const uint32_t cbeg = __ldg(&a.qG[h]), cend = __ldg(&a.qG[h + 1]);
     const uint32_t home_len = cend - cbeg;
     const uint32_t q0 = cbeg + it.y * kQueryBlock;
     const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
@@ -428,7 +430,7 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
     uint32_t odd = 0;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        c[j] = __ldg(&a.cc[(uint64_t)h * D + j]);
+        c[j] = __ldg(&a.qcc[(uint64_t)h * D + j]);
         odd |= ((uint32_t)c[j] & 1u) << j;
     }
 
@@ -704,7 +706,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                     w &= w - 1;
                     ++rechecks;
                     const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + 2 * D + 2]);
-                    if (!exact_member_ni(a.pts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
+                    if (!exact_member_ni(a.qpts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
                         m[s] &= ~(1u << q);
                 }
             }
@@ -819,7 +821,7 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
 
     // counts[0] = |G|, counts[1] = number of work items (device-side, so the
     // launch needs no read-back)
-    const uint32_t n_cells = counts[0];
+    const uint32_t n_cells = *a.ccells;   // non-empty candidate cells (binary search of B)
     uint32_t item_end = a.item_end;
     if (counts[1] < item_end) item_end = counts[1];
 
@@ -835,8 +837,14 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     bool failed = false;
 
     uint2 it;
-    if (fetch_item(st, a, item_end, lane, it)) {
+    // the first item with at least one candidate (in a two-set join a query
+    // cell may have no candidate point around it: nothing to compare)
+    bool have = false;
+    while (!have && fetch_item(st, a, item_end, lane, it)) {
         prepare_item<D, F32, UNI>(ws, 0, it, a, n_cells, lane, evals);
+        have = ws.hdr[0].nchunks != 0;
+    }
+    if (have) {
         for (;;) {
             // producer: keep up to nbuf chunks in flight, crossing into the
             // next item (at most one item ahead of the consumer)
@@ -851,8 +859,12 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                         st.prod_done = true;
                         break;
                     }
+                    const int ns = (st.prod_seq + 1) & smask;
+                    prepare_item<D, F32, UNI>(ws, ns, it, a, n_cells, lane, evals);
+                    // an item without candidates is done: the next one may
+                    // take the same slot
+                    if (ws.hdr[ns].nchunks == 0) continue;
                     ++st.prod_seq;
-                    prepare_item<D, F32, UNI>(ws, st.prod_seq & smask, it, a, n_cells, lane, evals);
                     st.p_chunk = 0;
                     st.rcur = 0;
                     continue;
@@ -1091,13 +1103,24 @@ sj_status template_table(Error &err, int d, bool uni, const uint32_t **out) {
 sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                          uint32_t item_end, uint2 *out, uint64_t cap,
                          unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
-                         int count_only, JoinArgs &a) {
+                         int count_only, JoinArgs &a, const Index *qix) {
     const Geometry &g = ix.g;
     const int d = g.d;
     const bool f32 = cfg.prec_fp32 && g.fp32_ok;
     const bool uni = cfg.unicomp != 0;
     if (!f32 && !ix.rec64.p) return fail(err, SJ_EINVAL, "FP64 records missing");
+    // the query side (work items, home cells, query points): another index
+    // on the same grid for a two-set join, else the candidate index itself
+    const Index &q = qix ? *qix : ix;
+    if (qix && (uni || !(f32 || q.rec64.p)))
+        return fail(err, SJ_EINVAL, "two-set joins search all adjacent cells and need both records");
     memset(&a, 0, sizeof(a));
+    a.qrec32 = static_cast<const float *>(q.rec32.p);
+    a.qrec64 = static_cast<const double *>(q.rec64.p);
+    a.qpts = static_cast<const double *>(q.pts.p);
+    a.qG = static_cast<const uint32_t *>(q.G.p);
+    a.qcc = static_cast<const int32_t *>(q.cc.p);
+    a.ccells = n_items_dev(ix) - 1;
     a.rec32 = static_cast<const float *>(ix.rec32.p);
     a.rec64 = static_cast<const double *>(ix.rec64.p);
     a.pts = static_cast<const double *>(ix.pts.p);
@@ -1106,7 +1129,7 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.cc = static_cast<const int32_t *>(ix.cc.p);
     a.M = static_cast<const uint32_t *>(ix.M.p);
     a.lut = static_cast<const uint32_t *>(ix.lut.p);
-    a.items = static_cast<const uint2 *>(ix.items.p);
+    a.items = static_cast<const uint2 *>(q.items.p);
     a.item_begin = item_begin;
     a.item_end = item_end;
     a.item_stride = cfg.item_stride > 0 ? cfg.item_stride : 1;
@@ -1150,17 +1173,18 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.timeout_ns = 2000000000ull;
     a.d = d;
     a.f32 = f32 ? 1 : 0;
-    a.dcounts = n_items_dev(ix) - 1;
+    a.dcounts = n_items_dev(q) - 1;
     return SJ_OK;
 }
 
 sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                       uint32_t item_end, uint2 *out, uint64_t cap,
                       unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
-                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                      const Index *qix) {
     JoinArgs a;
     SJ_TRY(fill_join_args(err, ix, cfg, item_begin, item_end, out, cap, d_counter, d_work, d_error,
-                          count_only, a));
+                          count_only, a, qix));
     const int d = a.d;
     const bool f32 = a.f32 != 0;
     const bool uni = cfg.unicomp != 0;
@@ -1176,7 +1200,7 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     if (item_end <= item_begin) blocks = 1;
     SJ_CUDA_TRY(cudaMemsetAsync(d_work, 0, sizeof(uint32_t), s));
     if (ev0) SJ_CUDA_TRY(cudaEventRecord(ev0, s));
-    fn<<<blocks, wpb * 32, smem, s>>>(a, n_items_dev(ix) - 1); note_launch();
+    fn<<<blocks, wpb * 32, smem, s>>>(a, a.dcounts); note_launch();
     SJ_CUDA_TRY(cudaGetLastError());
     if (ev1) SJ_CUDA_TRY(cudaEventRecord(ev1, s));
     return SJ_OK;

@@ -106,8 +106,15 @@ struct Index {
 // FP32 filter margin of a geometry (margin.cu): sets w32, lo32, hi32, fp32_ok.
 void fp32_margin(Geometry &g);
 
+// given_mm: per-dimension bounds (order keys, min/max interleaved) of a grid
+// shared with another point set; null to bound the points themselves.
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
-                      int lookup_mode, cudaStream_t s, Index &ix);
+                      int lookup_mode, cudaStream_t s, Index &ix,
+                      const unsigned long long *given_mm = nullptr);
+// Per-dimension min/max (order keys) of device points and a non-finite flag
+// (synchronises s).
+sj_status bounds_of(Error &err, const double *d_pts, uint64_t n, int d, cudaStream_t s,
+                    unsigned long long *mm, bool *nonfinite);
 void free_index(Index &ix, cudaStream_t s);
 sj_status ensure_rec64(Error &err, Index &ix, cudaStream_t s);
 // Build into a caller-provided device region, allocating nothing (index.cu).
@@ -129,6 +136,14 @@ struct JoinArgs {
     const uint32_t *M;
     const uint32_t *lut;
     const uint2 *items;
+    // query side: the same index for a self-join; another index on the
+    // same grid for a two-set join
+    const float *qrec32;
+    const double *qrec64;
+    const double *qpts;
+    const uint32_t *qG;
+    const int32_t *qcc;
+    const uint32_t *ccells;         // candidate |G| (device)
     uint32_t item_begin, item_end;
     uint32_t item_stride;           // sampled launches: every item_stride-th item
     uint32_t n_cells;
@@ -189,7 +204,7 @@ static_assert(sizeof(MultiJobs) <= 32000, "multi-join table exceeds the kernel p
 sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                          uint32_t item_end, uint2 *out, uint64_t cap,
                          unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
-                         int count_only, JoinArgs &a);
+                         int count_only, JoinArgs &a, const Index *qix = nullptr);
 sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb,
                       int *per_sm);
 // Index-free comparator (brute.cu): every ordered pair with the exact FP64
@@ -215,10 +230,12 @@ sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, 
                                double eps, Geometry &g);
 int n_templates(int d, bool uni);
 
+// qix: the query-side index of a two-set join (same grid as ix), else null.
 sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                       uint32_t item_end, uint2 *out, uint64_t cap,
                       unsigned long long *d_counter, uint32_t *d_work, uint32_t *d_error,
-                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                      int count_only, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                      const Index *qix = nullptr);
 
 // Device-wide exclusive scan of u32 (in may equal out).  *d_total receives the
 // sum.  Returns SJ_OK or an error.

@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
-    "sj_selfjoin_bruteforce_device",
+    "sj_selfjoin_bruteforce_device", "sj_join2_device",
 )
 
 
@@ -153,6 +153,8 @@ def load(build: bool = True):
                                       ctypes.POINTER(ctypes.c_uint64)]),
             "sj_selfjoin_bruteforce_device": (i32, [P, P, u64, i32, f64, P, u64,
                                                     ctypes.POINTER(ctypes.c_uint64), P]),
+            "sj_join2_device": (i32, [P, P, u64, P, u64, i32, f64, P, u64,
+                                      ctypes.POINTER(ctypes.c_uint64), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -304,6 +306,23 @@ class Context:
         if st == SJ_EOVERFLOW and not raise_overflow:
             return int(cnt.value)
         self._check(st, "sj_selfjoin_shard_device")
+        return int(cnt.value)
+
+    def sj_join2_device(self, R, S, eps: float, out, stream=None, raise_overflow: bool = True) -> int:
+        """Two-set join R ⋈ S into a device buffer of (index in R, index in S)
+        pairs; returns the pair count."""
+        pr, nr, dr, kr = _points_ptr(R)
+        ps, ns, ds, ks = _points_ptr(S)
+        if dr != ds:
+            raise ValueError("R and S must have the same dimension")
+        cap = 0 if out is None else out.shape[0]
+        optr = ctypes.c_void_p(out.data_ptr()) if out is not None and cap else None
+        cnt = ctypes.c_uint64(0)
+        st = self._lib.sj_join2_device(self._h, pr, nr, ps, ns, dr, float(eps), optr, cap,
+                                       ctypes.byref(cnt), _stream_ptr(stream))
+        if st == SJ_EOVERFLOW and not raise_overflow:
+            return int(cnt.value)
+        self._check(st, "sj_join2_device")
         return int(cnt.value)
 
     def sj_selfjoin_bruteforce_device(self, points, eps: float, out, stream=None,

@@ -325,3 +325,51 @@ def test_unicomp_3d_listing_guard_as_printed_misses_pairs():
     n_adjacent = sum(1 for a in cells for b in cells
                      if a < b and max(abs(x - y) for x, y in zip(a, b)) <= 1)
     assert len(seen) < n_adjacent or any(v != 1 for v in seen.values())
+
+
+# ------------------------------------------------------------------ two-set join
+# The two-set oracle is pinned to the self-join definition: R ⋈ R is the
+# self-join, the self-join of R ∪ S decomposes into R ⋈ R, S ⋈ S, R ⋈ S and
+# S ⋈ R, swapping the sets swaps the pairs, and boundary points follow the
+# inclusive predicate.
+
+def _split_keys(keys):
+    return keys >> np.uint64(32), keys & np.uint64(0xffffffff)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8])
+def test_join2_of_a_set_with_itself_is_the_self_join(d):
+    rng = np.random.default_rng(100 + d)
+    r = rng.uniform(0, 5, size=(300, d))
+    eps = 1.3
+    assert np.array_equal(orc.bruteforce2(r, r, eps), np.sort(orc.bruteforce(r, eps)))
+
+
+@pytest.mark.parametrize("d", [1, 2, 4, 7])
+def test_join2_decomposes_the_self_join_of_the_union(d):
+    rng = np.random.default_rng(200 + d)
+    r = rng.uniform(0, 6, size=(170, d))
+    s = rng.uniform(2, 8, size=(230, d))
+    s[:5] = r[:5]                         # coincident points across the sets
+    eps = 1.7
+    u = np.concatenate([r, s])
+    i, j = _split_keys(np.sort(orc.bruteforce(u, eps)))
+    nr = np.uint64(len(r))
+    cross = (i < nr) & (j >= nr)
+    want = np.sort((i[cross] << np.uint64(32)) | (j[cross] - nr))
+    got = orc.bruteforce2(r, s, eps)
+    assert np.array_equal(got, want)
+    # swapping the sets swaps the pairs
+    i2, j2 = _split_keys(orc.bruteforce2(s, r, eps))
+    assert np.array_equal(np.sort((j2 << np.uint64(32)) | i2), got)
+
+
+def test_join2_boundary_and_empty():
+    r = np.array([[0.0, 0.0]])
+    eps = 1.0
+    on = np.array([[1.0, 0.0]])                       # distance exactly eps: member
+    off = np.array([[np.nextafter(1.0, 2.0), 0.0]])   # one ulp beyond: not
+    assert len(orc.bruteforce2(r, on, eps)) == 1
+    assert len(orc.bruteforce2(r, off, eps)) == 0
+    far = np.array([[10.0, 10.0], [20.0, 0.0]])
+    assert len(orc.bruteforce2(r, far, eps)) == 0
