@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_cells(const EngTable *__restr
     const CellParams cp = e.cp;
     const uint32_t nc = e.counts[1];
     for (uint64_t h = (uint64_t)x * blockDim.x + threadIdx.x; h < nc; h += (uint64_t)X * blockDim.x)
-        cell_coords(e.B[h], h, cp, e.mwords, e.cc, e.M);
+        cell_coords(e.pts + (uint64_t)e.A[e.G[h]] * cp.d, h, cp, e.mwords, e.cc, e.M);
 }
 
 __global__ void __launch_bounds__(kEngThreads) eng_rec(const EngTable *__restrict__ t) {

@@ -108,15 +108,20 @@ __device__ __forceinline__ void bounds_accumulate(const double *__restrict__ pts
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
-// Cell coordinates of the non-empty cell h with linear id `id`, and its bits
-// in the occupancy bitmaps M_j (when M is given).
-__device__ __forceinline__ void cell_coords(uint64_t id, uint64_t h, const CellParams &cp,
+// Cell coordinates of the non-empty cell h, recomputed from one of its
+// points p with the formula of linear_cell (so they agree with the cell's
+// id without 64-bit divisions), and its bits in the occupancy bitmaps M_j
+// (when M is given).
+__device__ __forceinline__ void cell_coords(const double *p, uint64_t h, const CellParams &cp,
                                             uint32_t mwords, int32_t *__restrict__ cc,
                                             uint32_t *__restrict__ M) {
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j) {
         if (j < cp.d) {
-            const uint64_t c = (id / cp.stride[j]) % (uint64_t)cp.ng[j];
+            const double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
+            int64_t c = (int64_t)floor(q);
+            c = c < 0 ? 0 : c;
+            c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
             cc[h * cp.d + j] = (int32_t)c;
             if (M) {
                 uint32_t *w = &M[(uint64_t)j * mwords + (c >> 5)];

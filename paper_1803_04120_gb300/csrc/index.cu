@@ -102,14 +102,16 @@ __global__ void __launch_bounds__(kThreads) rle_kernel(const uint64_t *__restric
     if (k == 0) G[*n_cells] = (uint32_t)n;
 }
 
-__global__ void __launch_bounds__(kThreads) cells_kernel(const uint64_t *__restrict__ B,
+__global__ void __launch_bounds__(kThreads) cells_kernel(const double *__restrict__ pts,
+                                                         const uint32_t *__restrict__ A,
+                                                         const uint32_t *__restrict__ G,
                                                          const uint32_t *__restrict__ n_cells,
                                                          CellParams cp, uint32_t mwords,
                                                          int32_t *__restrict__ cc,
                                                          uint32_t *__restrict__ M) {
     uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= *n_cells) return;
-    cell_coords(B[h], h, cp, mwords, cc, M);
+    cell_coords(pts + (uint64_t)A[G[h]] * cp.d, h, cp, mwords, cc, M);
 }
 
 // FP32 record: y_j = fl32(x_j - g_min_j) for j < d, then the point id.
@@ -348,7 +350,8 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     SJ_B(dev_alloc(err, ix.cc, n * d * sizeof(int32_t), s));
     SJ_B(dev_alloc(err, ix.M, (uint64_t)d * ix.mwords * sizeof(uint32_t), s));
     SJ_BC(cudaMemsetAsync(ix.M.p, 0, (uint64_t)d * ix.mwords * sizeof(uint32_t), s));
-    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(ix.B.p), d_counts + 1, cp,
+    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, static_cast<const uint32_t *>(ix.A.p),
+                                                  static_cast<const uint32_t *>(ix.G.p), d_counts + 1, cp,
                                                   ix.mwords, static_cast<int32_t *>(ix.cc.p),
                                                   static_cast<uint32_t *>(ix.M.p)); note_launch();
     SJ_BC(cudaGetLastError());
@@ -537,7 +540,8 @@ sj_status build_index_static(Error &err, const double *d_pts, uint64_t n, int d,
     rle_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(skey.p), hs, n, d_counts + 1,
                                                  static_cast<uint64_t *>(ix.B.p),
                                                  static_cast<uint32_t *>(ix.G.p)); note_launch();
-    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(ix.B.p), d_counts + 1, cp,
+    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, static_cast<const uint32_t *>(ix.A.p),
+                                                  static_cast<const uint32_t *>(ix.G.p), d_counts + 1, cp,
                                                   ix.mwords, static_cast<int32_t *>(ix.cc.p),
                                                   static_cast<uint32_t *>(ix.M.p)); note_launch();
     rec32_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, static_cast<uint32_t *>(ix.A.p), n, cp,

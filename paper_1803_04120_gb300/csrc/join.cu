@@ -45,7 +45,9 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -981,11 +983,38 @@ int n_templates(int d, bool uni) {
     return uni ? p + 2 : p;
 }
 
+sj_status block_shape_uncached(Error &err, const void *fn, int sm_warp, int force_wpb, int dev,
+                               int *wpb_out, int *per_sm_out);
+
 // Warps per block of a join launch: the block size (8, 4, 2 or 1 warps)
 // that keeps the most warps resident per SM under the shared-memory and
 // register limits, or force_wpb when given and it fits.
 sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, int dev, int *wpb_out,
                       int *per_sm_out) {
+    // answers are cached: the occupancy queries cost more host time than a
+    // small join kernel takes on the device
+    static std::mutex cache_mu;
+    static std::map<std::tuple<const void *, int, int, int>, std::pair<int, int>> cache;
+    const auto key = std::make_tuple(fn, sm_warp, force_wpb, dev);
+    {
+        std::lock_guard<std::mutex> lk(cache_mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *wpb_out = it->second.first;
+            *per_sm_out = it->second.second;
+            return SJ_OK;
+        }
+    }
+    const sj_status st = block_shape_uncached(err, fn, sm_warp, force_wpb, dev, wpb_out, per_sm_out);
+    if (st == SJ_OK) {
+        std::lock_guard<std::mutex> lk(cache_mu);
+        cache[key] = std::make_pair(*wpb_out, *per_sm_out);
+    }
+    return st;
+}
+
+sj_status block_shape_uncached(Error &err, const void *fn, int sm_warp, int force_wpb, int dev,
+                               int *wpb_out, int *per_sm_out) {
     int smem_optin = 0;
     SJ_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     {

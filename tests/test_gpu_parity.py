@@ -354,3 +354,18 @@ def test_config3_full_size_streamed_digest(d):
     assert acc["count"] == o_count == st["pairs"]
     assert acc["hash"] == o_hash
     assert np.array_equal(deg, o_deg.astype(np.int64))
+
+
+def test_fp32_mode_falls_back_to_fp64_when_the_margin_is_unusable():
+    """A range of 5e6 against eps = 1 leaves no usable FP32 margin: the FP32
+    mode must then compute in FP64 (no rechecks) and still be exact."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(77)
+    x = np.stack([rng.uniform(0, 5e6, 20000), rng.uniform(0, 3.0, 20000)], axis=1)
+    x[:200, 0] = rng.uniform(1e6, 1e6 + 20.0, 200)     # a dense stretch with many pairs
+    st, _, _, _ = sj.sj_fp32_margin(2, 1.0, x.min(axis=0) - 1.0, x.max(axis=0) + 1.0)
+    assert st == sj.SJ_ERANGE
+    with sj.Context(prec=sj.SJ_PREC_FP32_RECHECK) as ctx:
+        got = np.sort(sj.pairs_to_keys(ctx.sj_selfjoin(x, 1.0)))
+        assert ctx.sj_last_stats()["rechecks"] == 0
+    assert np.array_equal(got, np.sort(orc.grid_join(x, 1.0)))
