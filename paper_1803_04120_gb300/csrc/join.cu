@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, minb_for(D, F32))
 // counters, output and error word; its dimension and precision select the
 // specialised loop.  The job table lives in the kernel parameters (constant
 // bank), read with warp-uniform indices.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     multi_join_kernel(const __grid_constant__ MultiJobs m) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;

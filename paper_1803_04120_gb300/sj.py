@@ -408,10 +408,10 @@ class Context:
         finally:
             self._lib.sj_result_free(r)
 
-    def sj_selfjoin_multi(self, jobs, raise_errors: bool = True):
+    def sj_selfjoin_multi(self, jobs, raise_errors: bool = True, copy: bool = True):
         """Joins [(points, eps), ...] together; returns a list with one
-        (count, 2) uint32 pair array per job (None for a failed job when
-        raise_errors is False)."""
+        (count, 2) uint32 pair array per job, or only its pair count when copy
+        is False (None for a failed job when raise_errors is False)."""
         keep = []
         arr = (sj_job * max(1, len(jobs)))()
         for k, (pts, eps) in enumerate(jobs):
@@ -424,7 +424,12 @@ class Context:
         res = []
         try:
             for k in range(len(jobs)):
-                res.append(_result_to_numpy(self._lib, ctypes.c_void_p(outs[k])) if outs[k] else None)
+                if not outs[k]:
+                    res.append(None)
+                elif copy:
+                    res.append(_result_to_numpy(self._lib, ctypes.c_void_p(outs[k])))
+                else:
+                    res.append(int(self._lib.sj_result_count(ctypes.c_void_p(outs[k]))))
         finally:
             for k in range(len(jobs)):
                 if outs[k]:
