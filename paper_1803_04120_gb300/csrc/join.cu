@@ -375,21 +375,28 @@ __device__ __forceinline__ void load_candidates(const unsigned char *buf, int rs
 template <int D, int NP>
 __device__ __forceinline__ void eval_query(const float *qd, const f2_t (*z)[D], const f2_t *qq2,
                                            float *sv) {
-    const ulonglong2 *q2 = reinterpret_cast<const ulonglong2 *>(qd);
-    f2_t m[D + 1];
+    // record: m_0 .. m_{d-1}, pp, id (16-byte loads, broadcast to the warp)
+    constexpr int V = (D + 2 + 3) / 4;
+    float r[4 * V];
+    const float4 *q4 = reinterpret_cast<const float4 *>(qd);
 #pragma unroll
-    for (int k = 0; k < (D + 2) / 2; ++k) {
-        const ulonglong2 v = q2[k];
-        m[2 * k] = v.x;
-        if (2 * k + 1 <= D) m[2 * k + 1] = v.y;
+    for (int k = 0; k < V; ++k) {
+        const float4 v = q4[k];
+        r[4 * k] = v.x;
+        r[4 * k + 1] = v.y;
+        r[4 * k + 2] = v.z;
+        r[4 * k + 3] = v.w;
     }
+    const f2_t pp = f2_pack(r[D], r[D]);
     f2_t acc[NP];
 #pragma unroll
-    for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_add(qq2[cp], m[D]);
+    for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_add(qq2[cp], pp);
 #pragma unroll
-    for (int j = 0; j < D; ++j)
+    for (int j = 0; j < D; ++j) {
+        const f2_t mj = f2_pack(r[j], r[j]);
 #pragma unroll
-        for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_fma(m[j], z[cp][j], acc[cp]);
+        for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_fma(mj, z[cp][j], acc[cp]);
+    }
 #pragma unroll
     for (int cp = 0; cp < NP; ++cp) f2_unpack(acc[cp], sv[2 * cp], sv[2 * cp + 1]);
 }
@@ -487,12 +494,10 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
                 const float z = __fsub_rn(r[j], o[j]);
                 pp = __fmaf_rn(z, z, pp);
                 const float m = -2.0f * z;
-                qd[2 * j] = m;
-                qd[2 * j + 1] = m;
+                qd[j] = m;
             }
-            qd[2 * D] = pp;
-            qd[2 * D + 1] = pp;
-            qd[2 * D + 2] = r[D];   // point id bits
+            qd[D] = pp;
+            qd[D + 1] = r[D];   // point id bits
         }
         if (lane < D) hd->o[lane] = o[lane];
     } else {
@@ -643,7 +648,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
             // search meets the query itself as an ordinary hit.)
             if (st.fill + nq > (uint32_t)a.eb) flush(st, ws, a, lane);
             if (!a.count_only && lane < (int)nq) {
-                const uint32_t qid = __float_as_uint(qbase[(size_t)lane * a.qrs + 2 * D + 2]);
+                const uint32_t qid = __float_as_uint(qbase[(size_t)lane * a.qrs + D + 1]);
                 ws.emit[st.fill + lane] = make_uint2(qid, qid);
             }
             st.fill += nq;
@@ -707,7 +712,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                     const uint32_t q = __ffs(w) - 1;
                     w &= w - 1;
                     ++rechecks;
-                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + 2 * D + 2]);
+                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + D + 1]);
                     if (!exact_member_ni(a.qpts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
                         m[s] &= ~(1u << q);
                 }
@@ -727,7 +732,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         const uint32_t hits = __reduce_add_sync(0xffffffffu, left);
         if (hits == 0) return;
         const uint32_t qid_l =
-            lane < (int)nq ? __float_as_uint(qbase[(size_t)lane * a.qrs + 2 * D + 2]) : 0u;
+            lane < (int)nq ? __float_as_uint(qbase[(size_t)lane * a.qrs + D + 1]) : 0u;
         if (hits * kPP >= kDirectPairs) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)hits * kPP);
@@ -1184,9 +1189,9 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.grab = cfg.grab > 0 ? cfg.grab : 1;
     const int esz = f32 ? 4 : 8;
     const int rsb = a.rs * esz;
-    // query record: FP32 (m_j, m_j) pairs, (pp, pp), id -> 2d + 3 floats;
+    // query record: FP32 m_0 .. m_{d-1}, pp, id -> d + 2 floats;
     // FP64: x_0..x_{d-1}, id
-    a.qrs = f32 ? ((2 * d + 3 + 3) & ~3) : ((d + 1 + 1) & ~1);
+    a.qrs = f32 ? ((d + 2 + 3) & ~3) : ((d + 1 + 1) & ~1);
     a.cb = 32 * cpl_for(d, f32);
     a.sm_ranges = round16(a.n_templates * (int)sizeof(uint2));
     a.sm_queries = round16(kQueryBlock * a.qrs * esz);
