@@ -290,6 +290,67 @@ def ablation_bench(dev: int, reps: int):
                     "for the brute-force comparison"}
 
 
+# ---------------------------------------------------------------- record frames
+
+def frame_bench(dev: int, reps: int):
+    """FP32 record frames.  Wide-domain clustered points (2,000,000 points,
+    about 2e6 cells per dimension): records relative to g_min leave no
+    usable FP32 margin there and the join computes in FP64, records relative
+    to the four-cell frame keep the FP32 filter.  On the 2,000,000-point
+    uniform workload (d = 2, 6): the cost of the frame step against the
+    rechecks it saves.  Pairs in device memory; whole call (index build
+    included) and join kernel times."""
+    import torch
+    from paper_1803_04120_gb300 import sj
+
+    stream = torch.cuda.Stream()
+
+    def measure(cfg, frame):
+        pts = torch.from_numpy(datagen.make_points(cfg)).cuda()
+        with sj.Context(frame=frame, profile=True, device=dev) as c:
+            n = c.sj_selfjoin_count(pts, cfg["eps"])
+            out = torch.empty((max(n, 1), 2), dtype=torch.int32, device="cuda")
+            c.sj_selfjoin_device(pts, cfg["eps"], out, stream=stream)
+            torch.cuda.synchronize()
+            c.sj_profile_read()
+            ts = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                assert c.sj_selfjoin_device(pts, cfg["eps"], out, stream=stream) == n
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            kms, nl = c.sj_profile_read()
+            st = c.sj_last_stats()
+        del out, pts
+        torch.cuda.empty_cache()
+        return n, {"ms": round(min(ts), 3), "kernel_ms": round(kms / max(nl, 1), 3),
+                   "rechecks": st["rechecks"],
+                   "arithmetic": {-1: "fp64", 0: "fp32 grid frame", 1: "fp32 cell frame"}[st["frame"]]}
+
+    wide = []
+    for d in (2, 3):
+        cfg = datagen.wide_clustered(d)
+        n, auto = measure(cfg, sj.SJ_FRAME_AUTO)
+        _, grid = measure(cfg, sj.SJ_FRAME_GRID)
+        wide.append({"d": d, "n": cfg["n"], "eps": cfg["eps"], "pairs": n,
+                     "auto": auto, "grid_frame_only": grid,
+                     "pairs_per_s_auto": round(n / (auto["ms"] / 1e3), 1),
+                     "speedup": round(grid["ms"] / auto["ms"], 2)})
+    uni = []
+    for d in (2, 6):
+        cfg = datagen.config2(d)
+        n, grid = measure(cfg, sj.SJ_FRAME_GRID)
+        _, cell = measure(cfg, sj.SJ_FRAME_CELL)
+        uni.append({"d": d, "pairs": n, "grid": grid, "cell": cell,
+                    "kernel_ratio_cell_over_grid": round(cell["kernel_ms"] / grid["kernel_ms"], 3)})
+    return {"wide_clustered": wide, "uniform_2M": uni,
+            "workload": "wide: 2,000,000 points, 20,000 Gaussian clusters (sigma log-U[0.1, 5]) "
+                        "with centres U[0, 1e6]^d plus 10% uniform background, eps = 0.5"}
+
+
 # ---------------------------------------------------------------- serving
 
 def _pct(v, q):
@@ -520,6 +581,8 @@ def run_gpu(args):
         line["skew"] = skew_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_ablation:
         line["ablation"] = ablation_bench(dev, max(1, min(args.steps, 3)))
+    if not args.no_frames:
+        line["frames"] = frame_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_cpu:
         v, cores, desc = cpu_oracle_sample(data, args.cpu_budget)
         line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -580,6 +643,8 @@ def main():
     ap.add_argument("--no-skew", action="store_true", help="skip the clustered workload")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the UNICOMP and brute-force comparisons")
+    ap.add_argument("--no-frames", action="store_true",
+                    help="skip the FP32 record-frame comparison")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -592,7 +657,7 @@ def main():
         # replicas: each rank runs the same workload on its own GPU; the
         # whole-job value is the sum over ranks of pairs over the max time
         # (the serving and clustered sections are single-GPU measurements)
-        args.serve_requests, args.no_skew, args.no_ablation = 0, True, True
+        args.serve_requests, args.no_skew, args.no_ablation, args.no_frames = 0, True, True, True
         import torch.distributed as dist
         dist.init_process_group("nccl")
         args.no_cpu = args.no_cpu or rank != 0

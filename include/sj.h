@@ -91,6 +91,18 @@ typedef enum { SJ_PREC_FP64 = 0, SJ_PREC_FP32_RECHECK = 1 } sj_precision;
  * it when the grid has at most max(2^25, 16 n) cells.  Results are identical. */
 typedef enum { SJ_LOOKUP_AUTO = 0, SJ_LOOKUP_DENSE = 1, SJ_LOOKUP_SEARCH = 2 } sj_lookup;
 
+/* Coordinate frame of the FP32 point records of SJ_PREC_FP32_RECHECK.
+ * SJ_FRAME_GRID stores fl32(x_j - g_min_j): its rounding error grows with
+ * the extent of the data, so the margin of values recomputed in FP64 widens
+ * with range / eps and the filter is dropped (FP64 arithmetic) beyond about
+ * 2e6.  SJ_FRAME_CELL stores each coordinate relative to a frame that
+ * repeats every four cells (the kernel undoes the frame step exactly), so
+ * the error is a few units in the last place of the cell side at any
+ * range.  SJ_FRAME_AUTO (default) keeps the grid frame while its margin is
+ * below 2^-10 eps^2, else takes the narrower margin.  Results are
+ * identical in every frame. */
+typedef enum { SJ_FRAME_AUTO = -1, SJ_FRAME_GRID = 0, SJ_FRAME_CELL = 1 } sj_frame;
+
 typedef struct {
     int32_t prec;            /* sj_precision; default SJ_PREC_FP32_RECHECK */
     int32_t unicomp;         /* 1 (default): Section V-B duplicate-search removal;
@@ -124,7 +136,8 @@ typedef struct {
     int32_t staging;         /* staged pairs per warp (128, 256, 512 or 1024) */
     int32_t wpb;             /* warps per block (1, 2, 4 or 8) */
     int32_t slots;           /* work items a warp holds at once (1 or 2) */
-    int32_t reserved[3];
+    int32_t frame;           /* sj_frame; default SJ_FRAME_AUTO */
+    int32_t reserved[2];
 } sj_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -174,6 +187,8 @@ typedef struct {
     double gmin[8], gmax[8]; /* g_min_j, g_max_j */
     int64_t ng[8];           /* |g_j| */
     uint64_t device_bytes;   /* device memory the index holds */
+    int32_t fp32;            /* 1: the FP32 filter has a usable margin on this grid */
+    int32_t frame;           /* sj_frame of the index's FP32 records */
 } sj_index_desc;
 
 SJ_API sj_status sj_index_info(const sj_index *idx, sj_index_desc *out);
@@ -190,16 +205,27 @@ SJ_API sj_status sj_index_export(const sj_index *idx, uint64_t *B, uint32_t *G,
 
 /* The classification margin of SJ_PREC_FP32_RECHECK for a grid with
  * dimension d, distance eps and padded bounds g_min_j, g_max_j
- * (Section IV-B: g_min_j = min_j - eps, g_max_j = max_j + eps).  The join
- * kernel computes an FP32 squared distance s32 from coordinates relative to
- * the centre of the query's cell (see the derivation in csrc/margin.cu);
- * s32 <= *lo implies membership by the exact FP64 test, s32 > *hi implies
- * non-membership, and only values in between are recomputed in FP64.
- * *w32 receives the cell side rounded to FP32.  Host-only, no device needed.
- * Returns SJ_ERANGE when no useful margin exists (the FP32 mode then
- * computes every distance in FP64), SJ_EINVAL for bad arguments. */
+ * (Section IV-B: g_min_j = min_j - eps, g_max_j = max_j + eps), with FP32
+ * records relative to g_min (SJ_FRAME_GRID).  The join kernel computes an
+ * FP32 squared distance s32 from coordinates relative to the centre of the
+ * query's cell (see the derivation in csrc/margin.cu); s32 <= *lo implies
+ * membership by the exact FP64 test, s32 > *hi implies non-membership, and
+ * only values in between are recomputed in FP64.  *w32 receives the cell
+ * side rounded to FP32.  Host-only, no device needed.  Returns SJ_ERANGE
+ * when this frame has no useful margin (the FP32 mode then takes the cell
+ * frame, see sj_frame, or computes in FP64), SJ_EINVAL for bad arguments. */
 SJ_API sj_status sj_fp32_margin(int d, double eps, const double *gmin, const double *gmax,
                                 float *w32, float *lo, float *hi);
+
+/* The same margin for the records of frame `frame` (SJ_FRAME_GRID, the
+ * frame of sj_fp32_margin, or SJ_FRAME_CELL; see sj_frame).  In the cell
+ * frame a record holds fl32(fl64(fl64(x_j - g_min_j) - fl64(4 K_j w))) with
+ * K_j = floor(c_j / 4) for the point's cell c_j, and the kernel moves a
+ * candidate of the neighbouring frame by 4 * w32 (derivation in
+ * csrc/margin.cu).  Errors as sj_fp32_margin, SJ_EINVAL for another frame. */
+SJ_API sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
+                                      const double *gmax, int frame, float *w32, float *lo,
+                                      float *hi);
 
 /* ------------------------------------------------------------------ */
 /* Self-join.                                                         */
@@ -386,7 +412,8 @@ typedef struct {
     int32_t wpb;             /* warps per block (0: by occupancy) */
     int32_t tuned;           /* 0 defaults, 1 from the tuner's cache, 2 tuned by this call */
     int32_t staging;         /* staged pairs per warp (0: by dimension) */
-    int32_t reserved_;
+    int32_t frame;           /* sj_frame of the FP32 filter used by the call;
+                                -1 when every distance was computed in FP64 */
 } sj_stats;
 
 SJ_API sj_status sj_last_stats(const sj_ctx *ctx, sj_stats *out);

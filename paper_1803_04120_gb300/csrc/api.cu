@@ -234,7 +234,8 @@ sj_status prepare_launch(Error &err, sj_ctx *ctx, Index &ix, cudaStream_t s) {
     return tune_launch(err, ix, ctx->launch, s, &ctx->launch_tuned);
 }
 
-void record_launch(sj_ctx *ctx) {
+void record_launch(sj_ctx *ctx, const Index &ix) {
+    ctx->stats.frame = (ctx->cfg.prec == SJ_PREC_FP32_RECHECK && ix.g.fp32_ok) ? ix.g.frame : -1;
     ctx->stats.grab = ctx->launch.grab;
     ctx->stats.nbuf = ctx->launch.nbuf;
     ctx->stats.wpb = ctx->launch.wpb;
@@ -541,12 +542,15 @@ sj_status host_join(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
         SJ_TRY(ensure_rec64(err, ix, ctx->s_main));
     SJ_TRY(prepare_launch(err, ctx, ix, ctx->s_main));
     SJ_TRY(run_batches(err, ctx, ix, sink));
-    record_launch(ctx);
+    record_launch(ctx, ix);
     if (sink.res && ctx->cfg.sorted) sort_result(sink.res);
     return SJ_OK;
 }
 
-void reset_stats(sj_ctx *ctx) { std::memset(&ctx->stats, 0, sizeof(ctx->stats)); }
+void reset_stats(sj_ctx *ctx) {
+    std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.frame = -1;
+}
 
 }  // namespace
 }  // namespace sj
@@ -574,6 +578,7 @@ void sj_config_default(sj_config *cfg) {
     cfg->staging = -1;
     cfg->wpb = -1;
     cfg->slots = -1;
+    cfg->frame = SJ_FRAME_AUTO;
 }
 
 const char *sj_status_str(sj_status st) {
@@ -600,6 +605,7 @@ sj_status sj_create(const sj_config *cfg, sj_ctx **out) {
     if (cfg) c = *cfg;
     if (c.prec != SJ_PREC_FP64 && c.prec != SJ_PREC_FP32_RECHECK) return SJ_EINVAL;
     if (c.lookup < SJ_LOOKUP_AUTO || c.lookup > SJ_LOOKUP_SEARCH) return SJ_EINVAL;
+    if (c.frame < SJ_FRAME_AUTO || c.frame > SJ_FRAME_CELL) return SJ_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
         cudaGetLastError();
@@ -663,7 +669,7 @@ sj_status sj_build_index(sj_ctx *ctx, const double *pts, uint64_t n, int d, doub
     sj_index *ix = new sj_index();
     ix->device = ctx->device;
     double t0 = now_ms();
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->s_main, ix->ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix->ix);
     if (st == SJ_OK && ctx->cfg.prec == SJ_PREC_FP64) st = ensure_rec64(sc.err, ix->ix, ctx->s_main);
     if (st == SJ_OK) st = read_counts(sc.err, ix->ix, ctx->s_main);
     if (st != SJ_OK) {
@@ -704,6 +710,8 @@ sj_status sj_index_info(const sj_index *ix, sj_index_desc *out) {
         out->ng[j] = x.g.ng[j];
     }
     out->device_bytes = x.bytes;
+    out->fp32 = x.g.fp32_ok;
+    out->frame = x.g.frame;
     return SJ_OK;
 }
 
@@ -729,7 +737,7 @@ static sj_status device_join_on(sj_ctx *ctx, Error &err, Index &ix, uint32_t *d_
     SJ_TRY(join_once(err, ctx, ix, item_begin, item_end, 1, reinterpret_cast<uint2 *>(d_pairs), cap,
                      count_only, s, r));
     *count = r[0];
-    record_launch(ctx);
+    record_launch(ctx, ix);
     ctx->stats.pairs = r[0];
     ctx->stats.evaluations = r[1];
     ctx->stats.rechecks = r[2];
@@ -751,7 +759,7 @@ sj_status sj_selfjoin_device(sj_ctx *ctx, const double *pts, uint64_t n, int d, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double t0 = now_ms();
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, s, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix);
     double t1 = now_ms();
     if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, d_pairs, cap_pairs, count, s, 0);
     free_index(ix, s);
@@ -776,7 +784,7 @@ sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double t0 = now_ms();
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, s, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix);
     double t1 = now_ms();
     uint32_t lo = 0, hi = 0;
     if (st == SJ_OK) st = shard_items(sc.err, ix, rank, world, s, &lo, &hi);
@@ -819,12 +827,13 @@ sj_status sj_join2_device(sj_ctx *ctx, const double *R, uint64_t nR, const doubl
             mm[2 * j] = std::min(mR[2 * j], mS[2 * j]);
             mm[2 * j + 1] = std::max(mR[2 * j + 1], mS[2 * j + 1]);
         }
-        SJ_TRY(build_index(err, static_cast<const double *>(dS.p), nS, d, eps, ctx->cfg.lookup, s, ixS, mm));
-        SJ_TRY(build_index(err, static_cast<const double *>(dR.p), nR, d, eps, ctx->cfg.lookup, s, ixR, mm));
+        SJ_TRY(build_index(err, static_cast<const double *>(dS.p), nS, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ixS, mm));
+        SJ_TRY(build_index(err, static_cast<const double *>(dR.p), nR, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ixR, mm));
         const double t1 = now_ms();
         ctx->stats.ms_index = t1 - t0;
         JoinLaunch l = default_launch(ctx);
         l.unicomp = 0;   // R and S differ: every query searches all adjacent cells
+        ctx->stats.frame = (l.prec_fp32 && ixS.g.fp32_ok) ? ixS.g.frame : -1;
         if (!(l.prec_fp32 && ixS.g.fp32_ok)) {
             SJ_TRY(ensure_rec64(err, ixS, s));
             SJ_TRY(ensure_rec64(err, ixR, s));
@@ -923,7 +932,7 @@ sj_status sj_selfjoin_count(sj_ctx *ctx, const double *pts, uint64_t n, int d, d
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
     double t0 = now_ms();
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->s_main, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix);
     if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, nullptr, 0, count, ctx->s_main, 1);
     free_index(ix, ctx->s_main);
     cudaStreamSynchronize(ctx->s_main);
@@ -940,7 +949,7 @@ static sj_status host_join_from_pts(sj_ctx *ctx, const double *pts, uint64_t n, 
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
     double t0 = now_ms();
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->s_main, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix);
     double t1 = now_ms();
     if (st == SJ_OK) st = host_join(sc.err, ctx, ix, sink);
     free_index(ix, ctx->s_main);

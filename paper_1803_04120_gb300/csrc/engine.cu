@@ -627,7 +627,7 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
             continue;
         }
         Error e2;
-        const sj_status gs = geometry_from_bounds(e2, mm, J.d, J.n, J.eps, m.g);
+        const sj_status gs = geometry_from_bounds(e2, mm, J.d, J.n, J.eps, e->cfg.frame, m.g);
         if (gs != SJ_OK) { job_fail(i, gs, e2.msg); continue; }
         uint64_t dense_limit = std::max<uint64_t>(16 * J.n, 1ull << 25);
         if (m.g.grid_cells > dense_limit || m.g.grid_cells + 1 > kEngMaxLut) {

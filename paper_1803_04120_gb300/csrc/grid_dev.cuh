@@ -30,8 +30,10 @@ __host__ __device__ inline double from_order_key(unsigned long long k) {
 // What the cell-id kernels need of the geometry.
 struct CellParams {
     int d;
+    int frame;                 // sj_frame of the FP32 records
     double gmin[kMaxDim];
     double inv_w;
+    double w;
     int64_t ng[kMaxDim];
     uint64_t stride[kMaxDim];
 };
@@ -40,7 +42,9 @@ inline CellParams cell_params(const Geometry &g) {
     CellParams cp;
     std::memset(&cp, 0, sizeof(cp));
     cp.d = g.d;
+    cp.frame = g.frame;
     cp.inv_w = 1.0 / g.w;
+    cp.w = g.w;
     for (int j = 0; j < g.d; ++j) {
         cp.gmin[j] = g.gmin[j];
         cp.ng[j] = g.ng[j];
@@ -132,8 +136,12 @@ __device__ __forceinline__ void cell_coords(const double *p, uint64_t h, const C
     }
 }
 
-// FP32 record of the point at cell-order position k: y_j = fl32(x_j - g_min_j)
-// for j < d, then the point id, zero padding up to rs floats.
+// FP32 record of the point at cell-order position k, then the point id and
+// zero padding up to rs floats.  Grid frame: y_j = fl32(x_j - g_min_j).
+// Cell frame: y_j = fl32(fl64(x_j - g_min_j) - fl64(4 K_j w)) with
+// K_j = floor(c_j / 4) for the point's cell coordinate c_j (the formula of
+// linear_cell), so that y_j lies within about four cell sides of 0 at any
+// extent of the grid.
 __device__ __forceinline__ void write_rec32(const double *__restrict__ pts,
                                             const uint32_t *__restrict__ A, uint64_t k,
                                             const CellParams &cp, int rs, float *__restrict__ rec) {
@@ -141,8 +149,19 @@ __device__ __forceinline__ void write_rec32(const double *__restrict__ pts,
     const double *p = pts + (uint64_t)i * cp.d;
     float *r = rec + k * rs;
 #pragma unroll
-    for (int j = 0; j < kMaxDim; ++j)
-        if (j < cp.d) r[j] = __double2float_rn(__dsub_rn(p[j], cp.gmin[j]));
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < cp.d) {
+            const double a = __dsub_rn(p[j], cp.gmin[j]);
+            double y = a;
+            if (cp.frame == SJ_FRAME_CELL) {
+                int64_t c = (int64_t)floor(__dmul_rn(a, cp.inv_w));
+                c = c < 0 ? 0 : c;
+                c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+                y = __dsub_rn(a, __dmul_rn((double)(4 * (c >> 2)), cp.w));
+            }
+            r[j] = __double2float_rn(y);
+        }
+    }
     r[cp.d] = __uint_as_float(i);
     for (int j = cp.d + 1; j < rs; ++j) r[j] = 0.0f;
 }

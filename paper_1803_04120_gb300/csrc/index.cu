@@ -162,7 +162,7 @@ inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kT
 // side w = eps (1 + 2^-16), |g_j| = floor((g_max_j - g_min_j) / w) + 1,
 // strides with dimension 1 fastest, and the FP32 margin.
 sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, uint64_t n,
-                               double eps, Geometry &g) {
+                               double eps, int frame_mode, Geometry &g) {
     g = Geometry();
     g.d = d;
     g.n = n;
@@ -184,7 +184,7 @@ sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, 
         stride *= (uint64_t)g.ng[j];
     }
     g.grid_cells = stride;
-    fp32_margin(g);  // margin.cu
+    fp32_margin(g, frame_mode);  // margin.cu
     return SJ_OK;
 }
 
@@ -225,7 +225,8 @@ sj_status bounds_of(Error &err, const double *d_pts, uint64_t n, int d, cudaStre
 }
 
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
-                      int lookup_mode, cudaStream_t s, Index &ix, const unsigned long long *given_mm) {
+                      int lookup_mode, int frame_mode, cudaStream_t s, Index &ix,
+                      const unsigned long long *given_mm) {
     ix = Index();
     ix.owner_stream = s;
     if (pts_any == nullptr || n == 0 || d < 1 || d > kMaxDim || !(eps > 0.0) || !std::isfinite(eps))
@@ -270,7 +271,7 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
 
     // geometry (Section IV-B)
     {
-        const sj_status gst = geometry_from_bounds(err, h_mm, d, n, eps, g);
+        const sj_status gst = geometry_from_bounds(err, h_mm, d, n, eps, frame_mode, g);
         if (gst != SJ_OK) { dev_free(scratch, s); return gst; }
     }
 
@@ -281,15 +282,7 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
                  (lookup_mode == SJ_LOOKUP_AUTO && g.grid_cells <= dense_limit);
     ix.dense = dense ? 1 : 0;
 
-    CellParams cp;
-    std::memset(&cp, 0, sizeof(cp));
-    cp.d = d;
-    cp.inv_w = 1.0 / g.w;
-    for (int j = 0; j < d; ++j) {
-        cp.gmin[j] = g.gmin[j];
-        cp.ng[j] = g.ng[j];
-        cp.stride[j] = g.stride[j];
-    }
+    const CellParams cp = cell_params(g);
 
     DevBuf key, val, skey_buf, head;
     auto cleanup = [&]() {
@@ -484,18 +477,10 @@ sj_status build_index_static(Error &err, const double *d_pts, uint64_t n, int d,
         stride *= (uint64_t)g.ng[j];
     }
     g.grid_cells = stride;
-    fp32_margin(g);
+    fp32_margin(g, SJ_FRAME_AUTO);
     ix.dense = 1;
 
-    CellParams cp;
-    std::memset(&cp, 0, sizeof(cp));
-    cp.d = d;
-    cp.inv_w = 1.0 / g.w;
-    for (int j = 0; j < d; ++j) {
-        cp.gmin[j] = g.gmin[j];
-        cp.ng[j] = g.ng[j];
-        cp.stride[j] = g.stride[j];
-    }
+    const CellParams cp = cell_params(g);
     uint64_t maxng = 1;
     for (int j = 0; j < d; ++j) maxng = (uint64_t)g.ng[j] > maxng ? (uint64_t)g.ng[j] : maxng;
     ix.mwords = (uint32_t)((maxng + 31) / 32);

@@ -323,10 +323,14 @@ __device__ __forceinline__ void emit_slot(Pipe &st, const WarpSmem &ws, const Jo
 // from shared memory with 16-byte loads, moves them into the frame of the
 // home cell centre o and packs them in pairs.  Slots past the chunk end get
 // z = 0, |z|^2 = +inf (never a member) and id 0xffffffff.
-template <int D, int CPL>
+// WRAP (cell-frame records): a candidate stored in the neighbouring
+// four-cell frame is moved by k = -rint(z / (4 w32)) frame steps,
+// z - 4 w32 k, which is exact.
+template <int D, int CPL, bool WRAP>
 __device__ __forceinline__ void load_candidates(const unsigned char *buf, int rs, uint32_t clen,
-                                                int lane, const float *o_smem, f2_t (*z)[D],
-                                                f2_t *qq2, uint32_t *cid) {
+                                                int lane, const float *o_smem, float w4,
+                                                float inv_w4, f2_t (*z)[D], f2_t *qq2,
+                                                uint32_t *cid) {
     constexpr int V = (D + 1 + 3) / 4;    // float4 per record (rs = 4 V)
     float o[D];
 #pragma unroll
@@ -356,7 +360,8 @@ __device__ __forceinline__ void load_candidates(const unsigned char *buf, int rs
                 float q2 = 0.0f;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    const float zz = __fsub_rn(r[j], o[j]);
+                    float zz = __fsub_rn(r[j], o[j]);
+                    if (WRAP) zz = __fmaf_rn(-w4, rintf(__fmul_rn(zz, inv_w4)), zz);
                     za[h2][j] = zz;
                     q2 = __fmaf_rn(zz, zz, q2);
                 }
@@ -484,7 +489,8 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
     if (F32) {
         float o[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) o[j] = ((float)c[j] + 0.5f) * a.w32;
+        for (int j = 0; j < D; ++j)
+            o[j] = ((float)(a.frame == SJ_FRAME_CELL ? (c[j] & 3) : c[j]) + 0.5f) * a.w32;
         if (lane < (int)nq) {
             const float *r = reinterpret_cast<const float *>(rec + (size_t)(q0 + lane) * rsb);
             float *qd = reinterpret_cast<float *>(ws.q[sl]) + (size_t)lane * a.qrs;
@@ -640,7 +646,10 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         const float hi32 = a.hi32, lo32 = a.lo32;
         f2_t z[NP][D], qq2[NP];
         uint32_t cid[CPL];
-        load_candidates<D, CPL>(buf, a.rs, clen, lane, hd->o, z, qq2, cid);
+        if (a.frame == SJ_FRAME_CELL)
+            load_candidates<D, CPL, true>(buf, a.rs, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
+        else
+            load_candidates<D, CPL, false>(buf, a.rs, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
         const float *qbase = reinterpret_cast<const float *>(ws.q[sl]);
         if (UNI && ch == 0) {
             // UNICOMP: the item's self-pairs, one per query point; every
@@ -1148,6 +1157,8 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     const Index &q = qix ? *qix : ix;
     if (qix && (uni || !(f32 || q.rec64.p)))
         return fail(err, SJ_EINVAL, "two-set joins search all adjacent cells and need both records");
+    if (qix && f32 && (q.g.frame != g.frame || !q.g.fp32_ok))
+        return fail(err, SJ_EINVAL, "two-set join indexes with different FP32 frames");
     memset(&a, 0, sizeof(a));
     a.qrec32 = static_cast<const float *>(q.rec32.p);
     a.qrec64 = static_cast<const double *>(q.rec64.p);
@@ -1179,6 +1190,9 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.lo32 = g.lo32;
     a.hi32 = g.hi32;
     a.w32 = g.w32;
+    a.w4 = g.w4;
+    a.inv_w4 = g.inv_w4;
+    a.frame = f32 ? g.frame : SJ_FRAME_GRID;
     a.E2 = g.E2;
     a.out = out;
     a.cap = cap;

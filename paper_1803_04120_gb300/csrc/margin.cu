@@ -1,7 +1,8 @@
 // margin.cu -- the proven error margin of the FP32 distance filter.
 //
-// The search-and-refine kernel evaluates, for a query p of home cell c and
-// a candidate q of an adjacent cell, in FP32 with round-to-nearest:
+// Grid frame (frame 0).  The search-and-refine kernel evaluates, for a
+// query p of home cell c and a candidate q of an adjacent cell, in FP32 with
+// round-to-nearest:
 //     o_j  = fl(fl(c_j + 1/2) * w32)                 home cell centre, w32 = fl32(w)
 //     z_j  = fl(y_j - o_j)                           y_j = fl32(fl64(x_j - g_min_j))
 //     pp   = fma chain of z_p,j^2,  qq = fma chain of z_q,j^2
@@ -27,27 +28,77 @@
 //     s32 <= lo := (R1 - H)^2 - E  =>  |Delta| <= R1  =>  s64 <= E2.
 // hi is rounded up and lo down to FP32 after a relative safety factor of
 // 2^-20 that covers the rounding of this host computation.
+//
+// Cell frame (frame 1).  The records hold coordinates relative to a frame
+// that repeats every four cells: with K_j = floor(c_j / 4) for the point's
+// own cell c_j and T_j = fl64(4 K_j w),
+//     y_j  = fl32(fl64(fl64(x_j - g_min_j) - T_j)),      0 <=~ y_j <~ 4 w,
+// and the home cell centre is o_j = fl(fl((c_j mod 4) + 1/2) * w32).  A
+// candidate of an adjacent cell may lie in the neighbouring frame (K differs
+// by dK in {-1, 0, 1}); the kernel undoes that with
+//     k = rint(fl(z_raw * inv4)),  z = z_raw - 4 w32 k,    inv4 = fl32(1 / (4 w32)),
+// which is exact (Sterbenz: |z_raw| is within a factor 2 of 4 w32 when
+// k != 0) and gives k = -dK while the home-frame value stays below 2 w in
+// magnitude.  The error no longer grows with the extent X_j except through
+// FP64 roundings:
+//  (a') P_j = x_j - g_min_j - 4 K_j w lies in [(m - 3vU) w, (m + 1 + 3vU) w]
+//       with m = c_j mod 4; |fl(x_j - g_min_j) - T_j - P_j| <= v (2 X_j + w);
+//       so |fl(x_j - g_min_j) - T_j| <= Y_j = (4 + 3vU) w + v (2 X_j + w) and
+//       |y_j - P_j| <= rho_j = v (2 X_j + w) + v Y_j + u (1 + v) Y_j + 2^-150;
+//  (c') |o_j - (m + 1/2) w| <= oerr = 3.1 u (4 w);
+//  Rp_j = (1+u)((1/2 + 3vU) w + rho_j + oerr); before the wrap
+//  |z_raw,j| <= Zr_j = (1+u)((15/2 + 3vU) w + rho_j + oerr); after it
+//  Rq_j = (3/2 + 3vU) w + rho_j + oerr + u Zr_j + 4 u w, the last term for the
+//  frame step 4 w32 against 4 w;
+//  (d') eta_j = 2 rho_j + u (Rp_j + Zr_j) + 4 u w (o cancels in z_p - z_q).
+// The wrap is valid when every Rq_j < 1.99 w; (e), (f), hi and lo as above.
+//
+// Frame choice (automatic): the grid frame needs no wrap step in the kernel
+// and is kept while its band is below 2^-10 E2; otherwise the frame with
+// the narrower band; FP64 arithmetic when neither has a usable margin.
 #include <cmath>
 
 #include "sj_internal.cuh"
 
 namespace sj {
 
-void fp32_margin(Geometry &g) {
+namespace {
+
+struct FrameMargin {
+    bool ok = false;
+    float lo32 = -1.0f, hi32 = 0.0f;
+};
+
+FrameMargin frame_margin(const Geometry &g, int frame) {
+    FrameMargin fm;
     const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
     const int d = g.d;
     const double w = g.w;
     double U = 0.0;
     for (int j = 0; j < d; ++j) U = std::fmax(U, (double)g.ng[j]);
     double H2 = 0.0, Rp2 = 0.0, Rq2 = 0.0, Xmax = 0.0;
+    bool wrap_ok = true;
     for (int j = 0; j < d; ++j) {
         const double X = (g.gmax[j] - g.gmin[j]) * (1.0 + 4.0 * v);
         Xmax = std::fmax(Xmax, X);
-        const double rho = X * (u + v + u * v) + std::ldexp(1.0, -150);
-        const double oerr = 3.1 * u * (X + w);
-        const double rp = (1.0 + u) * ((0.5 + 3.0 * v * U) * w + rho + oerr);
-        const double rq = (1.0 + u) * ((1.5 + 3.0 * v * U) * w + rho + oerr);
-        const double eta = 2.0 * rho + u * (rp + rq) * (1.0 + u);
+        double rp, rq, eta;
+        if (frame == SJ_FRAME_GRID) {
+            const double rho = X * (u + v + u * v) + std::ldexp(1.0, -150);
+            const double oerr = 3.1 * u * (X + w);
+            rp = (1.0 + u) * ((0.5 + 3.0 * v * U) * w + rho + oerr);
+            rq = (1.0 + u) * ((1.5 + 3.0 * v * U) * w + rho + oerr);
+            eta = 2.0 * rho + u * (rp + rq) * (1.0 + u);
+        } else {
+            const double Y = (4.0 + 3.0 * v * U) * w + v * (2.0 * X + w);
+            const double rho =
+                v * (2.0 * X + w) + v * Y + u * (1.0 + v) * Y + std::ldexp(1.0, -150);
+            const double oerr = 3.1 * u * 4.0 * w;
+            rp = (1.0 + u) * ((0.5 + 3.0 * v * U) * w + rho + oerr);
+            const double zr = (1.0 + u) * ((7.5 + 3.0 * v * U) * w + rho + oerr);
+            rq = (1.5 + 3.0 * v * U) * w + rho + oerr + u * zr + 4.0 * u * w;
+            eta = 2.0 * rho + u * (rp + zr) + 4.0 * u * w;
+            if (!(rq < 1.99 * w)) wrap_ok = false;
+        }
         H2 += eta * eta;
         Rp2 += rp * rp;
         Rq2 += rq * rq;
@@ -62,14 +113,11 @@ void fp32_margin(Geometry &g) {
                      (1.0 + safety);
     const double g64 = (d + 3) * v / (1.0 - (d + 3) * v);
     const double a64 = 2.0 * d * std::ldexp(1.0, -1074);
-
-    g.fp32_ok = 0;
-    g.lo32 = -1.0f;
-    g.hi32 = 0.0f;
-    g.w32 = (float)w;
-    if (!std::isfinite(g.E2) || !(Xmax < std::ldexp(1.0, 60)) || g.E2 < std::ldexp(1.0, -100) ||
-        !((Rp + Rq) * (Rp + Rq) < std::ldexp(1.0, 100)) || !std::isfinite(g.w32))
-        return;
+    const float w32 = (float)w;
+    if (!wrap_ok || !std::isfinite(g.E2) || !(Xmax < std::ldexp(1.0, 60)) ||
+        g.E2 < std::ldexp(1.0, -100) || !((Rp + Rq) * (Rp + Rq) < std::ldexp(1.0, 100)) ||
+        !(w32 > 0.0f) || !std::isfinite(4.0f * w32))
+        return fm;
     const double R2 = std::sqrt((g.E2 + a64) / (1.0 - g64)) * (1.0 + safety);
     const double hi = ((R2 + H) * (R2 + H) + E) * (1.0 + safety);
     float hi32 = (float)hi;
@@ -84,17 +132,56 @@ void fp32_margin(Geometry &g) {
         }
     }
     // a band wider than half of E2 makes the filter pointless: compute in FP64
-    if ((double)hi32 - (lo32 > 0.0f ? (double)lo32 : 0.0) > 0.5 * g.E2) return;
-    g.lo32 = lo32;
-    g.hi32 = hi32;
+    if ((double)hi32 - (lo32 > 0.0f ? (double)lo32 : 0.0) > 0.5 * g.E2) return fm;
+    fm.ok = true;
+    fm.lo32 = lo32;
+    fm.hi32 = hi32;
+    return fm;
+}
+
+double band_of(const FrameMargin &m) {
+    return (double)m.hi32 - (m.lo32 > 0.0f ? (double)m.lo32 : 0.0);
+}
+
+}  // namespace
+
+void fp32_margin(Geometry &g, int frame_mode) {
+    g.fp32_ok = 0;
+    g.frame = SJ_FRAME_GRID;
+    g.lo32 = -1.0f;
+    g.hi32 = 0.0f;
+    g.w32 = (float)g.w;
+    g.w4 = 4.0f * g.w32;
+    g.inv_w4 = (float)(1.0 / (4.0 * (double)g.w32));
+    const FrameMargin m0 = frame_margin(g, SJ_FRAME_GRID), m1 = frame_margin(g, SJ_FRAME_CELL);
+    int pick = -1;
+    if (frame_mode == SJ_FRAME_GRID) {
+        pick = m0.ok ? SJ_FRAME_GRID : -1;
+    } else if (frame_mode == SJ_FRAME_CELL) {
+        pick = m1.ok ? SJ_FRAME_CELL : -1;
+    } else if (m0.ok && band_of(m0) <= std::ldexp(g.E2, -10)) {
+        pick = SJ_FRAME_GRID;
+    } else if (m1.ok && (!m0.ok || band_of(m1) < band_of(m0))) {
+        pick = SJ_FRAME_CELL;
+    } else if (m0.ok) {
+        pick = SJ_FRAME_GRID;
+    }
+    if (pick < 0) return;
+    const FrameMargin &m = pick == SJ_FRAME_CELL ? m1 : m0;
+    g.frame = pick;
+    g.lo32 = m.lo32;
+    g.hi32 = m.hi32;
     g.fp32_ok = 1;
 }
 
 }  // namespace sj
 
-extern "C" sj_status sj_fp32_margin(int d, double eps, const double *gmin, const double *gmax,
-                                    float *w32, float *lo, float *hi) {
-    if (d < 1 || d > sj::kMaxDim || !gmin || !gmax || !(eps > 0.0) || !std::isfinite(eps))
+namespace {
+
+sj_status margin_entry(int d, double eps, const double *gmin, const double *gmax, int frame,
+                       float *w32, float *lo, float *hi) {
+    if (d < 1 || d > sj::kMaxDim || !gmin || !gmax || !(eps > 0.0) || !std::isfinite(eps) ||
+        (frame != SJ_FRAME_GRID && frame != SJ_FRAME_CELL))
         return SJ_EINVAL;
     sj::Geometry g;
     g.d = d;
@@ -108,9 +195,22 @@ extern "C" sj_status sj_fp32_margin(int d, double eps, const double *gmin, const
         if (!(cells < 2147483648.0)) return SJ_ERANGE;
         g.ng[j] = (int64_t)cells;
     }
-    sj::fp32_margin(g);
+    sj::fp32_margin(g, frame);
     if (w32) *w32 = g.w32;
     if (lo) *lo = g.lo32;
     if (hi) *hi = g.hi32;
     return g.fp32_ok ? SJ_OK : SJ_ERANGE;
+}
+
+}  // namespace
+
+extern "C" sj_status sj_fp32_margin(int d, double eps, const double *gmin, const double *gmax,
+                                    float *w32, float *lo, float *hi) {
+    return margin_entry(d, eps, gmin, gmax, SJ_FRAME_GRID, w32, lo, hi);
+}
+
+extern "C" sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
+                                          const double *gmax, int frame, float *w32, float *lo,
+                                          float *hi) {
+    return margin_entry(d, eps, gmin, gmax, frame, w32, lo, hi);
 }

@@ -444,6 +444,7 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
         }
     }
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.frame = -1;   // each job chooses its own frame
     ctx->stats.pairs = pairs;
     ctx->stats.evaluations = evals;
     ctx->stats.rechecks = rechecks;

@@ -75,6 +75,8 @@ struct Geometry {
     // unusable and the FP32 mode falls back to FP64 arithmetic.
     float lo32 = -1.0f, hi32 = 0.0f;
     float w32 = 0.0f;                  // fl32(w): cell side in the FP32 frame
+    float w4 = 0.0f, inv_w4 = 0.0f;    // 4 w32 and fl32(1 / (4 w32)): cell frame step
+    int frame = 0;                     // sj_frame of the FP32 records (grid or cell)
     int fp32_ok = 0;
 };
 
@@ -103,13 +105,16 @@ struct Index {
     cudaStream_t owner_stream = nullptr;
 };
 
-// FP32 filter margin of a geometry (margin.cu): sets w32, lo32, hi32, fp32_ok.
-void fp32_margin(Geometry &g);
+// FP32 filter margin of a geometry (margin.cu): chooses the record frame
+// (frame_mode: an sj_frame) and sets frame, w32, w4, inv_w4, lo32, hi32 and
+// fp32_ok.
+void fp32_margin(Geometry &g, int frame_mode);
 
 // given_mm: per-dimension bounds (order keys, min/max interleaved) of a grid
 // shared with another point set; null to bound the points themselves.
+// frame_mode: the sj_frame of the FP32 records (SJ_FRAME_AUTO chooses).
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
-                      int lookup_mode, cudaStream_t s, Index &ix,
+                      int lookup_mode, int frame_mode, cudaStream_t s, Index &ix,
                       const unsigned long long *given_mm = nullptr);
 // Per-dimension min/max (order keys) of device points and a non-finite flag
 // (synchronises s).
@@ -156,6 +161,8 @@ struct JoinArgs {
     uint64_t stride[kMaxDim];
     float lo32, hi32;
     float w32;                      // cell side in the FP32 frame
+    float w4, inv_w4;               // cell frame: frame step 4 w32 and its inverse
+    int frame;                      // sj_frame of the FP32 records
     double E2;
     int qrs;                        // staged query record stride (elements)
     // output
@@ -227,7 +234,7 @@ void tune_clear();
 const void *multi_join_fn();
 // Geometry of Section IV-B from per-dimension bounds (index.cu).
 sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, uint64_t n,
-                               double eps, Geometry &g);
+                               double eps, int frame_mode, Geometry &g);
 int n_templates(int d, bool uni);
 
 // qix: the query-side index of a two-set join (same grid as ix), else null.

@@ -17,7 +17,8 @@ uniform in [0, 100]^n, FP64):
     lower the realised mean).
   * ``clustered(n, d, seed)`` -- skewed density: 90 % of the points from
     1,000 isotropic Gaussian clusters (centres uniform in [0, 100]^d, sigma
-    log-uniform in [0.1, 5], cluster chosen uniformly), 10 % uniform.
+    log-uniform in [0.1, 5], cluster chosen uniformly), 10 % uniform;
+    ``side`` widens the domain of the centres and the background.
   * ``serving_requests(count, seed)`` -- a request stream of self-joins of
     uneven size and dimension with Poisson arrivals.
 """
@@ -78,9 +79,11 @@ def eps_for_neighbors(n: int, d: int, k: float, side: float = 100.0) -> float:
 
 
 def clustered(n: int, d: int, seed: int, clusters: int = 1000,
-              frac_clustered: float = 0.9) -> np.ndarray:
-    """Skewed-density points (see module docstring), FP64, not clipped."""
-    centres = unit(seed, 1, clusters * d).reshape(clusters, d) * 100.0
+              frac_clustered: float = 0.9, side: float = 100.0) -> np.ndarray:
+    """Skewed-density points (see module docstring), FP64, not clipped.
+    ``side`` scales the domain of the centres and of the background
+    (the cluster widths stay in [0.1, 5])."""
+    centres = unit(seed, 1, clusters * d).reshape(clusters, d) * side
     lu = unit(seed, 2, clusters)
     sigma = np.exp(math.log(0.1) + lu * (math.log(5.0) - math.log(0.1)))
     n_cl = int(round(n * frac_clustered))
@@ -91,7 +94,7 @@ def clustered(n: int, d: int, seed: int, clusters: int = 1000,
     u2 = unit(seed, 5, m)
     g = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
     pts_cl = centres[which] + g.reshape(n_cl, d) * sigma[which][:, None]
-    pts_bg = unit(seed, 6, (n - n_cl) * d).reshape(n - n_cl, d) * 100.0
+    pts_bg = unit(seed, 6, (n - n_cl) * d).reshape(n - n_cl, d) * side
     pts = np.concatenate([pts_cl, pts_bg], axis=0)
     perm = np.argsort(raw64(seed, 7, n), kind="stable")
     return np.ascontiguousarray(pts[perm])
@@ -139,7 +142,18 @@ def config4(d: int) -> dict:
     return dict(name=f"clustered-{d}d-5M", n=5_000_000, d=d, seed=40 + d, eps=0.5)
 
 
+def wide_clustered(d: int) -> dict:
+    """2,000,000 clustered points spread over [0, 1e6]^d (20,000 clusters of
+    about 90 points), eps = 0.5: about 2e6 cells per dimension, where the
+    FP32 records relative to g_min lose the precision the filter needs."""
+    return dict(name=f"wide-clustered-{d}d-2M", n=2_000_000, d=d, seed=60 + d, eps=0.5,
+                clusters=20000, side=1e6)
+
+
 def make_points(cfg: dict) -> np.ndarray:
+    if cfg["name"].startswith("wide-clustered"):
+        return clustered(cfg["n"], cfg["d"], cfg["seed"], clusters=cfg["clusters"],
+                         side=cfg["side"])
     if cfg["name"].startswith("clustered"):
         return clustered(cfg["n"], cfg["d"], cfg["seed"])
     return uniform(cfg["n"], cfg["d"], cfg["seed"])

@@ -24,6 +24,7 @@ SJ_EINVAL, SJ_ENOMEM, SJ_ERANGE, SJ_ECUDA = -1, -2, -3, -4
 SJ_ETIMEOUT, SJ_EBUSY, SJ_EOVERFLOW, SJ_ENOTFOUND = -5, -6, -7, -8
 SJ_PREC_FP64, SJ_PREC_FP32_RECHECK = 0, 1
 SJ_LOOKUP_AUTO, SJ_LOOKUP_DENSE, SJ_LOOKUP_SEARCH = 0, 1, 2
+SJ_FRAME_AUTO, SJ_FRAME_GRID, SJ_FRAME_CELL = -1, 0, 1
 
 # symbols the header declares (checked by the CPU test suite)
 ABI_FUNCTIONS = (
@@ -34,7 +35,7 @@ ABI_FUNCTIONS = (
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
-    "sj_selfjoin_bruteforce_device", "sj_join2_device",
+    "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
 )
 
 
@@ -52,7 +53,8 @@ class sj_config(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("serve_mem_bytes", ctypes.c_uint64), ("grab", ctypes.c_int32),
                 ("nbuf", ctypes.c_int32), ("staging", ctypes.c_int32), ("wpb", ctypes.c_int32),
-                ("slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("slots", ctypes.c_int32), ("frame", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class sj_index_desc(ctypes.Structure):
@@ -60,7 +62,8 @@ class sj_index_desc(ctypes.Structure):
                 ("eps", ctypes.c_double), ("cell_width", ctypes.c_double),
                 ("n_cells", ctypes.c_uint64), ("grid_cells", ctypes.c_uint64),
                 ("gmin", ctypes.c_double * 8), ("gmax", ctypes.c_double * 8),
-                ("ng", ctypes.c_int64 * 8), ("device_bytes", ctypes.c_uint64)]
+                ("ng", ctypes.c_int64 * 8), ("device_bytes", ctypes.c_uint64),
+                ("fp32", ctypes.c_int32), ("frame", ctypes.c_int32)]
 
 
 class sj_stats(ctypes.Structure):
@@ -71,7 +74,7 @@ class sj_stats(ctypes.Structure):
                 ("ms_join", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64), ("grab", ctypes.c_int32),
                 ("nbuf", ctypes.c_int32), ("wpb", ctypes.c_int32), ("tuned", ctypes.c_int32),
-                ("staging", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("staging", ctypes.c_int32), ("frame", ctypes.c_int32)]
 
 
 class sj_job(ctypes.Structure):
@@ -143,6 +146,9 @@ def load(build: bool = True):
                                       ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+            "sj_fp32_margin_frame": (i32, [i32, f64, P, P, i32, ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_float)]),
             "sj_selfjoin_noalloc": (i32, [P, u64, i32, f64, P, u64, ctypes.POINTER(ctypes.c_uint64),
                                           P, ctypes.c_char_p, ctypes.c_size_t]),
             "sj_selfjoin_multi": (i32, [P, ctypes.POINTER(sj_job), u64, PP, ctypes.POINTER(ctypes.c_int)]),
@@ -216,7 +222,7 @@ class Context:
                  device: int = 0, lookup: int = SJ_LOOKUP_AUTO, profile: bool = False,
                  max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True,
                  grab: int = -1, nbuf: int = -1, staging: int = -1, wpb: int = -1,
-                 slots: int = -1):
+                 slots: int = -1, frame: int = SJ_FRAME_AUTO):
         lib = load()
         cfg = sj_config()
         lib.sj_config_default(ctypes.byref(cfg))
@@ -225,6 +231,7 @@ class Context:
         cfg.device, cfg.lookup, cfg.profile = device, lookup, int(profile)
         cfg.max_inflight, cfg.serve_mem_bytes, cfg.autotune = max_inflight, serve_mem_bytes, int(autotune)
         cfg.grab, cfg.nbuf, cfg.staging, cfg.wpb, cfg.slots = grab, nbuf, staging, wpb, slots
+        cfg.frame = frame
         h = ctypes.c_void_p()
         st = lib.sj_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != SJ_OK:
@@ -484,7 +491,7 @@ class Index:
         return dict(n=dsc.n, d=d, dense=dsc.dense, eps=dsc.eps, cell_width=dsc.cell_width,
                     n_cells=dsc.n_cells, grid_cells=dsc.grid_cells,
                     gmin=list(dsc.gmin)[:d], gmax=list(dsc.gmax)[:d], ng=list(dsc.ng)[:d],
-                    device_bytes=dsc.device_bytes)
+                    device_bytes=dsc.device_bytes, fp32=dsc.fp32, frame=dsc.frame)
 
     def sj_index_export(self):
         """(B, G, A, M) as numpy arrays (Section IV-C)."""
@@ -530,6 +537,18 @@ def sj_fp32_margin(d: int, eps: float, gmin, gmax):
     w, lo, hi = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
     st = lib.sj_fp32_margin(d, float(eps), gmin.ctypes.data, gmax.ctypes.data,
                             ctypes.byref(w), ctypes.byref(lo), ctypes.byref(hi))
+    return st, w.value, lo.value, hi.value
+
+
+def sj_fp32_margin_frame(d: int, eps: float, gmin, gmax, frame: int):
+    """(status, w32, lo, hi) of the FP32 filter margin for records of the
+    given frame (SJ_FRAME_GRID or SJ_FRAME_CELL), host only."""
+    lib = load()
+    gmin = np.ascontiguousarray(gmin, dtype=np.float64)
+    gmax = np.ascontiguousarray(gmax, dtype=np.float64)
+    w, lo, hi = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    st = lib.sj_fp32_margin_frame(d, float(eps), gmin.ctypes.data, gmax.ctypes.data, int(frame),
+                                  ctypes.byref(w), ctypes.byref(lo), ctypes.byref(hi))
     return st, w.value, lo.value, hi.value
 
 

@@ -16,10 +16,12 @@ def run(ctx, r, s, eps):
     return np.sort(sj.pairs_to_keys(out[:n].cpu().numpy().view(np.uint32)))
 
 
-@pytest.mark.parametrize("prec", [sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64])
-def test_join2_matches_oracle(prec):
+@pytest.mark.parametrize("prec,frame", [(sj.SJ_PREC_FP32_RECHECK, sj.SJ_FRAME_AUTO),
+                                        (sj.SJ_PREC_FP32_RECHECK, sj.SJ_FRAME_CELL),
+                                        (sj.SJ_PREC_FP64, sj.SJ_FRAME_AUTO)])
+def test_join2_matches_oracle(prec, frame):
     rng = np.random.default_rng(5)
-    with sj.Context(prec=prec) as ctx:
+    with sj.Context(prec=prec, frame=frame) as ctx:
         for d in range(1, 9):
             r = rng.uniform(0, 20, size=(int(rng.integers(1, 3000)), d))
             s = rng.uniform(5, 30, size=(int(rng.integers(1, 3000)), d))

@@ -34,10 +34,12 @@ def mixed_jobs(seed, count, n_lo=50, n_hi=6000):
     return jobs
 
 
-@pytest.mark.parametrize("prec", [sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64])
-def test_multi_matches_oracle(prec):
+@pytest.mark.parametrize("prec,frame", [(sj.SJ_PREC_FP32_RECHECK, sj.SJ_FRAME_AUTO),
+                                        (sj.SJ_PREC_FP32_RECHECK, sj.SJ_FRAME_CELL),
+                                        (sj.SJ_PREC_FP64, sj.SJ_FRAME_AUTO)])
+def test_multi_matches_oracle(prec, frame):
     jobs = mixed_jobs(1, 40)
-    with sj.Context(prec=prec) as ctx:
+    with sj.Context(prec=prec, frame=frame) as ctx:
         res = ctx.sj_selfjoin_multi(jobs)
         st = ctx.sj_last_stats()
     assert len(res) == len(jobs)

@@ -356,16 +356,97 @@ def test_config3_full_size_streamed_digest(d):
     assert np.array_equal(deg, o_deg.astype(np.int64))
 
 
-def test_fp32_mode_falls_back_to_fp64_when_the_margin_is_unusable():
-    """A range of 5e6 against eps = 1 leaves no usable FP32 margin: the FP32
-    mode must then compute in FP64 (no rechecks) and still be exact."""
-    torch = pytest.importorskip("torch")
+def test_wide_grid_uses_the_cell_frame_and_grid_frame_falls_back():
+    """A range of 5e6 against eps = 1: the grid frame has no usable FP32
+    margin and computes in FP64 (no rechecks); the automatic choice takes the
+    cell frame and keeps the FP32 filter.  Both are exact."""
     rng = np.random.default_rng(77)
     x = np.stack([rng.uniform(0, 5e6, 20000), rng.uniform(0, 3.0, 20000)], axis=1)
     x[:200, 0] = rng.uniform(1e6, 1e6 + 20.0, 200)     # a dense stretch with many pairs
     st, _, _, _ = sj.sj_fp32_margin(2, 1.0, x.min(axis=0) - 1.0, x.max(axis=0) + 1.0)
     assert st == sj.SJ_ERANGE
-    with sj.Context(prec=sj.SJ_PREC_FP32_RECHECK) as ctx:
+    want = np.sort(orc.grid_join(x, 1.0))
+    with sj.Context(frame=sj.SJ_FRAME_GRID) as ctx:
         got = np.sort(sj.pairs_to_keys(ctx.sj_selfjoin(x, 1.0)))
-        assert ctx.sj_last_stats()["rechecks"] == 0
-    assert np.array_equal(got, np.sort(orc.grid_join(x, 1.0)))
+        stats = ctx.sj_last_stats()
+        assert stats["rechecks"] == 0 and stats["frame"] == -1
+    assert np.array_equal(got, want)
+    with sj.Context() as ctx:
+        got = np.sort(sj.pairs_to_keys(ctx.sj_selfjoin(x, 1.0)))
+        assert ctx.sj_last_stats()["frame"] == sj.SJ_FRAME_CELL
+        idx = ctx.sj_build_index(x, 1.0)
+        info = idx.sj_index_info()
+        assert info["fp32"] == 1 and info["frame"] == sj.SJ_FRAME_CELL
+        idx.free()
+    assert np.array_equal(got, want)
+
+
+@pytest.fixture(scope="module")
+def cell_ctxs():
+    out = {}
+    for uni in (True, False):
+        for lookup in (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH):
+            out[(uni, lookup)] = sj.Context(unicomp=uni, lookup=lookup, frame=sj.SJ_FRAME_CELL)
+    yield out
+    for c in out.values():
+        c.close()
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_cell_frame_random_all_dims(cell_ctxs, d):
+    rng = np.random.default_rng(3000 + d)
+    for trial in range(3):
+        n = int(rng.integers(50, 3000))
+        pts = rng.uniform(-10, 10, size=(n, d)) + (0.0 if trial == 0 else 1e4)
+        if trial == 1:
+            pts[n // 3: 2 * n // 3] = pts[: 2 * n // 3 - n // 3]   # duplicates
+        k = float(rng.choice([4.0, 40.0, 400.0]))
+        eps = (k * 20.0 ** d / (n * datagen.ball_volume(d))) ** (1.0 / d)
+        want = orc.grid_join(pts, eps)
+        for key, ctx in cell_ctxs.items():
+            assert_same(gpu_keys(ctx, pts, eps), want, f"cell frame d={d} trial={trial} {key}")
+            assert ctx.sj_last_stats()["frame"] == sj.SJ_FRAME_CELL
+
+
+def test_cell_frame_band_pairs_and_frame_boundaries(cell_ctxs):
+    """Pairs at the threshold (the FP64 recheck decides) and pairs across
+    the four-cell frame boundaries, far from the origin of the grid."""
+    rng = np.random.default_rng(78)
+    for d in (2, 3, 6):
+        eps = 0.37
+        w = eps * (1.0 + 2.0 ** -16)
+        base = 3e5 + rng.uniform(0, 30, size=(400, d))
+        g0 = base[:, 0].min() - eps
+        for p in base[::2]:
+            c = int((p[0] - g0) / w)
+            p[0] = g0 + (4 * (c // 4) + 4) * w - 0.5 * eps
+        extra = []
+        for p in base:
+            v = rng.normal(size=d)
+            v /= np.linalg.norm(v)
+            v[0] = abs(v[0])
+            f = 1.0 + float(rng.choice([-3, -1, 0, 1, 3])) * 2.0 ** -24 * float(rng.random())
+            if rng.random() < 0.5:
+                f = 1.0 + float(rng.integers(-4, 5)) * 2.0 ** -52
+            extra.append(p + v * eps * f)
+        pts = np.concatenate([base, np.array(extra)])
+        want = orc.grid_join(pts, eps)
+        for key, ctx in cell_ctxs.items():
+            assert_same(gpu_keys(ctx, pts, eps), want, f"cell band d={d} {key}")
+        ctx = cell_ctxs[(True, sj.SJ_LOOKUP_AUTO)]
+        ctx.sj_selfjoin(pts, eps)
+        assert ctx.sj_last_stats()["rechecks"] > 0
+
+
+def test_cell_frame_config1_lattice_and_boundaries(cell_ctxs):
+    cfg = datagen.CONFIG1
+    pts = datagen.make_points(cfg)
+    want = orc.bruteforce(pts, cfg["eps"])
+    for key, ctx in cell_ctxs.items():
+        assert_same(gpu_keys(ctx, pts, cfg["eps"]), want, f"cell config1 {key}")
+    # unit lattice with eps = 1: 2d + 1 pairs per interior point (closed form)
+    for d, m in ((2, 30), (3, 12)):
+        lat = np.stack(np.meshgrid(*[np.arange(m, dtype=np.float64)] * d, indexing="ij"), -1).reshape(-1, d)
+        total = m ** d + 2 * d * (m - 1) * m ** (d - 1)
+        for key, ctx in cell_ctxs.items():
+            assert len(ctx.sj_selfjoin(lat, 1.0)) == total, (d, key)

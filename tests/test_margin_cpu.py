@@ -129,3 +129,138 @@ def test_margin_rejects_unusable_grids():
     assert st in (sj.SJ_ERANGE,)
     st, _, _, _ = sj.sj_fp32_margin(2, -1.0, np.zeros(2), np.ones(2))
     assert st == sj.SJ_EINVAL
+
+
+# ---------------------------------------------------------------- cell frame
+
+def rec_cell(x, gmin, w, inv_w, ng):
+    """The cell-frame record of one coordinate and its cell: y =
+    fl32(fl64(fl64(x - g_min) - fl64(4 K w))), K = floor(c / 4)."""
+    a = r64(F(x) - F(gmin))
+    c = min(max(int(math.floor(r64(a * F(inv_w)))), 0), ng - 1)
+    T = r64(F(4 * (c >> 2)) * F(w))
+    return r32(r64(a - T)), c
+
+
+def kernel_s32_cell(p, q, gmin, w, w32, inv_w, ng):
+    """s32 as the kernel computes it on cell-frame records: the home cell
+    centre within the four-cell frame, the candidate moved by whole frame
+    steps k = rint(z / (4 w32)) (ties to even), then the same expanded sum
+    as in the grid frame.  Returns (s32, number of frame steps taken)."""
+    d = len(p)
+    inv4 = r32(r64(F(1) / (4 * F(w32))))
+    zp, zq, steps = [], [], 0
+    for j in range(d):
+        yp, cp = rec_cell(p[j], gmin[j], w, inv_w, ng[j])
+        yq, _ = rec_cell(q[j], gmin[j], w, inv_w, ng[j])
+        o = r32(r32(F(cp & 3) + F(1, 2)) * F(w32))
+        zp.append(r32(yp - o))
+        zr = r32(yq - o)
+        k = round(r32(zr * inv4))            # round half to even, like rintf
+        steps += k != 0
+        zq.append(r32(-(4 * F(w32)) * k + zr))
+    pp = F(0)
+    qq = F(0)
+    for j in range(d):
+        pp = r32(zp[j] * zp[j] + pp)
+        qq = r32(zq[j] * zq[j] + qq)
+    acc = r32(qq + pp)
+    for j in range(d):
+        acc = r32((-2 * zp[j]) * zq[j] + acc)
+    return acc, steps
+
+
+@pytest.mark.parametrize("d,eps,scale,offset", [
+    (2, 0.5, 1e7, 0.0), (3, 1.0, 1e6, 1e9), (2, 0.31915, 100.0, 0.0), (6, 13.55112, 100.0, 0.0),
+    (8, 0.9, 10.0, 5.0), (1, 1e-3, 1e5, -3e5), (4, 2e-4, 4e4, 0.0)])
+def test_cell_frame_margin_sound_on_threshold_pairs(d, eps, scale, offset):
+    rng = np.random.default_rng(int(scale) % 1000 + 31 * d)
+    w = eps * (1.0 + 2.0 ** -16)
+    pts = offset + rng.uniform(0, scale, size=(60, d))
+    # half of the points sit just below a four-cell frame boundary in
+    # dimension 0, so that their partners fall into the next frame
+    g0 = float(np.min(pts[:, 0])) - eps
+    for p in pts[::2]:
+        c = int((p[0] - g0) / w)
+        p[0] = g0 + (4 * (c // 4) + 4) * w - 0.3 * eps
+    extra = []
+    for p in pts:
+        v = rng.normal(size=d)
+        v /= np.linalg.norm(v)
+        v[0] = abs(v[0])
+        for f in (1.0, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -52, 1.0 + 3e-7, 1.0 - 3e-7,
+                  1.0 + 2e-6, 1.0 - 2e-6):
+            extra.append(p + v * eps * f)
+    allp = np.concatenate([pts, np.array(extra)])
+    gmin = allp.min(axis=0) - eps
+    gmax = allp.max(axis=0) + eps
+    st, w32, lo, hi = sj.sj_fp32_margin_frame(d, eps, gmin, gmax, sj.SJ_FRAME_CELL)
+    assert st == sj.SJ_OK
+    E2 = r64(F(eps) * F(eps))
+    inv_w = 1.0 / w
+    ng = [int(math.floor((gmax[j] - gmin[j]) / w)) + 1 for j in range(d)]
+    # the band does not grow with the extent of the grid
+    assert (hi - max(lo, 0.0)) / float(E2) < 2000 * 2.0 ** -24
+    checked = stepped = 0
+    for k, p in enumerate(pts):
+        cells = [rec_cell(p[j], gmin[j], w, inv_w, ng[j])[1] for j in range(d)]
+        for q in extra[7 * k: 7 * k + 7]:
+            cq = [rec_cell(q[j], gmin[j], w, inv_w, ng[j])[1] for j in range(d)]
+            if max(abs(a - b) for a, b in zip(cells, cq)) > 1:
+                continue
+            for a, b, ca, cb in ((p, q, cells, cq), (q, p, cq, cells)):
+                s, steps = kernel_s32_cell(a, b, gmin, w, w32, inv_w, ng)
+                mem = exact_member(a, b, E2)
+                if s <= F(lo):
+                    assert mem, (d, k)
+                if s > F(hi):
+                    assert not mem, (d, k)
+                stepped += steps > 0
+                checked += 1
+    assert checked > 200
+    assert stepped > 20      # pairs across a frame boundary were exercised
+
+
+def test_cell_frame_exact_difference_across_frames():
+    """On coordinates exact in FP32 (multiples of 2^-8 and w a power of 2)
+    every step above is exact, so the kernel's z_p - z_q must equal x_p - x_q
+    exactly, also when q lies in the neighbouring four-cell frame and the
+    grid is 2^30 cells wide."""
+    eps = 2.0 ** -3 * (1.0 - 2.0 ** -20)
+    w = eps * (1.0 + 2.0 ** -16)
+    gmin = 0.0
+    ng = 2 ** 30
+    inv_w = 1.0 / w
+    for c in (3, 7, 4 * 12345 + 3, 2 ** 29 + 3, 2 ** 30 - 5):
+        x = (c + 0.75) * w
+        x = float(F(x).limit_denominator(2 ** 40))
+        for dx in (0.3 * eps, 0.9 * eps, -0.8 * eps):
+            y = x + dx
+            yp, cp = rec_cell(x, gmin, w, inv_w, ng)
+            yq, cq = rec_cell(y, gmin, w, inv_w, ng)
+            w32 = r32(F(w))
+            o = r32(r32(F(cp & 3) + F(1, 2)) * w32)
+            inv4 = r32(r64(F(1) / (4 * w32)))
+            zr = r32(yq - o)
+            k = round(r32(zr * inv4))
+            assert k == -((cq >> 2) - (cp >> 2))
+            zq = r32(-(4 * w32) * k + zr)
+            assert zq == zr - 4 * w32 * k           # the frame step is exact
+            zp = r32(yp - o)
+            assert abs(float(zp - zq) + dx) < 8 * 2.0 ** -24 * w + 4 * abs(c) * 2.0 ** -53 * w
+
+
+def test_cell_frame_margin_at_any_extent():
+    # the grid frame gives up on wide grids; the cell frame keeps a narrow band
+    for d, X in ((1, 1e8), (2, 1e8), (3, 5e8), (8, 1e7)):
+        gmin, gmax = np.zeros(d), np.full(d, X)
+        st0, _, _, _ = sj.sj_fp32_margin_frame(d, 1.0, gmin, gmax, sj.SJ_FRAME_GRID)
+        st1, _, lo, hi = sj.sj_fp32_margin_frame(d, 1.0, gmin, gmax, sj.SJ_FRAME_CELL)
+        assert st0 == sj.SJ_ERANGE
+        assert st1 == sj.SJ_OK and 0.0 < lo < 1.0 < hi and hi - lo < 2000 * 2.0 ** -24
+    st, _, _, _ = sj.sj_fp32_margin_frame(2, 1.0, np.zeros(2), np.ones(2), 7)
+    assert st == sj.SJ_EINVAL
+    # where the grid frame is tight both frames give similar bands
+    st0, _, lo0, hi0 = sj.sj_fp32_margin_frame(3, 2.0, np.zeros(3), np.full(3, 100.0), sj.SJ_FRAME_GRID)
+    st1, _, lo1, hi1 = sj.sj_fp32_margin_frame(3, 2.0, np.zeros(3), np.full(3, 100.0), sj.SJ_FRAME_CELL)
+    assert st0 == st1 == sj.SJ_OK and hi1 - lo1 < hi0 - lo0
