@@ -39,8 +39,9 @@
  *     pairs ascending by the 64-bit key (i << 32) | j.
  *   - Errors: SJ_EINVAL for a NULL argument, n = 0, d outside [1, 8],
  *     eps <= 0 or non-finite, or any NaN/Inf coordinate; SJ_ERANGE when
- *     n >= 2^32, a dimension would need 2^31 or more cells, or the product of
- *     the cell counts reaches 2^63; SJ_ENOMEM when device or pinned memory
+ *     n >= 2^32 or a dimension would need 2^31 or more cells (grids whose
+ *     cell count reaches 2^63 are ordered by coordinate tuple, see
+ *     sj_lookup); SJ_ENOMEM when device or pinned memory
  *     runs out; SJ_ECUDA for any other CUDA error (the message is in
  *     sj_last_error); SJ_ETIMEOUT when a bounded device wait expired;
  *     SJ_EOVERFLOW when a caller-provided output buffer is too small (the
@@ -88,8 +89,18 @@ typedef enum { SJ_PREC_FP64 = 0, SJ_PREC_FP32_RECHECK = 1 } sj_precision;
  * SJ_LOOKUP_SEARCH binary-searches the sorted array B of non-empty cell ids,
  * as the paper does.  SJ_LOOKUP_DENSE adds a table over all cells of the grid
  * (4 bytes per cell) that answers a lookup with one load; SJ_LOOKUP_AUTO uses
- * it when the grid has at most max(2^25, 16 n) cells.  Results are identical. */
-typedef enum { SJ_LOOKUP_AUTO = 0, SJ_LOOKUP_DENSE = 1, SJ_LOOKUP_SEARCH = 2 } sj_lookup;
+ * it when the grid has at most max(2^25, 16 n) cells.  SJ_LOOKUP_COORDS
+ * orders the cells by their coordinate tuples (c_n, ..., c_1) instead of
+ * linear ids (the same order, built with one radix sort per group of
+ * dimensions) and binary-searches the tuples; no B is built.  It is taken
+ * automatically when the grid has 2^63 or more cells, where linear ids do
+ * not fit in 64 bits.  Results are identical in every mode. */
+typedef enum {
+    SJ_LOOKUP_AUTO = 0,
+    SJ_LOOKUP_DENSE = 1,
+    SJ_LOOKUP_SEARCH = 2,
+    SJ_LOOKUP_COORDS = 3
+} sj_lookup;
 
 /* Coordinate frame of the FP32 point records of SJ_PREC_FP32_RECHECK.
  * SJ_FRAME_GRID stores fl32(x_j - g_min_j): its rounding error grows with
@@ -183,7 +194,8 @@ typedef struct {
     double eps;
     double cell_width;       /* w */
     uint64_t n_cells;        /* |G| = |B|, non-empty cells */
-    uint64_t grid_cells;     /* product of |g_j|, all cells of the grid */
+    uint64_t grid_cells;     /* product of |g_j|, all cells of the grid
+                                (2^64 - 1 when it reaches 2^63) */
     double gmin[8], gmax[8]; /* g_min_j, g_max_j */
     int64_t ng[8];           /* |g_j| */
     uint64_t device_bytes;   /* device memory the index holds */
@@ -194,7 +206,9 @@ typedef struct {
 SJ_API sj_status sj_index_info(const sj_index *idx, sj_index_desc *out);
 
 /* Copies the Section IV-C arrays to host memory (any pointer may be NULL):
- *   B[n_cells]          sorted linear ids of the non-empty cells;
+ *   B[n_cells]          sorted linear ids of the non-empty cells (not
+ *                       built for cells ordered by coordinate tuple:
+ *                       a non-NULL B then gives SJ_ERANGE);
  *   G[n_cells + 1]      cell h holds A[G[h] .. G[h+1]);
  *   A[n]                point ids in cell order;
  *   M[d * ceil(max_j |g_j| / 32)]  bit c of row j is set when some point

@@ -604,7 +604,7 @@ sj_status sj_create(const sj_config *cfg, sj_ctx **out) {
     sj_config_default(&c);
     if (cfg) c = *cfg;
     if (c.prec != SJ_PREC_FP64 && c.prec != SJ_PREC_FP32_RECHECK) return SJ_EINVAL;
-    if (c.lookup < SJ_LOOKUP_AUTO || c.lookup > SJ_LOOKUP_SEARCH) return SJ_EINVAL;
+    if (c.lookup < SJ_LOOKUP_AUTO || c.lookup > SJ_LOOKUP_COORDS) return SJ_EINVAL;
     if (c.frame < SJ_FRAME_AUTO || c.frame > SJ_FRAME_CELL) return SJ_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
@@ -720,6 +720,7 @@ sj_status sj_index_export(const sj_index *ix, uint64_t *B, uint32_t *G, uint32_t
     const Index &x = ix->ix;
     cudaSetDevice(ix->device);
     cudaError_t e = cudaDeviceSynchronize();
+    if (B && !x.B.p) return SJ_ERANGE;   // cells ordered by coordinate tuple: no linear ids
     if (e == cudaSuccess && B) e = cudaMemcpy(B, x.B.p, x.n_cells * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && G) e = cudaMemcpy(G, x.G.p, (x.n_cells + 1) * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && A) e = cudaMemcpy(A, x.A.p, x.g.n * 4, cudaMemcpyDeviceToHost);

@@ -53,20 +53,23 @@ inline CellParams cell_params(const Geometry &g) {
     return cp;
 }
 
-// Linear cell id of point p: c_j = floor((x_j - g_min_j) * (1 / w)) in FP64,
-// clamped to the grid, id = sum_j c_j * stride_j (dimension 1 fastest).
+// Cell coordinate of point p in dimension j: c_j = floor((x_j - g_min_j) *
+// (1 / w)) in FP64, clamped to the grid.  Every part of the index computes
+// a point's cell with this one formula.
+__device__ __forceinline__ int64_t cell_coord(const double *p, int j, const CellParams &cp) {
+    const double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
+    int64_t c = (int64_t)floor(q);
+    c = c < 0 ? 0 : c;
+    c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+    return c;
+}
+
+// Linear cell id of point p: id = sum_j c_j * stride_j (dimension 1 fastest).
 __device__ __forceinline__ uint64_t linear_cell(const double *p, const CellParams &cp) {
     uint64_t id = 0;
 #pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) {
-        if (j < cp.d) {
-            double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
-            int64_t c = (int64_t)floor(q);
-            c = c < 0 ? 0 : c;
-            c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
-            id += (uint64_t)c * cp.stride[j];
-        }
-    }
+    for (int j = 0; j < kMaxDim; ++j)
+        if (j < cp.d) id += (uint64_t)cell_coord(p, j, cp) * cp.stride[j];
     return id;
 }
 
@@ -122,10 +125,7 @@ __device__ __forceinline__ void cell_coords(const double *p, uint64_t h, const C
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j) {
         if (j < cp.d) {
-            const double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
-            int64_t c = (int64_t)floor(q);
-            c = c < 0 ? 0 : c;
-            c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+            const int64_t c = cell_coord(p, j, cp);
             cc[h * cp.d + j] = (int32_t)c;
             if (M) {
                 uint32_t *w = &M[(uint64_t)j * mwords + (c >> 5)];
@@ -154,9 +154,7 @@ __device__ __forceinline__ void write_rec32(const double *__restrict__ pts,
             const double a = __dsub_rn(p[j], cp.gmin[j]);
             double y = a;
             if (cp.frame == SJ_FRAME_CELL) {
-                int64_t c = (int64_t)floor(__dmul_rn(a, cp.inv_w));
-                c = c < 0 ? 0 : c;
-                c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+                const int64_t c = cell_coord(p, j, cp);
                 y = __dsub_rn(a, __dmul_rn((double)(4 * (c >> 2)), cp.w));
             }
             r[j] = __double2float_rn(y);

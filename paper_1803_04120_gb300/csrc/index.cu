@@ -153,6 +153,61 @@ __global__ void __launch_bounds__(kThreads) item_fill_kernel(const uint32_t *__r
     for (uint32_t b = 0; b < nb; ++b) items[o + b] = make_uint2((uint32_t)h, b);
 }
 
+// Coordinate-tuple order (grids of 2^63 or more cells).  The points are
+// sorted by one group of dimensions at a time, dimension 1 first, with the
+// stable radix sort; a group packs the cell coordinates of its dimensions
+// into one 64-bit key (higher dimensions in higher bits).
+struct TupleGroup {
+    int j0, j1;                    // dimensions [j0, j1)
+    int shift[kMaxDim];            // bit position of c_j in the key
+};
+
+__global__ void __launch_bounds__(kThreads) iota_kernel(uint32_t *__restrict__ v, uint64_t n) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(kThreads) tuple_key_kernel(const double *__restrict__ pts,
+                                                             const uint32_t *__restrict__ val,
+                                                             uint64_t n, CellParams cp, TupleGroup tg,
+                                                             uint64_t *__restrict__ key) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double *p = pts + (uint64_t)val[k] * cp.d;
+    uint64_t y = 0;
+    for (int j = tg.j0; j < tg.j1; ++j) y |= (uint64_t)cell_coord(p, j, cp) << tg.shift[j];
+    key[k] = y;
+}
+
+// head[k] = 1 where the cell of the point at sorted position k differs from
+// the previous one.
+__global__ void __launch_bounds__(kThreads) tuple_head_kernel(const double *__restrict__ pts,
+                                                              const uint32_t *__restrict__ A,
+                                                              uint64_t n, CellParams cp,
+                                                              uint32_t *__restrict__ head) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t h = 1;
+    if (k > 0) {
+        const double *p = pts + (uint64_t)A[k] * cp.d, *q = pts + (uint64_t)A[k - 1] * cp.d;
+        h = 0;
+        for (int j = 0; j < cp.d; ++j) h |= cell_coord(p, j, cp) != cell_coord(q, j, cp);
+    }
+    head[k] = h;
+}
+
+// G from the exclusive scan of the head flags (no B: there are no linear ids).
+__global__ void __launch_bounds__(kThreads) tuple_rle_kernel(const uint32_t *__restrict__ hscan,
+                                                             uint64_t n,
+                                                             const uint32_t *__restrict__ n_cells,
+                                                             uint32_t *__restrict__ G) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t next = k + 1 < n ? hscan[k + 1] : *n_cells;
+    if (next != hscan[k]) G[hscan[k]] = (uint32_t)k;
+    if (k == 0) G[*n_cells] = (uint32_t)n;
+}
+
 inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -170,7 +225,6 @@ sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, 
     g.E2 = eps * eps;
     g.w = eps * (1.0 + std::ldexp(1.0, -16));
     double total = 1.0;
-    uint64_t stride = 1;
     for (int j = 0; j < d; ++j) {
         const double mn = from_order_key(mm[2 * j]), mx = from_order_key(mm[2 * j + 1]);
         g.gmin[j] = mn - eps;
@@ -179,11 +233,20 @@ sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, 
         if (!(cells < 2147483648.0)) return fail(err, SJ_ERANGE, "a dimension needs 2^31 or more cells");
         g.ng[j] = (int64_t)cells;
         total *= cells;
-        if (!(total < 9.2e18)) return fail(err, SJ_ERANGE, "grid has 2^63 or more cells");
-        g.stride[j] = stride;
-        stride *= (uint64_t)g.ng[j];
     }
-    g.grid_cells = stride;
+    if (total < 9.2e18) {
+        uint64_t stride = 1;
+        for (int j = 0; j < d; ++j) {
+            g.stride[j] = stride;
+            stride *= (uint64_t)g.ng[j];
+        }
+        g.grid_cells = stride;
+    } else {
+        // linear ids would not fit in 64 bits: cells are ordered by their
+        // coordinate tuples instead (the same order)
+        g.huge = 1;
+        g.grid_cells = ~0ull;
+    }
     fp32_margin(g, frame_mode);  // margin.cu
     return SJ_OK;
 }
@@ -278,9 +341,11 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     // 2-3. cell ids and the sort by cell
     uint64_t dense_limit = (uint64_t)16 * n;
     if (dense_limit < (1ull << 25)) dense_limit = 1ull << 25;
-    bool dense = (lookup_mode == SJ_LOOKUP_DENSE && g.grid_cells < (1ull << 32) - 1) ||
-                 (lookup_mode == SJ_LOOKUP_AUTO && g.grid_cells <= dense_limit);
+    const bool tuple = g.huge || lookup_mode == SJ_LOOKUP_COORDS;
+    bool dense = !tuple && ((lookup_mode == SJ_LOOKUP_DENSE && g.grid_cells < (1ull << 32) - 1) ||
+                            (lookup_mode == SJ_LOOKUP_AUTO && g.grid_cells <= dense_limit));
     ix.dense = dense ? 1 : 0;
+    ix.tuple = tuple ? 1 : 0;
 
     const CellParams cp = cell_params(g);
 
@@ -310,6 +375,31 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
                                                         static_cast<uint32_t *>(val.p), lut, n,
                                                         static_cast<uint32_t *>(ix.A.p), skey); note_launch();
         SJ_BC(cudaGetLastError());
+    } else if (tuple) {
+        uint32_t *v = static_cast<uint32_t *>(val.p);
+        iota_kernel<<<grid_for(n), kThreads, 0, s>>>(v, n); note_launch();
+        SJ_BC(cudaGetLastError());
+        for (int j0 = 0; j0 < d;) {
+            TupleGroup tg;
+            std::memset(&tg, 0, sizeof(tg));
+            tg.j0 = j0;
+            int bits = 0, j = j0;
+            while (j < d) {
+                int bj = 1;
+                while (bj < 31 && ((uint64_t)(g.ng[j] - 1) >> bj)) ++bj;
+                if (bits + bj > 64) break;
+                tg.shift[j] = bits;
+                bits += bj;
+                ++j;
+            }
+            tg.j1 = j;
+            tuple_key_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, v, n, cp, tg,
+                                                              static_cast<uint64_t *>(key.p)); note_launch();
+            SJ_BC(cudaGetLastError());
+            SJ_B(radix_sort_pairs(err, static_cast<uint64_t *>(key.p), v, n, bits, s));
+            j0 = j;
+        }
+        SJ_BC(cudaMemcpyAsync(ix.A.p, val.p, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     } else {
         cell_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, cp, static_cast<uint64_t *>(key.p),
                                                      static_cast<uint32_t *>(val.p), nullptr); note_launch();
@@ -325,15 +415,26 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     // 4. B and G
     SJ_B(dev_alloc(err, head, n * sizeof(uint32_t), s));
     uint32_t *hs = static_cast<uint32_t *>(head.p);
-    head_kernel<<<grid_for(n), kThreads, 0, s>>>(skey, n, hs); note_launch();
+    if (tuple)
+        tuple_head_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, static_cast<const uint32_t *>(ix.A.p),
+                                                           n, cp, hs);
+    else
+        head_kernel<<<grid_for(n), kThreads, 0, s>>>(skey, n, hs);
+    note_launch();
     SJ_BC(cudaGetLastError());
     SJ_B(exclusive_scan_u32(err, hs, hs, n, d_counts + 1, s));
-    SJ_B(dev_alloc(err, ix.B, n * sizeof(uint64_t), s));
     SJ_B(dev_alloc(err, ix.G, (n + 1) * sizeof(uint32_t), s));
     // the scan total counts heads before position n = |G|
-    rle_kernel<<<grid_for(n), kThreads, 0, s>>>(skey, hs, n, d_counts + 1,
-                                                 static_cast<uint64_t *>(ix.B.p),
-                                                 static_cast<uint32_t *>(ix.G.p)); note_launch();
+    if (tuple) {
+        tuple_rle_kernel<<<grid_for(n), kThreads, 0, s>>>(hs, n, d_counts + 1,
+                                                          static_cast<uint32_t *>(ix.G.p));
+    } else {
+        SJ_B(dev_alloc(err, ix.B, n * sizeof(uint64_t), s));
+        rle_kernel<<<grid_for(n), kThreads, 0, s>>>(skey, hs, n, d_counts + 1,
+                                                     static_cast<uint64_t *>(ix.B.p),
+                                                     static_cast<uint32_t *>(ix.G.p));
+    }
+    note_launch();
     SJ_BC(cudaGetLastError());
 
     // 5. cell coordinates and M_j

@@ -235,6 +235,28 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *__restrict__
     return lo;
 }
 
+// First cell in [0, n) whose coordinate tuple is not below (b_{D-1}, ...,
+// b_1, x), compared from dimension D down to dimension 1: the order of the
+// linear ids, for grids whose linear ids do not fit in 64 bits.
+template <int D>
+__device__ __forceinline__ uint32_t lower_bound_tuple(const int32_t *__restrict__ cc, uint32_t n,
+                                                      const int32_t *b, int32_t x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const int32_t *t = cc + (uint64_t)mid * D;
+        int cmp = 0;
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            const int32_t tj = __ldg(&t[j]);
+            const int32_t kj = j ? b[j] : x;
+            if (cmp == 0) cmp = tj < kj ? -1 : (tj > kj ? 1 : 0);
+        }
+        if (cmp < 0) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 // Per-item header kept in shared memory (one per item slot).
 struct ItemHdr {
     uint32_t h, qb, nq, home_len, K, nchunks, nranges, pad;
@@ -464,6 +486,11 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
             if (a.dense) {
                 beg = __ldg(&a.lut[id_lo]);
                 e = __ldg(&a.lut[id_hi + 1]);
+            } else if (a.tuple) {
+                const uint32_t hl = lower_bound_tuple<D>(a.cc, n_cells, b, xlo);
+                const uint32_t hh = lower_bound_tuple<D>(a.cc, n_cells, b, xhi + 1);
+                beg = __ldg(&a.G[hl]);
+                e = __ldg(&a.G[hh]);
             } else {
                 const uint32_t hl = lower_bound_u64(a.B, n_cells, id_lo);
                 const uint32_t hh = lower_bound_u64(a.B, n_cells, id_hi + 1);
@@ -1180,6 +1207,7 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.item_stride = cfg.item_stride > 0 ? cfg.item_stride : 1;
     a.mwords = ix.mwords;
     a.dense = ix.dense;
+    a.tuple = ix.tuple;
     a.rs = f32 ? ix.rs32 : ix.rs64;
     a.n_templates = n_templates(d, uni);
     SJ_TRY(template_table(err, d, uni, &a.tmpl));

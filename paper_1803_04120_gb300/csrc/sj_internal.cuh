@@ -69,7 +69,10 @@ struct Geometry {
     double gmin[kMaxDim] = {}, gmax[kMaxDim] = {};
     int64_t ng[kMaxDim] = {};
     uint64_t stride[kMaxDim] = {};     // linear id = sum c_j * stride[j], stride[0] = 1
-    uint64_t grid_cells = 0;           // product of ng
+    uint64_t grid_cells = 0;           // product of ng (saturated when huge)
+    // 1: the grid has 2^63 or more cells, so linear ids do not fit in 64
+    // bits; cells are then ordered and searched by coordinate tuple
+    int huge = 0;
     // FP32 filter thresholds: s32 <= lo32 -> member, s32 > hi32 -> not a
     // member, otherwise recompute in FP64.  fp32_ok = 0 when the margin is
     // unusable and the FP32 mode falls back to FP64 arithmetic.
@@ -84,6 +87,7 @@ struct Geometry {
 struct Index {
     Geometry g;
     int dense = 0;                 // dense lookup table built
+    int tuple = 0;                 // cells sorted and searched by coordinate tuple (no B)
     uint64_t n_cells = 0;          // |G|
     uint32_t n_items = 0;          // work items (cell, query block)
     uint32_t max_cell = 0;         // largest cell population
@@ -154,6 +158,7 @@ struct JoinArgs {
     uint32_t n_cells;
     uint32_t mwords;
     int dense;
+    int tuple;                      // cells searched by coordinate tuple (cc), not by B
     int rs;                         // record stride in elements of the mode's type
     int n_templates;
     const uint32_t *tmpl;           // row templates of (d, UNICOMP), device memory

@@ -23,7 +23,7 @@ SJ_OK, SJ_PENDING = 0, 1
 SJ_EINVAL, SJ_ENOMEM, SJ_ERANGE, SJ_ECUDA = -1, -2, -3, -4
 SJ_ETIMEOUT, SJ_EBUSY, SJ_EOVERFLOW, SJ_ENOTFOUND = -5, -6, -7, -8
 SJ_PREC_FP64, SJ_PREC_FP32_RECHECK = 0, 1
-SJ_LOOKUP_AUTO, SJ_LOOKUP_DENSE, SJ_LOOKUP_SEARCH = 0, 1, 2
+SJ_LOOKUP_AUTO, SJ_LOOKUP_DENSE, SJ_LOOKUP_SEARCH, SJ_LOOKUP_COORDS = 0, 1, 2, 3
 SJ_FRAME_AUTO, SJ_FRAME_GRID, SJ_FRAME_CELL = -1, 0, 1
 
 # symbols the header declares (checked by the CPU test suite)
@@ -494,7 +494,8 @@ class Index:
                     device_bytes=dsc.device_bytes, fp32=dsc.fp32, frame=dsc.frame)
 
     def sj_index_export(self):
-        """(B, G, A, M) as numpy arrays (Section IV-C)."""
+        """(B, G, A, M) as numpy arrays (Section IV-C); B is None for cells
+        ordered by coordinate tuple (no linear ids)."""
         info = self.sj_index_info()
         nc, n, d = info["n_cells"], info["n"], info["d"]
         mwords = (max(info["ng"]) + 31) // 32
@@ -502,8 +503,11 @@ class Index:
         G = np.empty(nc + 1, np.uint32)
         A = np.empty(n, np.uint32)
         M = np.empty((d, mwords), np.uint32)
-        st = self._ctx._lib.sj_index_export(self._h, B.ctypes.data, G.ctypes.data, A.ctypes.data,
-                                            M.ctypes.data)
+        lib = self._ctx._lib
+        st = lib.sj_index_export(self._h, B.ctypes.data, G.ctypes.data, A.ctypes.data, M.ctypes.data)
+        if st == SJ_ERANGE:
+            B = None
+            st = lib.sj_index_export(self._h, None, G.ctypes.data, A.ctypes.data, M.ctypes.data)
         if st != SJ_OK:
             raise SJError(st, "sj_index_export")
         return B, G, A, M

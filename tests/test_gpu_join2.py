@@ -66,3 +66,17 @@ def test_join2_device_inputs_and_overflow():
         assert ctx.sj_join2_device(r, s, 8.0, small, raise_overflow=False) == n
         got = run(ctx, r, s, 8.0)
     assert np.array_equal(got, oracle.bruteforce2(r.cpu().numpy(), s.cpu().numpy(), 8.0))
+
+
+def test_join2_on_a_grid_of_2_63_or_more_cells():
+    """R and S spread over [0, 1e7]^3 with eps = 0.5: the union grid has
+    about 8e21 cells and is searched by coordinate tuple."""
+    rng = np.random.default_rng(65)
+    centres = rng.uniform(0, 1e7, size=(60, 3))
+    r = centres[rng.integers(0, 60, 3000)] + rng.normal(0, 0.3, size=(3000, 3))
+    s = centres[rng.integers(0, 60, 4000)] + rng.normal(0, 0.3, size=(4000, 3))
+    for prec in (sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64):
+        with sj.Context(prec=prec) as ctx:
+            got = run(ctx, r, s, 0.5)
+        want = oracle.bruteforce2(r, s, 0.5)
+        assert len(want) > 0 and np.array_equal(got, want), prec

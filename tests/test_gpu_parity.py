@@ -19,13 +19,15 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 MODES = [(sj.SJ_PREC_FP32_RECHECK, True), (sj.SJ_PREC_FP64, True),
          (sj.SJ_PREC_FP32_RECHECK, False), (sj.SJ_PREC_FP64, False)]
+# dense table, binary search of B, binary search of coordinate tuples
+LOOKUPS = (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH, sj.SJ_LOOKUP_COORDS)
 
 
 @pytest.fixture(scope="module")
 def ctxs():
     out = {}
     for prec, uni in MODES:
-        for lookup in (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH):
+        for lookup in LOOKUPS:
             out[(prec, uni, lookup)] = sj.Context(prec=prec, unicomp=uni, lookup=lookup)
     yield out
     for c in out.values():
@@ -53,7 +55,7 @@ def test_config1_equals_bruteforce(ctxs, prec, uni):
     cfg = datagen.CONFIG1
     pts = datagen.make_points(cfg)
     want = orc.bruteforce(pts, cfg["eps"])
-    for lookup in (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH):
+    for lookup in LOOKUPS:
         got = gpu_keys(ctxs[(prec, uni, lookup)], pts, cfg["eps"])
         assert_same(got, want, f"config1 prec={prec} unicomp={uni} lookup={lookup}")
 
@@ -102,10 +104,12 @@ def test_edge_cases(ctxs):
     # eps small against the data range: self-pairs only
     k = gpu_keys(ctx, pts, 1e-4)
     assert_same(k, (np.arange(300, dtype=np.uint64) << np.uint64(32)) | np.arange(300, dtype=np.uint64), "tiny eps")
-    # a grid of 2^63 or more cells is refused, not approximated
+    # 2^31 or more cells in one dimension are refused, not approximated
     with pytest.raises(sj.SJError) as ei:
         ctx.sj_selfjoin(pts, 1e-12)
     assert ei.value.status == sj.SJ_ERANGE
+    # 1e24 cells: coordinate-tuple order, self-pairs only
+    assert_same(gpu_keys(ctx, pts, 1e-6), k, "1e24-cell grid")
     assert ctx.sj_selfjoin(pts, 1e-4).shape[0] == 300
     # negative and large-offset coordinates
     off = datagen.uniform(2000, 2, seed=10) - 1e6
@@ -385,7 +389,7 @@ def test_wide_grid_uses_the_cell_frame_and_grid_frame_falls_back():
 def cell_ctxs():
     out = {}
     for uni in (True, False):
-        for lookup in (sj.SJ_LOOKUP_AUTO, sj.SJ_LOOKUP_SEARCH):
+        for lookup in LOOKUPS:
             out[(uni, lookup)] = sj.Context(unicomp=uni, lookup=lookup, frame=sj.SJ_FRAME_CELL)
     yield out
     for c in out.values():
@@ -450,3 +454,49 @@ def test_cell_frame_config1_lattice_and_boundaries(cell_ctxs):
         total = m ** d + 2 * d * (m - 1) * m ** (d - 1)
         for key, ctx in cell_ctxs.items():
             assert len(ctx.sj_selfjoin(lat, 1.0)) == total, (d, key)
+
+
+def wide_clusters(n, d, side, seed, sigma=0.3, per=100):
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0, side, size=(n // per, d))
+    pts = centres[rng.integers(0, len(centres), n)] + rng.normal(0, sigma, size=(n, d))
+    pts[: n // 20] = rng.uniform(0, side, size=(n // 20, d))       # isolated background
+    return pts
+
+
+@pytest.mark.parametrize("d,side,n", [(3, 1e7, 20000), (5, 1e5, 8000), (8, 1e3, 5000)])
+def test_grid_of_2_63_or_more_cells(d, side, n):
+    """Grids whose linear ids overflow 64 bits (about 8e21 cells at 3-D,
+    1e31 at 5-D, 3e26 at 8-D) are ordered and searched by coordinate tuple;
+    the result equals the definition (brute force)."""
+    pts = wide_clusters(n, d, side, seed=90 + d)
+    eps = 0.5
+    want = orc.bruteforce(pts, eps)
+    for prec in (sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64):
+        for uni in (True, False):
+            with sj.Context(prec=prec, unicomp=uni) as ctx:
+                assert_same(gpu_keys(ctx, pts, eps), want, f"huge grid d={d} prec={prec} uni={uni}")
+                if prec == sj.SJ_PREC_FP32_RECHECK:
+                    assert ctx.sj_last_stats()["frame"] == sj.SJ_FRAME_CELL
+                idx = ctx.sj_build_index(pts, eps)
+                info = idx.sj_index_info()
+                assert info["grid_cells"] == 2 ** 64 - 1 and info["dense"] == 0
+                B, G, A, M = idx.sj_index_export()
+                assert B is None and G[-1] == n and np.array_equal(np.sort(A), np.arange(n))
+                idx.free()
+    assert len(want) > n          # some pairs beyond the self-pairs
+
+
+def test_coordinate_order_matches_linear_order():
+    """On an ordinary grid the coordinate-tuple order is the linear-id
+    order: the same A and G as the sort by linear id, and no B."""
+    pts = datagen.uniform(30000, 4, seed=91)
+    eps = datagen.eps_for_neighbors(30000, 4, 20)
+    with sj.Context(lookup=sj.SJ_LOOKUP_SEARCH) as c1, sj.Context(lookup=sj.SJ_LOOKUP_COORDS) as c2:
+        i1, i2 = c1.sj_build_index(pts, eps), c2.sj_build_index(pts, eps)
+        B1, G1, A1, M1 = i1.sj_index_export()
+        B2, G2, A2, M2 = i2.sj_index_export()
+        assert B2 is None and B1 is not None
+        assert np.array_equal(G1, G2) and np.array_equal(A1, A2) and np.array_equal(M1, M2)
+        i1.free()
+        i2.free()
