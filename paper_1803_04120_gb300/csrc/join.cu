@@ -653,8 +653,9 @@ __device__ __forceinline__ void drop_hits(uint32_t (&m)[CPL], uint32_t c) {
 }
 
 // Compares chunk `ch` (in ring slot r) of the item in slot `sl` with the
-// item's queries and stages the pairs found.
-template <int D, bool F32, bool UNI>
+// item's queries and stages the pairs found.  FR: the FP32 record frame,
+// 0 grid, 1 cell, 2 read from the arguments at run time (multi-join).
+template <int D, bool F32, bool UNI, int FR>
 __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int sl, uint32_t ch,
                                               int r, const JoinArgs &a, int lane,
                                               unsigned long long &rechecks) {
@@ -673,7 +674,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         const float hi32 = a.hi32, lo32 = a.lo32;
         f2_t z[NP][D], qq2[NP];
         uint32_t cid[CPL];
-        if (a.frame == SJ_FRAME_CELL)
+        if (FR == 2 ? a.frame == SJ_FRAME_CELL : FR == 1)
             load_candidates<D, CPL, true>(buf, a.rs, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
         else
             load_candidates<D, CPL, false>(buf, a.rs, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
@@ -844,7 +845,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
 // The warp's mbarriers are initialised on entry and invalidated on a normal
 // exit, so a warp can run several joins one after another in the same
 // shared-memory area.  Returns false when a bounded wait expired.
-template <int D, bool F32, bool UNI>
+template <int D, bool F32, bool UNI, int FR>
 __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *counts,
                                           unsigned char *smem, int warp, int lane) {
     constexpr int CPL = cpl_for(D, F32);
@@ -928,7 +929,8 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                     (void)mbar_wait_bounded(&ws.bar[k % nbuf], (k / nbuf) & 1u, a.timeout_ns);
                 break;
             }
-            consume_chunk<D, F32, UNI>(st, ws, st.cons_seq & smask, st.c_chunk, r, a, lane, rechecks);
+            consume_chunk<D, F32, UNI, FR>(st, ws, st.cons_seq & smask, st.c_chunk, r, a, lane,
+                                           rechecks);
             ++st.consumed;
             ++st.c_chunk;
             if (st.c_chunk == ws.hdr[st.cons_seq & smask].nchunks) {
@@ -951,11 +953,11 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     return !failed;
 }
 
-template <int D, bool F32, bool UNI>
+template <int D, bool F32, bool UNI, int FR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, minb_for(D, F32))
     join_kernel(const JoinArgs a, const uint32_t *counts) {
     extern __shared__ __align__(128) unsigned char smem[];
-    (void)join_body<D, F32, UNI>(a, counts, smem, threadIdx.x >> 5, threadIdx.x & 31);
+    (void)join_body<D, F32, UNI, FR>(a, counts, smem, threadIdx.x >> 5, threadIdx.x & 31);
 }
 
 // Many joins in one persistent launch: every warp takes part in the joins in
@@ -975,8 +977,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
         bool ok = true;
         switch (a.d * 2 + (a.f32 ? 1 : 0)) {
 #define SJ_MJ_CASE(DD)                                                                  \
-    case 2 * DD: ok = join_body<DD, false, true>(a, a.dcounts, smem, warp, lane); break; \
-    case 2 * DD + 1: ok = join_body<DD, true, true>(a, a.dcounts, smem, warp, lane); break;
+    case 2 * DD: ok = join_body<DD, false, true, 0>(a, a.dcounts, smem, warp, lane); break; \
+    case 2 * DD + 1: ok = join_body<DD, true, true, 2>(a, a.dcounts, smem, warp, lane); break;
             SJ_MJ_CASE(1)
             SJ_MJ_CASE(2)
             SJ_MJ_CASE(3)
@@ -994,22 +996,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
 
 typedef void (*KernelFn)(const JoinArgs, const uint32_t *);
 
+// The FP32 kernels come in a grid-frame and a cell-frame variant, so that
+// each inlines one candidate transform only.
 template <int D>
-KernelFn pick(bool f32, bool uni) {
-    if (f32) return uni ? join_kernel<D, true, true> : join_kernel<D, true, false>;
-    return uni ? join_kernel<D, false, true> : join_kernel<D, false, false>;
+KernelFn pick(bool f32, bool uni, bool cell) {
+    if (f32 && cell) return uni ? join_kernel<D, true, true, 1> : join_kernel<D, true, false, 1>;
+    if (f32) return uni ? join_kernel<D, true, true, 0> : join_kernel<D, true, false, 0>;
+    return uni ? join_kernel<D, false, true, 0> : join_kernel<D, false, false, 0>;
 }
 
-KernelFn pick_kernel(int d, bool f32, bool uni) {
+KernelFn pick_kernel(int d, bool f32, bool uni, bool cell) {
     switch (d) {
-        case 1: return pick<1>(f32, uni);
-        case 2: return pick<2>(f32, uni);
-        case 3: return pick<3>(f32, uni);
-        case 4: return pick<4>(f32, uni);
-        case 5: return pick<5>(f32, uni);
-        case 6: return pick<6>(f32, uni);
-        case 7: return pick<7>(f32, uni);
-        case 8: return pick<8>(f32, uni);
+        case 1: return pick<1>(f32, uni, cell);
+        case 2: return pick<2>(f32, uni, cell);
+        case 3: return pick<3>(f32, uni, cell);
+        case 4: return pick<4>(f32, uni, cell);
+        case 5: return pick<5>(f32, uni, cell);
+        case 6: return pick<6>(f32, uni, cell);
+        case 7: return pick<7>(f32, uni, cell);
+        case 8: return pick<8>(f32, uni, cell);
         default: return nullptr;
     }
 }
@@ -1265,7 +1270,7 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     const bool f32 = a.f32 != 0;
     const bool uni = cfg.unicomp != 0;
 
-    KernelFn fn = pick_kernel(d, f32, uni);
+    KernelFn fn = pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
     int dev = 0;
     SJ_CUDA_TRY(cudaGetDevice(&dev));
