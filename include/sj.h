@@ -201,6 +201,10 @@ typedef struct {
     uint64_t device_bytes;   /* device memory the index holds */
     int32_t fp32;            /* 1: the FP32 filter has a usable margin on this grid */
     int32_t frame;           /* sj_frame of the index's FP32 records */
+    int32_t grid_d;          /* dimensions the grid covers: d, or 6 when d > 8 */
+    int32_t grid_dim[8];     /* the point dimension of each grid dimension; eps,
+                                gmin, gmax, ng, n_cells, grid_cells and the
+                                arrays of sj_index_export describe these */
 } sj_index_desc;
 
 SJ_API sj_status sj_index_info(const sj_index *idx, sj_index_desc *out);
@@ -240,6 +244,16 @@ SJ_API sj_status sj_fp32_margin(int d, double eps, const double *gmin, const dou
 SJ_API sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
                                       const double *gmax, int frame, float *w32, float *lo,
                                       float *hi);
+
+/* The margin of the FP32 filter for points of more than 8 dimensions
+ * (d <= 16), whose search sums fl32(y_p,j - y_q,j)^2 with fused
+ * multiply-adds over all d dimensions, y_j = fl32(fl64(x_j - fmin_j)),
+ * fmin_j = min_j - eps, fmax_j = max_j + eps (derivation in
+ * csrc/margin.cu).  s32 <= *lo implies membership, s32 > *hi
+ * non-membership.  Returns SJ_ERANGE when no useful margin exists (those
+ * joins then compute in FP64), SJ_EINVAL for bad arguments.  Host-only. */
+SJ_API sj_status sj_fp32_margin_diff(int d, double eps, const double *fmin,
+                                     const double *fmax, float *lo, float *hi);
 
 /* ------------------------------------------------------------------ */
 /* Self-join.                                                         */

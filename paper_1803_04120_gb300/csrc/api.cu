@@ -177,7 +177,7 @@ struct Scoped {
 sj_status check_args(Error &err, const double *pts, uint64_t n, int d, double eps) {
     if (!pts) return fail(err, SJ_EINVAL, "pts is NULL");
     if (n == 0) return fail(err, SJ_EINVAL, "n must be positive");
-    if (d < 1 || d > kMaxDim) return fail(err, SJ_EINVAL, "d must be in [1, 8]");
+    if (d < 1 || d > kMaxPointDim) return fail(err, SJ_EINVAL, "d must be in [1, 16]");
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(err, SJ_EINVAL, "eps must be positive and finite");
     if (n >= (1ull << 32)) return fail(err, SJ_ERANGE, "n must be below 2^32");
     return SJ_OK;
@@ -229,7 +229,9 @@ JoinLaunch launch_cfg(const sj_ctx *ctx) { return ctx->launch; }
 sj_status prepare_launch(Error &err, sj_ctx *ctx, Index &ix, cudaStream_t s) {
     ctx->launch = default_launch(ctx);
     ctx->launch_tuned = 0;
-    if (!ctx->cfg.autotune || launch_forced(ctx->cfg)) return SJ_OK;
+    // the tuned parameters belong to the main kernel, not the one for more
+    // than 8 dimensions
+    if (!ctx->cfg.autotune || launch_forced(ctx->cfg) || ix.dfull > kMaxDim) return SJ_OK;
     SJ_TRY(read_counts(err, ix, s));
     return tune_launch(err, ix, ctx->launch, s, &ctx->launch_tuned);
 }
@@ -698,7 +700,9 @@ sj_status sj_index_info(const sj_index *ix, sj_index_desc *out) {
     std::memset(out, 0, sizeof(*out));
     const Index &x = ix->ix;
     out->n = x.g.n;
-    out->d = x.g.d;
+    out->d = x.dfull > kMaxDim ? x.dfull : x.g.d;
+    out->grid_d = x.g.d;
+    for (int j = 0; j < x.g.d; ++j) out->grid_dim[j] = x.dfull > kMaxDim ? x.gdim[j] : j;
     out->dense = x.dense;
     out->eps = x.g.eps;
     out->cell_width = x.g.w;
@@ -805,6 +809,7 @@ sj_status sj_join2_device(sj_ctx *ctx, const double *R, uint64_t nR, const doubl
     reset_stats(ctx);
     sj_status st = check_args(sc.err, R, nR, d, eps);
     if (st == SJ_OK) st = check_args(sc.err, S, nS, d, eps);
+    if (st == SJ_OK && d > kMaxDim) st = fail(sc.err, SJ_EINVAL, "two-set joins take at most 8 dimensions");
     if (st != SJ_OK) return sc.done(st);
     if (!d_pairs && cap_pairs) return sc.done(fail(sc.err, SJ_EINVAL, "d_pairs is NULL"));
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);

@@ -76,16 +76,17 @@ __device__ __forceinline__ uint64_t linear_cell(const double *p, const CellParam
 // Accumulates per-dimension min / max (order keys) of points i0, i0 + step,
 // ... below n into minmax[2j], minmax[2j + 1] and sets bit 0 of *flag when a
 // coordinate is NaN or infinite.  Called by every thread of full warps.
+template <int MAXD = kMaxDim>
 __device__ __forceinline__ void bounds_accumulate(const double *__restrict__ pts, uint64_t n, int d,
                                                   uint64_t i0, uint64_t step,
                                                   unsigned long long *minmax, uint32_t *flag) {
-    unsigned long long lo[kMaxDim], hi[kMaxDim];
+    unsigned long long lo[MAXD], hi[MAXD];
 #pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) { lo[j] = ~0ULL; hi[j] = 0ULL; }
+    for (int j = 0; j < MAXD; ++j) { lo[j] = ~0ULL; hi[j] = 0ULL; }
     bool bad = false;
     for (uint64_t i = i0; i < n; i += step) {
 #pragma unroll
-        for (int j = 0; j < kMaxDim; ++j) {
+        for (int j = 0; j < MAXD; ++j) {
             if (j < d) {
                 const double x = pts[i * d + j];
                 const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -97,7 +98,7 @@ __device__ __forceinline__ void bounds_accumulate(const double *__restrict__ pts
         }
     }
 #pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) {
+    for (int j = 0; j < MAXD; ++j) {
         if (j < d) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {

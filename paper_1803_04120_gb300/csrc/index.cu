@@ -208,6 +208,48 @@ __global__ void __launch_bounds__(kThreads) tuple_rle_kernel(const uint32_t *__r
     if (k == 0) G[*n_cells] = (uint32_t)n;
 }
 
+// High-dimensional path (more than kMaxDim dimensions) ---------------------
+
+struct DimVals {
+    double v[kMaxPointDim];
+};
+
+__global__ void __launch_bounds__(kThreads) bounds_full_kernel(const double *__restrict__ pts,
+                                                               uint64_t n, int d,
+                                                               unsigned long long *minmax,
+                                                               uint32_t *flag) {
+    bounds_accumulate<kMaxPointDim>(pts, n, d, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                    (uint64_t)gridDim.x * blockDim.x, minmax, flag);
+}
+
+// proj[i][t] = x_i[gdim[t]]: the grid dimensions of every point.
+struct GridDims {
+    int v[kMaxDim];
+};
+
+__global__ void __launch_bounds__(kThreads) project_kernel(const double *__restrict__ pts,
+                                                           uint64_t n, int d, int k, GridDims gd,
+                                                           double *__restrict__ proj) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int t = 0; t < k; ++t) proj[i * k + t] = pts[i * d + gd.v[t]];
+}
+
+// Cell-ordered records of all d coordinates: fl32(x_j - fmin_j), then the id.
+__global__ void __launch_bounds__(kThreads) recd32_kernel(const double *__restrict__ pts,
+                                                          const uint32_t *__restrict__ A,
+                                                          uint64_t n, int d, DimVals fmin, int rs,
+                                                          float *__restrict__ rec) {
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t i = A[k];
+    const double *p = pts + (uint64_t)i * d;
+    float *r = rec + k * rs;
+    for (int j = 0; j < d; ++j) r[j] = __double2float_rn(__dsub_rn(p[j], fmin.v[j]));
+    r[d] = __uint_as_float(i);
+    for (int j = d + 1; j < rs; ++j) r[j] = 0.0f;
+}
+
 inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -252,8 +294,9 @@ sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, 
 }
 
 void free_index(Index &ix, cudaStream_t s) {
-    DevBuf *all[] = {&ix.pts, &ix.rec32, &ix.rec64, &ix.A, &ix.B, &ix.G,
-                     &ix.cc,  &ix.M,     &ix.lut,   &ix.items, &ix.counts_dev};
+    DevBuf *all[] = {&ix.pts, &ix.rec32, &ix.rec64, &ix.A,          &ix.B,
+                     &ix.G,   &ix.cc,    &ix.M,     &ix.lut,        &ix.items,
+                     &ix.counts_dev,     &ix.ptsd,  &ix.recd32,     &ix.recd64};
     for (DevBuf *b : all) dev_free(*b, s);
 }
 
@@ -287,9 +330,119 @@ sj_status bounds_of(Error &err, const double *d_pts, uint64_t n, int d, cudaStre
     return SJ_OK;
 }
 
+// Index of points with more than kMaxDim dimensions: bounds of every
+// dimension, the kHdGridDims dimensions with the most cells as the grid
+// (built by build_index from the projected points), then the cell-ordered
+// records of all coordinates and the margin of the difference-form filter.
+static sj_status build_index_hd(Error &err, const double *pts_any, uint64_t n, int d, double eps,
+                                int lookup_mode, cudaStream_t s, Index &ix) {
+    ix = Index();
+    ix.owner_stream = s;
+    if (n >= (1ull << 32)) return fail(err, SJ_ERANGE, "n must be below 2^32");
+    DevBuf full, proj, scratch;
+    auto cleanup = [&]() { dev_free(full, s); dev_free(proj, s); dev_free(scratch, s); };
+    sj_status st = SJ_OK;
+#define SJ_H(expr) do { st = (expr); if (st != SJ_OK) { cleanup(); return st; } } while (0)
+#define SJ_HC(expr) do { cudaError_t e__ = (expr); if (e__ != cudaSuccess) { set_cuda_error(err, e__, #expr, __FILE__, __LINE__); cleanup(); return err.st; } } while (0)
+    SJ_H(dev_alloc(err, full, n * d * sizeof(double), s));
+    SJ_HC(cudaMemcpyAsync(full.p, pts_any, n * d * sizeof(double), cudaMemcpyDefault, s));
+    const double *pts = static_cast<const double *>(full.p);
+    SJ_H(dev_alloc(err, scratch, (2 * kMaxPointDim) * sizeof(unsigned long long) + 64, s));
+    unsigned long long *d_minmax = static_cast<unsigned long long *>(scratch.p);
+    uint32_t *d_flag = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxPointDim);
+    init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_flag); note_launch();
+    {
+        int blocks = 2 * sm_count(-1);
+        const uint64_t need = (n + kThreads - 1) / kThreads;
+        if ((uint64_t)blocks > need) blocks = (int)need;
+        bounds_full_kernel<<<blocks, kThreads, 0, s>>>(pts, n, d, d_minmax, d_flag); note_launch();
+    }
+    SJ_HC(cudaGetLastError());
+    unsigned long long h[2 * kMaxPointDim + 8];
+    SJ_HC(cudaMemcpyAsync(h, d_minmax, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SJ_HC(cudaStreamSynchronize(s));
+    if (reinterpret_cast<const uint32_t *>(h + 2 * kMaxPointDim)[0] & 1u) {
+        cleanup();
+        return fail(err, SJ_EINVAL, "non-finite coordinate");
+    }
+    const double w = eps * (1.0 + std::ldexp(1.0, -16));
+    double fmin[kMaxPointDim], fmax[kMaxPointDim], cells[kMaxPointDim];
+    for (int j = 0; j < d; ++j) {
+        fmin[j] = from_order_key(h[2 * j]) - eps;
+        fmax[j] = from_order_key(h[2 * j + 1]) + eps;
+        cells[j] = std::floor((fmax[j] - fmin[j]) / w) + 1.0;
+    }
+    // the grid: the kHdGridDims dimensions with the most cells, in order
+    bool taken[kMaxPointDim] = {};
+    for (int t = 0; t < kHdGridDims; ++t) {
+        int best = -1;
+        for (int j = 0; j < d; ++j)
+            if (!taken[j] && (best < 0 || cells[j] > cells[best])) best = j;
+        taken[best] = true;
+    }
+    GridDims gd;
+    int k = 0;
+    for (int j = 0; j < d; ++j)
+        if (taken[j]) gd.v[k++] = j;
+    unsigned long long mm[2 * kMaxDim];
+    for (int t = 0; t < k; ++t) {
+        mm[2 * t] = h[2 * gd.v[t]];
+        mm[2 * t + 1] = h[2 * gd.v[t] + 1];
+    }
+    SJ_H(dev_alloc(err, proj, n * k * sizeof(double), s));
+    project_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, d, k, gd, static_cast<double *>(proj.p));
+    note_launch();
+    SJ_HC(cudaGetLastError());
+    Index inner;
+    st = build_index(err, static_cast<const double *>(proj.p), n, k, eps, lookup_mode, SJ_FRAME_GRID,
+                     s, inner, mm);
+    if (st != SJ_OK) {
+        free_index(inner, s);
+        cleanup();
+        return st;
+    }
+    ix = inner;
+    dev_free(proj, s);
+    dev_free(scratch, s);
+    ix.dfull = d;
+    for (int t = 0; t < k; ++t) ix.gdim[t] = gd.v[t];
+    for (int j = 0; j < d; ++j) {
+        ix.fmin[j] = fmin[j];
+        ix.fmax[j] = fmax[j];
+    }
+    ix.ptsd = full;
+    full = DevBuf();
+    ix.rsd32 = (d + 1 + 3) / 4 * 4;
+    ix.rsd64 = (d + 1 + 1) / 2 * 2;
+    DimVals fv;
+    for (int j = 0; j < kMaxPointDim; ++j) fv.v[j] = j < d ? fmin[j] : 0.0;
+    st = dev_alloc(err, ix.recd32, n * ix.rsd32 * sizeof(float), s);
+    if (st != SJ_OK) { free_index(ix, s); return st; }
+    recd32_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<const double *>(ix.ptsd.p),
+                                                   static_cast<const uint32_t *>(ix.A.p), n, d, fv,
+                                                   ix.rsd32, static_cast<float *>(ix.recd32.p));
+    note_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(err, e, "recd32_kernel", __FILE__, __LINE__);
+        free_index(ix, s);
+        return err.st;
+    }
+    Geometry &g = ix.g;
+    g.fp32_ok = fp32_margin_diff(d, eps, fmin, fmax, &g.lo32, &g.hi32) ? 1 : 0;  // margin.cu
+    g.frame = SJ_FRAME_GRID;
+    ix.bytes += ix.ptsd.bytes + ix.recd32.bytes;
+#undef SJ_H
+#undef SJ_HC
+    return SJ_OK;
+}
+
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
                       int lookup_mode, int frame_mode, cudaStream_t s, Index &ix,
                       const unsigned long long *given_mm) {
+    if (d > kMaxDim && d <= kMaxPointDim && !given_mm && pts_any && n && eps > 0.0 &&
+        std::isfinite(eps))
+        return build_index_hd(err, pts_any, n, d, eps, lookup_mode, s, ix);
     ix = Index();
     ix.owner_stream = s;
     if (pts_any == nullptr || n == 0 || d < 1 || d > kMaxDim || !(eps > 0.0) || !std::isfinite(eps))
@@ -484,6 +637,18 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
 
 // Builds the FP64 records when a FP64-mode join first needs them.
 sj_status ensure_rec64(Error &err, Index &ix, cudaStream_t s) {
+    if (ix.dfull > kMaxDim) {
+        if (ix.recd64.p) return SJ_OK;
+        const uint64_t n = ix.g.n;
+        SJ_TRY(dev_alloc(err, ix.recd64, n * ix.rsd64 * sizeof(double), s));
+        rec64_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<const double *>(ix.ptsd.p),
+                                                      static_cast<const uint32_t *>(ix.A.p), n,
+                                                      ix.dfull, ix.rsd64,
+                                                      static_cast<double *>(ix.recd64.p)); note_launch();
+        SJ_CUDA_TRY(cudaGetLastError());
+        ix.bytes += ix.recd64.bytes;
+        return SJ_OK;
+    }
     if (ix.rec64.p) return SJ_OK;
     const uint64_t n = ix.g.n;
     SJ_TRY(dev_alloc(err, ix.rec64, n * ix.rs64 * sizeof(double), s));

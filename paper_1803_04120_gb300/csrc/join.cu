@@ -445,34 +445,16 @@ __device__ __forceinline__ bool fetch_item(Pipe &st, const JoinArgs &a, uint32_t
     return true;
 }
 
-// Builds ranges, header and staged queries of item `it` in item slot `sl`.
-template <int D, bool F32, bool UNI>
-__device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 it,
-                                             const JoinArgs &a, uint32_t n_cells, int lane,
-                                             unsigned long long &evals) {
-    typedef typename std::conditional<F32, float, double>::type T;
-    const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
-    // the query side: the item's cell and points (the candidate side is
-    // read through a.lut / a.B / a.G and the ranges)
-    const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.qrec32)
-                                   : reinterpret_cast<const unsigned char *>(a.qrec64);
-    const uint32_t h = it.x;
-    const uint32_t cbeg = __ldg(&a.qG[h]), cend = __ldg(&a.qG[h + 1]);
-    const uint32_t home_len = cend - cbeg;
-    const uint32_t q0 = cbeg + it.y * kQueryBlock;
-    const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
-
-    int32_t c[D];
-    uint32_t odd = 0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        c[j] = __ldg(&a.qcc[(uint64_t)h * D + j]);
-        odd |= ((uint32_t)c[j] & 1u) << j;
-    }
-
-    // candidate ranges
-    uint2 *rt = ws.ranges[sl];
-    uint32_t nranges = 0, K = 0;
+// Candidate ranges of a query cell with coordinates c (odd: their parity
+// bits): one entry per row template that survives the M_j clip and holds
+// points, written to rt as (first record, running candidate count); K is
+// the number of candidates.
+template <int D, bool UNI>
+__device__ __forceinline__ void build_ranges(const int32_t *c, uint32_t odd, const JoinArgs &a,
+                                             uint32_t n_cells, int lane, uint2 *rt,
+                                             uint32_t &nranges, uint32_t &K) {
+    nranges = 0;
+    K = 0;
     for (int t0 = 0; t0 < a.n_templates; t0 += 32) {
         const int t = t0 + lane;
         uint32_t beg = 0, len = 0;
@@ -510,6 +492,37 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
         nranges += __popc(nz);
         K += __shfl_sync(0xffffffffu, incl, 31);
     }
+}
+
+// Builds ranges, header and staged queries of item `it` in item slot `sl`.
+template <int D, bool F32, bool UNI>
+__device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 it,
+                                             const JoinArgs &a, uint32_t n_cells, int lane,
+                                             unsigned long long &evals) {
+    typedef typename std::conditional<F32, float, double>::type T;
+    const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
+    // the query side: the item's cell and points (the candidate side is
+    // read through a.lut / a.B / a.G and the ranges)
+    const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.qrec32)
+                                   : reinterpret_cast<const unsigned char *>(a.qrec64);
+    const uint32_t h = it.x;
+    const uint32_t cbeg = __ldg(&a.qG[h]), cend = __ldg(&a.qG[h + 1]);
+    const uint32_t home_len = cend - cbeg;
+    const uint32_t q0 = cbeg + it.y * kQueryBlock;
+    const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
+
+    int32_t c[D];
+    uint32_t odd = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        c[j] = __ldg(&a.qcc[(uint64_t)h * D + j]);
+        odd |= ((uint32_t)c[j] & 1u) << j;
+    }
+
+    // candidate ranges
+    uint2 *rt = ws.ranges[sl];
+    uint32_t nranges, K;
+    build_ranges<D, UNI>(c, odd, a, n_cells, lane, rt, nranges, K);
 
     // staged queries
     ItemHdr *hd = &ws.hdr[sl];
@@ -994,6 +1007,172 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     }
 }
 
+// The exact predicate for the high-dimensional kernel's rechecks: a
+// function of its own, so that the main kernels' non-inlined recheck keeps
+// its register budget.
+__device__ __noinline__ bool exact_member_hd(const double *__restrict__ a,
+                                             const double *__restrict__ b, int d, double E2) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double t = __dsub_rn(a[j], b[j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s <= E2;
+}
+
+// High-dimensional search (points of more than kMaxDim dimensions): the
+// grid covers kHdGridDims of them.  A warp takes one work item at a time,
+// builds its candidate ranges like the main kernel, stages the item's
+// queries (records of all dfull coordinates) in shared memory, and lets each
+// lane take every 32nd candidate of each range, read straight from the
+// cell-ordered records in global memory, and compare it with every query.
+// FP32: the difference-form sum against [lo32, hi32] (margin.cu), values in
+// between rechecked with the exact FP64 predicate on the input points, in a
+// warp-uniform branch; FP64: the exact predicate on the FP64 records.  Hits
+// are written after one atomic reservation per query and 32 candidates.
+// There are no waits, so no time limits.
+template <bool F32, bool UNI>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    hd_join_kernel(const JoinArgs a, const uint32_t *counts) {
+    constexpr int K = kHdGridDims;
+    typedef typename std::conditional<F32, float, double>::type T;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char *wbase = smem + (size_t)warp * a.sm_warp;
+    uint2 *rt = reinterpret_cast<uint2 *>(wbase);
+    T *qs = reinterpret_cast<T *>(wbase + a.sm_ranges);
+    const T *rec = F32 ? reinterpret_cast<const T *>(a.recd32) : reinterpret_cast<const T *>(a.recd64);
+    const int dd = a.dfull, rs = a.rsd;
+    const uint32_t n_cells = *a.ccells;
+    uint32_t item_end = a.item_end;
+    if (counts[1] < item_end) item_end = counts[1];
+    const unsigned lt = (1u << lane) - 1u;
+    constexpr unsigned long long kMult = UNI ? 2ull : 1ull;
+    unsigned long long evals = 0, rechecks = 0;
+    for (;;) {
+        uint32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(a.work, 1u);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        const uint64_t item = (uint64_t)a.item_begin + (uint64_t)pos * a.item_stride;
+        if (item >= item_end) break;
+        const uint2 it = a.items[item];
+        const uint32_t h = it.x;
+        const uint32_t cbeg = __ldg(&a.qG[h]), cend = __ldg(&a.qG[h + 1]);
+        const uint32_t home_len = cend - cbeg;
+        const uint32_t ql0 = it.y * kQueryBlock;
+        const uint32_t q0 = cbeg + ql0;
+        const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
+        int32_t c[K];
+        uint32_t odd = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            c[j] = __ldg(&a.qcc[(uint64_t)h * K + j]);
+            odd |= ((uint32_t)c[j] & 1u) << j;
+        }
+        __syncwarp();   // the previous item's ranges and queries are no longer read
+        uint32_t nranges, kc;
+        build_ranges<K, UNI>(c, odd, a, n_cells, lane, rt, nranges, kc);
+        uint32_t qid_l = 0;
+        if (lane < (int)nq) {
+            const T *r = rec + (size_t)(q0 + lane) * rs;
+            T *qd = qs + (size_t)lane * rs;
+            for (int j = 0; j < dd; ++j) qd[j] = r[j];
+            qid_l = F32 ? __float_as_uint((float)r[dd])
+                        : (uint32_t)__double_as_longlong((double)r[dd]);
+        }
+        __syncwarp();
+        if (lane == 0)
+            evals += UNI ? (uint64_t)nq * (kc - home_len) + (uint64_t)nq * (home_len - 1) -
+                               (uint64_t)nq * ql0 - (uint64_t)nq * (nq - 1) / 2
+                         : (uint64_t)nq * kc;
+        if (UNI) {
+            // the self-pair of every query, once
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)nq);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (!a.count_only && lane < (int)nq && base + lane < a.cap)
+                a.out[base + lane] = make_uint2(qid_l, qid_l);
+        }
+        uint32_t kstart = 0;
+        for (uint32_t ri = 0; ri < nranges; ++ri) {
+            const uint2 rg = rt[ri];
+            const uint32_t len = rg.y - kstart;
+            for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+                const uint32_t p = p0 + lane;
+                const bool valid = p < len;
+                const uint32_t kpos = kstart + p;   // position in the item's candidate list
+                T y[kMaxPointDim];
+                uint32_t cid = 0xffffffffu;
+#pragma unroll
+                for (int j = 0; j < kMaxPointDim; ++j) y[j] = (T)0;
+                if (valid) {
+                    const T *r = rec + (size_t)(rg.x + p) * rs;
+#pragma unroll
+                    for (int j = 0; j < kMaxPointDim; ++j)
+                        if (j < dd) y[j] = r[j];
+                    cid = F32 ? __float_as_uint((float)r[dd])
+                              : (uint32_t)__double_as_longlong((double)r[dd]);
+                }
+                for (uint32_t qi = 0; qi < nq; ++qi) {
+                    const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
+                    // in the home cell under UNICOMP only candidates after the query
+                    const bool cand = valid && (!UNI || kpos >= home_len || kpos > ql0 + qi);
+                    const T *qd = qs + (size_t)qi * rs;
+                    bool hit;
+                    if (F32) {
+                        float sum = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < kMaxPointDim; ++j) {
+                            if (j < dd) {
+                                const float t = __fsub_rn((float)qd[j], (float)y[j]);
+                                sum = __fmaf_rn(t, t, sum);
+                            }
+                        }
+                        hit = cand && sum <= a.hi32;
+                        const bool band = hit && !(sum <= a.lo32);
+                        if (__any_sync(0xffffffffu, band)) {
+                            if (band) {
+                                hit = exact_member_hd(a.ptsd + (size_t)qid * dd,
+                                                      a.ptsd + (size_t)cid * dd, dd, a.E2);
+                                ++rechecks;
+                            }
+                        }
+                    } else {
+                        double sum = 0.0;
+#pragma unroll
+                        for (int j = 0; j < kMaxPointDim; ++j) {
+                            if (j < dd) {
+                                const double t = __dsub_rn((double)qd[j], (double)y[j]);
+                                sum = __dadd_rn(sum, __dmul_rn(t, t));
+                            }
+                        }
+                        hit = cand && sum <= a.E2;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (m) {
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)__popc(m) * kMult);
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (hit && !a.count_only) {
+                            const unsigned long long at = base + (unsigned long long)__popc(m & lt) * kMult;
+                            if (at < a.cap) a.out[at] = make_uint2(qid, cid);
+                            if (UNI && at + 1 < a.cap) a.out[at + 1] = make_uint2(cid, qid);
+                        }
+                    }
+                }
+            }
+            kstart = rg.y;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rechecks += __shfl_xor_sync(0xffffffffu, rechecks, o);
+    if (lane == 0) {
+        if (evals) atomicAdd(&a.counter[1], evals);
+        if (rechecks) atomicAdd(&a.counter[2], rechecks);
+    }
+}
+
 typedef void (*KernelFn)(const JoinArgs, const uint32_t *);
 
 // The FP32 kernels come in a grid-frame and a cell-frame variant, so that
@@ -1183,7 +1362,9 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     const int d = g.d;
     const bool f32 = cfg.prec_fp32 && g.fp32_ok;
     const bool uni = cfg.unicomp != 0;
-    if (!f32 && !ix.rec64.p) return fail(err, SJ_EINVAL, "FP64 records missing");
+    const bool hd = ix.dfull > kMaxDim;
+    if (!f32 && !(hd ? ix.recd64.p : ix.rec64.p)) return fail(err, SJ_EINVAL, "FP64 records missing");
+    if (hd && qix) return fail(err, SJ_EINVAL, "two-set joins take at most 8 dimensions");
     // the query side (work items, home cells, query points): another index
     // on the same grid for a two-set join, else the candidate index itself
     const Index &q = qix ? *qix : ix;
@@ -1255,6 +1436,16 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.d = d;
     a.f32 = f32 ? 1 : 0;
     a.dcounts = n_items_dev(q) - 1;
+    if (hd) {
+        // the high-dimensional kernel: ranges, then the staged query records
+        a.recd32 = static_cast<const float *>(ix.recd32.p);
+        a.recd64 = static_cast<const double *>(ix.recd64.p);
+        a.ptsd = static_cast<const double *>(ix.ptsd.p);
+        a.dfull = ix.dfull;
+        a.rsd = f32 ? ix.rsd32 : ix.rsd64;
+        a.sm_queries = round16(kQueryBlock * a.rsd * esz);
+        a.sm_warp = a.sm_ranges + a.sm_queries;
+    }
     return SJ_OK;
 }
 
@@ -1270,7 +1461,10 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     const bool f32 = a.f32 != 0;
     const bool uni = cfg.unicomp != 0;
 
-    KernelFn fn = pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
+    KernelFn fn = ix.dfull > kMaxDim
+                      ? (f32 ? (uni ? hd_join_kernel<true, true> : hd_join_kernel<true, false>)
+                             : (uni ? hd_join_kernel<false, true> : hd_join_kernel<false, false>))
+                      : pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
     int dev = 0;
     SJ_CUDA_TRY(cudaGetDevice(&dev));

@@ -56,6 +56,19 @@
 // Frame choice (automatic): the grid frame needs no wrap step in the kernel
 // and is kept while its band is below 2^-10 E2; otherwise the frame with
 // the narrower band; FP64 arithmetic when neither has a usable margin.
+//
+// Difference form (points of more than 8 dimensions).  The kernel stores
+// y_j = fl32(fl64(x_j - fmin_j)) for every dimension (fmin_j = min_j - eps,
+// X_j = fmax_j - fmin_j) and evaluates
+//     t_j = fl(y_p,j - y_q,j),   s32 = fma(t_{d-1}, t_{d-1}, ... fma(t_0, t_0, 0)).
+//  (a) |y_j - (x_j - fmin_j)| <= rho_j = X_j (u + v + uv) + 2^-150;
+//  (b) |t_j - Delta_j| <= 2 rho_j + u (|Delta_j| + 2 rho_j);
+//  (c) every term is non-negative, so (1 - g_d) |t|^2 <= s32 <= (1 + g_d) |t|^2.
+// Member: |Delta| <= R2, each |Delta_j| <= R2, so |t| <= R2 + H2 with
+// H2 = |(2 rho_j + u (R2 + 2 rho_j))_j| and hi = (1 + g_d)(R2 + H2)^2.
+// Conversely s32 <= lo = (1 - g_d)(R1 - H1)^2 gives |t| <= T = R1 - H1, each
+// |Delta_j| <= (T + 2 rho_j (1 + u)) / (1 - u) <= D_j (T <= R1), and
+// |Delta| <= T + H1 <= R1 with H1 = |(2 rho_j + u (D_j + 2 rho_j))_j|.
 #include <cmath>
 
 #include "sj_internal.cuh"
@@ -145,6 +158,48 @@ double band_of(const FrameMargin &m) {
 
 }  // namespace
 
+bool fp32_margin_diff(int d, double eps, const double *fmin, const double *fmax, float *lo32,
+                      float *hi32) {
+    const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
+    const double safety = std::ldexp(1.0, -20);
+    const double E2 = eps * eps;
+    const double gd = d * u / (1.0 - d * u);
+    const double g64 = (d + 3) * v / (1.0 - (d + 3) * v);
+    const double a64 = 2.0 * d * std::ldexp(1.0, -1074);
+    *lo32 = -1.0f;
+    *hi32 = 0.0f;
+    if (!std::isfinite(E2) || E2 < std::ldexp(1.0, -100)) return false;
+    const double R2 = std::sqrt((E2 + a64) / (1.0 - g64)) * (1.0 + safety);
+    const double R1 = std::sqrt((E2 - a64) / (1.0 + g64)) * (1.0 - safety);
+    double h2 = 0.0, h1 = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double X = (fmax[j] - fmin[j]) * (1.0 + 4.0 * v);
+        if (!(X < std::ldexp(1.0, 60))) return false;
+        const double rho = X * (u + v + u * v) + std::ldexp(1.0, -150);
+        const double e2 = 2.0 * rho + u * (R2 + 2.0 * rho);
+        const double Dj = (R1 + 2.0 * rho * (1.0 + u)) / (1.0 - u);
+        const double e1 = 2.0 * rho + u * (Dj + 2.0 * rho);
+        h2 += e2 * e2;
+        h1 += e1 * e1;
+    }
+    const double H2 = std::sqrt(h2) * (1.0 + safety), H1 = std::sqrt(h1) * (1.0 + safety);
+    const double hi = (1.0 + gd) * (R2 + H2) * (R2 + H2) * (1.0 + safety);
+    float h = (float)hi;
+    if ((double)h < hi) h = std::nextafter(h, INFINITY);
+    float l = -1.0f;
+    if (R1 > H1) {
+        const double lo = (1.0 - gd) * (R1 - H1) * (R1 - H1) * (1.0 - safety);
+        if (lo > 0.0) {
+            l = (float)lo;
+            if ((double)l > lo) l = std::nextafter(l, -INFINITY);
+        }
+    }
+    if (!std::isfinite(h) || (double)h - (l > 0.0f ? (double)l : 0.0) > 0.5 * E2) return false;
+    *lo32 = l;
+    *hi32 = h;
+    return true;
+}
+
 void fp32_margin(Geometry &g, int frame_mode) {
     g.fp32_ok = 0;
     g.frame = SJ_FRAME_GRID;
@@ -213,4 +268,15 @@ extern "C" sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
                                           const double *gmax, int frame, float *w32, float *lo,
                                           float *hi) {
     return margin_entry(d, eps, gmin, gmax, frame, w32, lo, hi);
+}
+
+extern "C" sj_status sj_fp32_margin_diff(int d, double eps, const double *fmin,
+                                         const double *fmax, float *lo, float *hi) {
+    if (d < 1 || d > sj::kMaxPointDim || !fmin || !fmax || !(eps > 0.0) || !std::isfinite(eps))
+        return SJ_EINVAL;
+    float l = -1.0f, h = 0.0f;
+    const bool ok = sj::fp32_margin_diff(d, eps, fmin, fmax, &l, &h);
+    if (lo) *lo = l;
+    if (hi) *hi = h;
+    return ok ? SJ_OK : SJ_ERANGE;
 }

@@ -22,7 +22,9 @@
 
 namespace sj {
 
-constexpr int kMaxDim = 8;
+constexpr int kMaxDim = 8;             // grid dimensions, and point dimensions of the main path
+constexpr int kMaxPointDim = 16;       // point dimensions (d > kMaxDim: high-dimensional path)
+constexpr int kHdGridDims = 6;         // grid dimensions of the high-dimensional path
 constexpr int kWarpsPerBlock = 8;      // 256 threads per block, as in Section VI-B
 constexpr int kQueryBlock = 32;        // query points per work item
 constexpr uint32_t kErrTimeout = 1u;   // device error word bits
@@ -107,8 +109,26 @@ struct Index {
     int counts_read = 0;
     uint64_t bytes = 0;
     cudaStream_t owner_stream = nullptr;
+    // Points of more than kMaxDim dimensions: the grid (g, and every array
+    // above) covers the kHdGridDims dimensions gdim[] with the most cells,
+    // built from the projected points; the search refines on all dfull
+    // coordinates, read from the cell-ordered records below.  g.lo32, g.hi32
+    // and g.fp32_ok then hold the margin of the difference-form FP32 sum
+    // (margin.cu, fp32_margin_diff).
+    int dfull = 0;                 // point dimensions (g.d when dfull <= kMaxDim)
+    int gdim[kMaxDim] = {};        // original dimension of grid dimension j
+    double fmin[kMaxPointDim] = {}, fmax[kMaxPointDim] = {};  // min - eps, max + eps, all dims
+    DevBuf ptsd;                   // n x dfull FP64 input (row-major), exact rechecks
+    DevBuf recd32;                 // cell-ordered fl32(x_j - fmin_j), j < dfull, then the id
+    DevBuf recd64;                 // cell-ordered x_j, j < dfull, then the id
+    int rsd32 = 0, rsd64 = 0;      // their strides (floats / doubles)
 };
 
+// FP32 margin of the high-dimensional path (margin.cu): the kernel sums
+// fl32(y_p - y_q)^2 with fused multiply-adds over all d dimensions,
+// y = fl32(fl64(x_j - fmin_j)).  Returns false when no useful margin exists.
+bool fp32_margin_diff(int d, double eps, const double *fmin, const double *fmax, float *lo32,
+                      float *hi32);
 // FP32 filter margin of a geometry (margin.cu): chooses the record frame
 // (frame_mode: an sj_frame) and sets frame, w32, w4, inv_w4, lo32, hi32 and
 // fp32_ok.
@@ -190,6 +210,12 @@ struct JoinArgs {
     int d;
     int f32;
     const uint32_t *dcounts;
+    // high-dimensional path: records of all dfull coordinates
+    const float *recd32;
+    const double *recd64;
+    const double *ptsd;
+    int dfull;
+    int rsd;                        // their stride in elements of the mode's type
 };
 
 struct JoinLaunch {

@@ -36,6 +36,7 @@ ABI_FUNCTIONS = (
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
     "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
+    "sj_fp32_margin_diff",
 )
 
 
@@ -63,7 +64,8 @@ class sj_index_desc(ctypes.Structure):
                 ("n_cells", ctypes.c_uint64), ("grid_cells", ctypes.c_uint64),
                 ("gmin", ctypes.c_double * 8), ("gmax", ctypes.c_double * 8),
                 ("ng", ctypes.c_int64 * 8), ("device_bytes", ctypes.c_uint64),
-                ("fp32", ctypes.c_int32), ("frame", ctypes.c_int32)]
+                ("fp32", ctypes.c_int32), ("frame", ctypes.c_int32),
+                ("grid_d", ctypes.c_int32), ("grid_dim", ctypes.c_int32 * 8)]
 
 
 class sj_stats(ctypes.Structure):
@@ -146,6 +148,8 @@ def load(build: bool = True):
                                       ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+            "sj_fp32_margin_diff": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float)]),
             "sj_fp32_margin_frame": (i32, [i32, f64, P, P, i32, ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float)]),
@@ -487,17 +491,18 @@ class Index:
         st = self._ctx._lib.sj_index_info(self._h, ctypes.byref(dsc))
         if st != SJ_OK:
             raise SJError(st, "sj_index_info")
-        d = dsc.d
-        return dict(n=dsc.n, d=d, dense=dsc.dense, eps=dsc.eps, cell_width=dsc.cell_width,
+        g = dsc.grid_d
+        return dict(n=dsc.n, d=dsc.d, dense=dsc.dense, eps=dsc.eps, cell_width=dsc.cell_width,
                     n_cells=dsc.n_cells, grid_cells=dsc.grid_cells,
-                    gmin=list(dsc.gmin)[:d], gmax=list(dsc.gmax)[:d], ng=list(dsc.ng)[:d],
-                    device_bytes=dsc.device_bytes, fp32=dsc.fp32, frame=dsc.frame)
+                    gmin=list(dsc.gmin)[:g], gmax=list(dsc.gmax)[:g], ng=list(dsc.ng)[:g],
+                    device_bytes=dsc.device_bytes, fp32=dsc.fp32, frame=dsc.frame,
+                    grid_d=g, grid_dim=list(dsc.grid_dim)[:g])
 
     def sj_index_export(self):
         """(B, G, A, M) as numpy arrays (Section IV-C); B is None for cells
         ordered by coordinate tuple (no linear ids)."""
         info = self.sj_index_info()
-        nc, n, d = info["n_cells"], info["n"], info["d"]
+        nc, n, d = info["n_cells"], info["n"], info["grid_d"]
         mwords = (max(info["ng"]) + 31) // 32
         B = np.empty(nc, np.uint64)
         G = np.empty(nc + 1, np.uint32)
@@ -554,6 +559,18 @@ def sj_fp32_margin_frame(d: int, eps: float, gmin, gmax, frame: int):
     st = lib.sj_fp32_margin_frame(d, float(eps), gmin.ctypes.data, gmax.ctypes.data, int(frame),
                                   ctypes.byref(w), ctypes.byref(lo), ctypes.byref(hi))
     return st, w.value, lo.value, hi.value
+
+
+def sj_fp32_margin_diff(d: int, eps: float, fmin, fmax):
+    """(status, lo, hi) of the FP32 margin used for points of more than 8
+    dimensions (difference-form sum; host only)."""
+    lib = load()
+    fmin = np.ascontiguousarray(fmin, dtype=np.float64)
+    fmax = np.ascontiguousarray(fmax, dtype=np.float64)
+    lo, hi = ctypes.c_float(), ctypes.c_float()
+    st = lib.sj_fp32_margin_diff(d, float(eps), fmin.ctypes.data, fmax.ctypes.data,
+                                 ctypes.byref(lo), ctypes.byref(hi))
+    return st, lo.value, hi.value
 
 
 def sj_shard_bounds(item_block, rank: int, world: int):

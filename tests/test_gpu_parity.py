@@ -272,7 +272,7 @@ def test_invalid_arguments():
             ctx.sj_selfjoin(bad, 1.0)
         assert ei.value.status == sj.SJ_EINVAL
         with pytest.raises(sj.SJError) as ei:
-            ctx.sj_selfjoin(np.zeros((4, 9)), 1.0)
+            ctx.sj_selfjoin(np.zeros((4, 17)), 1.0)
         assert ei.value.status == sj.SJ_EINVAL
         # the context stays usable after errors
         assert ctx.sj_selfjoin(pts, 1.0).shape[0] == 100

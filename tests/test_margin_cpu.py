@@ -264,3 +264,57 @@ def test_cell_frame_margin_at_any_extent():
     st0, _, lo0, hi0 = sj.sj_fp32_margin_frame(3, 2.0, np.zeros(3), np.full(3, 100.0), sj.SJ_FRAME_GRID)
     st1, _, lo1, hi1 = sj.sj_fp32_margin_frame(3, 2.0, np.zeros(3), np.full(3, 100.0), sj.SJ_FRAME_CELL)
     assert st0 == st1 == sj.SJ_OK and hi1 - lo1 < hi0 - lo0
+
+
+# ---------------------------------------------------------------- difference form (d > 8)
+
+def kernel_s32_diff(p, q, fmin):
+    """s32 of the high-dimensional kernel: fma chain of fl32(y_p - y_q)^2."""
+    acc = F(0)
+    for j in range(len(p)):
+        yp = r32(r64(F(p[j]) - F(fmin[j])))
+        yq = r32(r64(F(q[j]) - F(fmin[j])))
+        t = r32(yp - yq)
+        acc = r32(t * t + acc)
+    return acc
+
+
+@pytest.mark.parametrize("d,eps,scale,offset", [
+    (9, 30.0, 100.0, 0.0), (12, 0.7, 1000.0, -50.0), (16, 55.0, 100.0, 0.0), (3, 0.37, 30.0, 1e5)])
+def test_difference_form_margin_sound_on_threshold_pairs(d, eps, scale, offset):
+    rng = np.random.default_rng(int(eps * 100) + d)
+    pts = offset + rng.uniform(0, scale, size=(50, d))
+    extra = []
+    for p in pts:
+        v = rng.normal(size=d)
+        v /= np.linalg.norm(v)
+        for f in (1.0, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -52, 1.0 + 3e-7, 1.0 - 3e-7,
+                  1.0 + 2e-6, 1.0 - 2e-6, 0.5, 1.7):
+            extra.append(p + v * eps * f)
+    allp = np.concatenate([pts, np.array(extra)])
+    fmin = allp.min(axis=0) - eps
+    fmax = allp.max(axis=0) + eps
+    st, lo, hi = sj.sj_fp32_margin_diff(d, eps, fmin, fmax)
+    assert st == sj.SJ_OK
+    E2 = r64(F(eps) * F(eps))
+    X = float(np.max(fmax - fmin))
+    assert 0.0 < lo < float(E2) < hi
+    assert (hi - lo) / float(E2) < 1e-4 + 40 * 2.0 ** -24 * X / eps
+    checked = 0
+    for k, p in enumerate(pts):
+        for q in extra[9 * k: 9 * k + 9]:
+            s = kernel_s32_diff(p, q, fmin)
+            mem = exact_member(p, q, E2)
+            if s <= F(lo):
+                assert mem, (d, k)
+            if s > F(hi):
+                assert not mem, (d, k)
+            checked += 1
+    assert checked == 450
+
+
+def test_difference_form_margin_arguments():
+    st, _, _ = sj.sj_fp32_margin_diff(17, 1.0, np.zeros(17), np.ones(17))
+    assert st == sj.SJ_EINVAL
+    st, _, _ = sj.sj_fp32_margin_diff(10, 1e-9, np.zeros(10), np.full(10, 1e8))
+    assert st == sj.SJ_ERANGE
