@@ -351,6 +351,62 @@ def frame_bench(dev: int, reps: int):
                         "with centres U[0, 1e6]^d plus 10% uniform background, eps = 0.5"}
 
 
+# ---------------------------------------------------------------- more than 8 dimensions
+
+def highdim_bench(dev: int, reps: int):
+    """Points of 16 dimensions (grid over the six with the most cells, the
+    difference-form FP32 filter over all sixteen): uniform and clustered
+    workloads, the FP32 filter with FP64 recheck against plain FP64, pairs
+    in device memory, whole call (index build included)."""
+    import torch
+    from paper_1803_04120_gb300 import sj
+
+    rng = np.random.default_rng(16)
+    d = 16
+    n_u = 200_000
+    eps_u = (64.0 * 100.0 ** d / (n_u * datagen.ball_volume(d))) ** (1.0 / d)
+    uni = datagen.uniform(n_u, d, seed=161)
+    n_c = 1_000_000
+    centres = rng.uniform(0, 100, size=(1000, d))
+    clu = centres[rng.integers(0, 1000, n_c)] + rng.normal(0, 2.0, size=(n_c, d))
+    cases = [(f"uniform {n_u:,} points in [0,100]^16, 64 neighbours", uni, eps_u),
+             (f"{n_c:,} points in 1,000 Gaussian clusters (sigma 2) in [0,100]^16", clu, 8.0)]
+    stream = torch.cuda.Stream()
+    out = []
+    for name, pts_np, eps in cases:
+        pts = torch.from_numpy(pts_np).cuda()
+        row = {"workload": name, "n": len(pts_np), "d": d, "eps": round(eps, 4)}
+        for key, prec in (("fp32", sj.SJ_PREC_FP32_RECHECK), ("fp64", sj.SJ_PREC_FP64)):
+            with sj.Context(prec=prec, profile=True, device=dev) as c:
+                n = c.sj_selfjoin_count(pts, eps)
+                buf = torch.empty((max(n, 1), 2), dtype=torch.int32, device="cuda")
+                c.sj_selfjoin_device(pts, eps, buf, stream=stream)
+                torch.cuda.synchronize()
+                c.sj_profile_read()
+                ts = []
+                for _ in range(reps if prec == sj.SJ_PREC_FP32_RECHECK else 1):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    assert c.sj_selfjoin_device(pts, eps, buf, stream=stream) == n
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                kms, nl = c.sj_profile_read()
+                st = c.sj_last_stats()
+                del buf
+            row["pairs"] = n
+            row[key] = {"ms": round(min(ts), 3), "kernel_ms": round(kms / max(nl, 1), 3),
+                        "evaluations": st["evaluations"], "rechecks": st["rechecks"],
+                        "pairs_per_s": round(n / (min(ts) / 1e3), 1),
+                        "evaluations_per_s": round(st["evaluations"] / (kms / max(nl, 1) / 1e3), 1)}
+        row["speedup_fp32"] = round(row["fp64"]["ms"] / row["fp32"]["ms"], 2)
+        out.append(row)
+        del pts
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- serving
 
 def _pct(v, q):
@@ -583,6 +639,8 @@ def run_gpu(args):
         line["ablation"] = ablation_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_frames:
         line["frames"] = frame_bench(dev, max(1, min(args.steps, 3)))
+    if not args.no_highdim:
+        line["highdim"] = highdim_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_cpu:
         v, cores, desc = cpu_oracle_sample(data, args.cpu_budget)
         line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -645,6 +703,8 @@ def main():
                     help="skip the UNICOMP and brute-force comparisons")
     ap.add_argument("--no-frames", action="store_true",
                     help="skip the FP32 record-frame comparison")
+    ap.add_argument("--no-highdim", action="store_true",
+                    help="skip the 16-dimensional workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -658,6 +718,7 @@ def main():
         # whole-job value is the sum over ranks of pairs over the max time
         # (the serving and clustered sections are single-GPU measurements)
         args.serve_requests, args.no_skew, args.no_ablation, args.no_frames = 0, True, True, True
+        args.no_highdim = True
         import torch.distributed as dist
         dist.init_process_group("nccl")
         args.no_cpu = args.no_cpu or rank != 0

@@ -37,7 +37,13 @@
  *     sj_result are library-owned host memory, valid until sj_result_free.
  *   - Pair order is unspecified unless sj_config.sorted = 1, which orders
  *     pairs ascending by the 64-bit key (i << 32) | j.
- *   - Errors: SJ_EINVAL for a NULL argument, n = 0, d outside [1, 8],
+ *   - Points have d in [1, 16] dimensions.  For d > 8 the grid covers the
+ *     six dimensions with the most cells and the search refines on all d
+ *     (the 3^d search of Section IV-D degenerates beyond the paper's 2-6
+ *     dimensions); the two-set join, sj_selfjoin_multi, sj_submit,
+ *     sj_selfjoin_noalloc, sj_selfjoin_bruteforce_device and the margin
+ *     calls of the main path take d in [1, 8].
+ *   - Errors: SJ_EINVAL for a NULL argument, n = 0, d outside [1, 16],
  *     eps <= 0 or non-finite, or any NaN/Inf coordinate; SJ_ERANGE when
  *     n >= 2^32 or a dimension would need 2^31 or more cells (grids whose
  *     cell count reaches 2^63 are ordered by coordinate tuple, see
