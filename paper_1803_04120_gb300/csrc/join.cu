@@ -449,17 +449,55 @@ __device__ __forceinline__ bool fetch_item(Pipe &st, const JoinArgs &a, uint32_t
 // bits): one entry per row template that survives the M_j clip and holds
 // points, written to rt as (first record, running candidate count); K is
 // the number of candidates.
+// Under UNICOMP the table holds the home row (template 0), the two stage-0
+// cells (1, 2; gate 0) and, per stage k = 1 .. D-1, 2 * 3^(k-1) rows from
+// template 3^(k-1) + 2 on (gate k).  Only the stages whose gate coordinate
+// is odd take part, so the lanes are mapped onto those templates alone:
+// at 6-D about 123 of 245, half the passes.
+template <int D>
+__device__ __forceinline__ int active_template(uint32_t odd, uint32_t r) {
+    if (r == 0) return 0;
+    --r;
+    if (odd & 1u) {
+        if (r < 2) return 1 + (int)r;
+        r -= 2;
+    }
+    uint32_t p = 1;   // 3^(k-1)
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+        if ((odd >> k) & 1u) {
+            if (r < 2 * p) return (int)(p + 2 + r);
+            r -= 2 * p;
+        }
+        p *= 3;
+    }
+    return -1;
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t active_templates(uint32_t odd) {
+    uint32_t n = 1 + ((odd & 1u) ? 2u : 0u), p = 1;
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+        if ((odd >> k) & 1u) n += 2 * p;
+        p *= 3;
+    }
+    return n;
+}
+
 template <int D, bool UNI>
 __device__ __forceinline__ void build_ranges(const int32_t *c, uint32_t odd, const JoinArgs &a,
                                              uint32_t n_cells, int lane, uint2 *rt,
                                              uint32_t &nranges, uint32_t &K) {
     nranges = 0;
     K = 0;
-    for (int t0 = 0; t0 < a.n_templates; t0 += 32) {
-        const int t = t0 + lane;
+    const int n_t = UNI ? (int)active_templates<D>(odd) : a.n_templates;
+    for (int t0 = 0; t0 < n_t; t0 += 32) {
+        const int t = UNI ? (t0 + lane < n_t ? active_template<D>(odd, (uint32_t)(t0 + lane)) : -1)
+                          : (t0 + lane < n_t ? t0 + lane : -1);
         uint32_t beg = 0, len = 0;
         int32_t xlo, xhi, b[D];
-        if (t < a.n_templates && row_of<D, UNI>(t, c, odd, a, xlo, xhi, b)) {
+        if (t >= 0 && row_of<D, UNI>(t, c, odd, a, xlo, xhi, b)) {
             uint64_t base = 0;
 #pragma unroll
             for (int j = 1; j < D; ++j) base += (uint64_t)b[j] * a.stride[j];
@@ -1032,7 +1070,7 @@ __device__ __noinline__ bool exact_member_hd(const double *__restrict__ a,
 // are written after one atomic reservation per query and 32 candidates.
 // There are no waits, so no time limits.
 template <bool F32, bool UNI>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     hd_join_kernel(const JoinArgs a, const uint32_t *counts) {
     constexpr int K = kHdGridDims;
     typedef typename std::conditional<F32, float, double>::type T;
@@ -1098,6 +1136,76 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         for (uint32_t ri = 0; ri < nranges; ++ri) {
             const uint2 rg = rt[ri];
             const uint32_t len = rg.y - kstart;
+            if (F32) {
+                // two candidates per lane (p and p + 32), packed as f32x2
+                for (uint32_t p0 = 0; p0 < len; p0 += 64) {
+                    uint32_t cid[2] = {0xffffffffu, 0xffffffffu}, kp[2];
+                    bool valid[2];
+                    const float *rr[2];
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const uint32_t p = p0 + 32 * h2 + lane;
+                        valid[h2] = p < len;
+                        kp[h2] = kstart + p;
+                        rr[h2] = reinterpret_cast<const float *>(rec) + (size_t)(rg.x + (valid[h2] ? p : 0)) * rs;
+                        if (valid[h2]) cid[h2] = __float_as_uint(rr[h2][dd]);
+                    }
+                    f2_t yy[kMaxPointDim];
+#pragma unroll
+                    for (int j = 0; j < kMaxPointDim; ++j) {
+                        const float y0 = (valid[0] && j < dd) ? rr[0][j] : 0.0f;
+                        const float y1 = (valid[1] && j < dd) ? rr[1][j] : 0.0f;
+                        yy[j] = f2_pack(y0, y1);
+                    }
+                    const f2_t neg1 = f2_pack(-1.0f, -1.0f);
+                    for (uint32_t qi = 0; qi < nq; ++qi) {
+                        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
+                        const float *qd = reinterpret_cast<const float *>(qs) + (size_t)qi * rs;
+                        f2_t acc = f2_pack(0.0f, 0.0f);
+#pragma unroll
+                        for (int j = 0; j < kMaxPointDim; ++j) {
+                            if (j < dd) {
+                                const float qj = qd[j];
+                                // fl(q - y) on both halves, then the running fma sum
+                                const f2_t t = f2_fma(yy[j], neg1, f2_pack(qj, qj));
+                                acc = f2_fma(t, t, acc);
+                            }
+                        }
+                        float sv[2];
+                        f2_unpack(acc, sv[0], sv[1]);
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            // in the home cell under UNICOMP only candidates after the query
+                            const bool cand =
+                                valid[h2] && (!UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi);
+                            bool hit = cand && sv[h2] <= a.hi32;
+                            const bool band = hit && !(sv[h2] <= a.lo32);
+                            if (__any_sync(0xffffffffu, band)) {
+                                if (band) {
+                                    hit = exact_member_hd(a.ptsd + (size_t)qid * dd,
+                                                          a.ptsd + (size_t)cid[h2] * dd, dd, a.E2);
+                                    ++rechecks;
+                                }
+                            }
+                            const unsigned m = __ballot_sync(0xffffffffu, hit);
+                            if (m) {
+                                unsigned long long base = 0;
+                                if (lane == 0)
+                                    base = atomicAdd(&a.counter[0], (unsigned long long)__popc(m) * kMult);
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (hit && !a.count_only) {
+                                    const unsigned long long at =
+                                        base + (unsigned long long)__popc(m & lt) * kMult;
+                                    if (at < a.cap) a.out[at] = make_uint2(qid, cid[h2]);
+                                    if (UNI && at + 1 < a.cap) a.out[at + 1] = make_uint2(cid[h2], qid);
+                                }
+                            }
+                        }
+                    }
+                }
+                kstart = rg.y;
+                continue;
+            }
             for (uint32_t p0 = 0; p0 < len; p0 += 32) {
                 const uint32_t p = p0 + lane;
                 const bool valid = p < len;
