@@ -1069,18 +1069,20 @@ __device__ __noinline__ bool exact_member_hd(const double *__restrict__ a,
 // warp-uniform branch; FP64: the exact predicate on the FP64 records.  Hits
 // are written after one atomic reservation per query and 32 candidates.
 // There are no waits, so no time limits.
-template <bool F32, bool UNI>
+template <bool F32, bool UNI, int G4>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     hd_join_kernel(const JoinArgs a, const uint32_t *counts) {
+    // DW = 4 G4 >= d coordinates take part; those past d are zero on both
+    // sides, and an exact zero term leaves every sum (FP32 or FP64) unchanged
     constexpr int K = kHdGridDims;
-    typedef typename std::conditional<F32, float, double>::type T;
+    constexpr int DW = 4 * G4;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char *wbase = smem + (size_t)warp * a.sm_warp;
     uint2 *rt = reinterpret_cast<uint2 *>(wbase);
-    T *qs = reinterpret_cast<T *>(wbase + a.sm_ranges);
-    const T *rec = F32 ? reinterpret_cast<const T *>(a.recd32) : reinterpret_cast<const T *>(a.recd64);
+    // staged queries: DW values each, as (q, q) float pairs (FP32) or doubles
+    unsigned char *qs = wbase + a.sm_ranges;
     const int dd = a.dfull, rs = a.rsd;
     const uint32_t n_cells = *a.ccells;
     uint32_t item_end = a.item_end;
@@ -1088,6 +1090,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     const unsigned lt = (1u << lane) - 1u;
     constexpr unsigned long long kMult = UNI ? 2ull : 1ull;
     unsigned long long evals = 0, rechecks = 0;
+
+    // one classified hit per lane: reservation by ballot, then the writes
+    auto emit = [&](bool hit, uint32_t qid, uint32_t cid) {
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (!m) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)__popc(m) * kMult);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (hit && !a.count_only) {
+            const unsigned long long at = base + (unsigned long long)__popc(m & lt) * kMult;
+            if (at < a.cap) a.out[at] = make_uint2(qid, cid);
+            if (UNI && at + 1 < a.cap) a.out[at + 1] = make_uint2(cid, qid);
+        }
+    };
+
     for (;;) {
         uint32_t pos = 0;
         if (lane == 0) pos = atomicAdd(a.work, 1u);
@@ -1113,11 +1130,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
         build_ranges<K, UNI>(c, odd, a, n_cells, lane, rt, nranges, kc);
         uint32_t qid_l = 0;
         if (lane < (int)nq) {
-            const T *r = rec + (size_t)(q0 + lane) * rs;
-            T *qd = qs + (size_t)lane * rs;
-            for (int j = 0; j < dd; ++j) qd[j] = r[j];
-            qid_l = F32 ? __float_as_uint((float)r[dd])
-                        : (uint32_t)__double_as_longlong((double)r[dd]);
+            if (F32) {
+                const float *r = a.recd32 + (size_t)(q0 + lane) * rs;
+                f2_t *qd = reinterpret_cast<f2_t *>(qs) + (size_t)lane * DW;
+#pragma unroll
+                for (int j = 0; j < DW; ++j) {
+                    const float v = j < dd ? r[j] : 0.0f;
+                    qd[j] = f2_pack(v, v);
+                }
+                qid_l = __float_as_uint(r[dd]);
+            } else {
+                const double *r = a.recd64 + (size_t)(q0 + lane) * rs;
+                double *qd = reinterpret_cast<double *>(qs) + (size_t)lane * DW;
+#pragma unroll
+                for (int j = 0; j < DW; ++j) qd[j] = j < dd ? r[j] : 0.0;
+                qid_l = (uint32_t)__double_as_longlong(r[dd]);
+            }
         }
         __syncwarp();
         if (lane == 0)
@@ -1141,132 +1169,99 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                 for (uint32_t p0 = 0; p0 < len; p0 += 64) {
                     uint32_t cid[2] = {0xffffffffu, 0xffffffffu}, kp[2];
                     bool valid[2];
-                    const float *rr[2];
+                    float4 y4[2][G4];
 #pragma unroll
                     for (int h2 = 0; h2 < 2; ++h2) {
                         const uint32_t p = p0 + 32 * h2 + lane;
                         valid[h2] = p < len;
                         kp[h2] = kstart + p;
-                        rr[h2] = reinterpret_cast<const float *>(rec) + (size_t)(rg.x + (valid[h2] ? p : 0)) * rs;
-                        if (valid[h2]) cid[h2] = __float_as_uint(rr[h2][dd]);
-                    }
-                    f2_t yy[kMaxPointDim];
 #pragma unroll
-                    for (int j = 0; j < kMaxPointDim; ++j) {
-                        const float y0 = (valid[0] && j < dd) ? rr[0][j] : 0.0f;
-                        const float y1 = (valid[1] && j < dd) ? rr[1][j] : 0.0f;
-                        yy[j] = f2_pack(y0, y1);
+                        for (int g = 0; g < G4; ++g) y4[h2][g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (valid[h2]) {
+                            const float *r = a.recd32 + (size_t)(rg.x + p) * rs;
+#pragma unroll
+                            for (int g = 0; g < G4; ++g) y4[h2][g] = *reinterpret_cast<const float4 *>(r + 4 * g);
+                            cid[h2] = __float_as_uint(r[dd]);
+                        }
+                    }
+                    f2_t yy[DW];
+#pragma unroll
+                    for (int g = 0; g < G4; ++g) {
+                        const float4 u = y4[0][g], v = y4[1][g];
+                        const int j = 4 * g;
+                        yy[j] = f2_pack(j < dd ? u.x : 0.f, j < dd ? v.x : 0.f);
+                        yy[j + 1] = f2_pack(j + 1 < dd ? u.y : 0.f, j + 1 < dd ? v.y : 0.f);
+                        yy[j + 2] = f2_pack(j + 2 < dd ? u.z : 0.f, j + 2 < dd ? v.z : 0.f);
+                        yy[j + 3] = f2_pack(j + 3 < dd ? u.w : 0.f, j + 3 < dd ? v.w : 0.f);
                     }
                     const f2_t neg1 = f2_pack(-1.0f, -1.0f);
                     for (uint32_t qi = 0; qi < nq; ++qi) {
                         const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
-                        const float *qd = reinterpret_cast<const float *>(qs) + (size_t)qi * rs;
+                        const ulonglong2 *qd =
+                            reinterpret_cast<const ulonglong2 *>(reinterpret_cast<const f2_t *>(qs) + (size_t)qi * DW);
                         f2_t acc = f2_pack(0.0f, 0.0f);
 #pragma unroll
-                        for (int j = 0; j < kMaxPointDim; ++j) {
-                            if (j < dd) {
-                                const float qj = qd[j];
-                                // fl(q - y) on both halves, then the running fma sum
-                                const f2_t t = f2_fma(yy[j], neg1, f2_pack(qj, qj));
-                                acc = f2_fma(t, t, acc);
-                            }
+                        for (int j2 = 0; j2 < DW / 2; ++j2) {
+                            const ulonglong2 q2 = qd[j2];   // (q_j, q_j), (q_j+1, q_j+1)
+                            // fl(q - y) on both halves, then the running fma sum
+                            const f2_t t0 = f2_fma(yy[2 * j2], neg1, q2.x);
+                            acc = f2_fma(t0, t0, acc);
+                            const f2_t t1 = f2_fma(yy[2 * j2 + 1], neg1, q2.y);
+                            acc = f2_fma(t1, t1, acc);
                         }
                         float sv[2];
                         f2_unpack(acc, sv[0], sv[1]);
+                        bool hit[2], band[2];
 #pragma unroll
                         for (int h2 = 0; h2 < 2; ++h2) {
                             // in the home cell under UNICOMP only candidates after the query
                             const bool cand =
                                 valid[h2] && (!UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi);
-                            bool hit = cand && sv[h2] <= a.hi32;
-                            const bool band = hit && !(sv[h2] <= a.lo32);
-                            if (__any_sync(0xffffffffu, band)) {
-                                if (band) {
-                                    hit = exact_member_hd(a.ptsd + (size_t)qid * dd,
-                                                          a.ptsd + (size_t)cid[h2] * dd, dd, a.E2);
+                            hit[h2] = cand && sv[h2] <= a.hi32;
+                            band[h2] = hit[h2] && !(sv[h2] <= a.lo32);
+                        }
+                        if (__any_sync(0xffffffffu, band[0] || band[1])) {
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                if (band[h2]) {
+                                    hit[h2] = exact_member_hd(a.ptsd + (size_t)qid * dd,
+                                                              a.ptsd + (size_t)cid[h2] * dd, dd, a.E2);
                                     ++rechecks;
                                 }
                             }
-                            const unsigned m = __ballot_sync(0xffffffffu, hit);
-                            if (m) {
-                                unsigned long long base = 0;
-                                if (lane == 0)
-                                    base = atomicAdd(&a.counter[0], (unsigned long long)__popc(m) * kMult);
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                if (hit && !a.count_only) {
-                                    const unsigned long long at =
-                                        base + (unsigned long long)__popc(m & lt) * kMult;
-                                    if (at < a.cap) a.out[at] = make_uint2(qid, cid[h2]);
-                                    if (UNI && at + 1 < a.cap) a.out[at + 1] = make_uint2(cid[h2], qid);
-                                }
-                            }
                         }
+                        emit(hit[0], qid, cid[0]);
+                        emit(hit[1], qid, cid[1]);
                     }
                 }
-                kstart = rg.y;
-                continue;
-            }
-            for (uint32_t p0 = 0; p0 < len; p0 += 32) {
-                const uint32_t p = p0 + lane;
-                const bool valid = p < len;
-                const uint32_t kpos = kstart + p;   // position in the item's candidate list
-                T y[kMaxPointDim];
-                uint32_t cid = 0xffffffffu;
+            } else {
+                for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+                    const uint32_t p = p0 + lane;
+                    const bool valid = p < len;
+                    const uint32_t kpos = kstart + p;   // position in the item's candidate list
+                    double y[DW];
+                    uint32_t cid = 0xffffffffu;
 #pragma unroll
-                for (int j = 0; j < kMaxPointDim; ++j) y[j] = (T)0;
-                if (valid) {
-                    const T *r = rec + (size_t)(rg.x + p) * rs;
+                    for (int j = 0; j < DW; ++j) y[j] = 0.0;
+                    if (valid) {
+                        const double *r = a.recd64 + (size_t)(rg.x + p) * rs;
 #pragma unroll
-                    for (int j = 0; j < kMaxPointDim; ++j)
-                        if (j < dd) y[j] = r[j];
-                    cid = F32 ? __float_as_uint((float)r[dd])
-                              : (uint32_t)__double_as_longlong((double)r[dd]);
-                }
-                for (uint32_t qi = 0; qi < nq; ++qi) {
-                    const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
-                    // in the home cell under UNICOMP only candidates after the query
-                    const bool cand = valid && (!UNI || kpos >= home_len || kpos > ql0 + qi);
-                    const T *qd = qs + (size_t)qi * rs;
-                    bool hit;
-                    if (F32) {
-                        float sum = 0.0f;
-#pragma unroll
-                        for (int j = 0; j < kMaxPointDim; ++j) {
-                            if (j < dd) {
-                                const float t = __fsub_rn((float)qd[j], (float)y[j]);
-                                sum = __fmaf_rn(t, t, sum);
-                            }
-                        }
-                        hit = cand && sum <= a.hi32;
-                        const bool band = hit && !(sum <= a.lo32);
-                        if (__any_sync(0xffffffffu, band)) {
-                            if (band) {
-                                hit = exact_member_hd(a.ptsd + (size_t)qid * dd,
-                                                      a.ptsd + (size_t)cid * dd, dd, a.E2);
-                                ++rechecks;
-                            }
-                        }
-                    } else {
+                        for (int j = 0; j < DW; ++j)
+                            if (j < dd) y[j] = r[j];
+                        cid = (uint32_t)__double_as_longlong(r[dd]);
+                    }
+                    for (uint32_t qi = 0; qi < nq; ++qi) {
+                        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
+                        const bool cand = valid && (!UNI || kpos >= home_len || kpos > ql0 + qi);
+                        const double *qd = reinterpret_cast<const double *>(qs) + (size_t)qi * DW;
+                        // the exact predicate, in dimension order (zero terms add nothing)
                         double sum = 0.0;
 #pragma unroll
-                        for (int j = 0; j < kMaxPointDim; ++j) {
-                            if (j < dd) {
-                                const double t = __dsub_rn((double)qd[j], (double)y[j]);
-                                sum = __dadd_rn(sum, __dmul_rn(t, t));
-                            }
+                        for (int j = 0; j < DW; ++j) {
+                            const double t = __dsub_rn(qd[j], y[j]);
+                            sum = __dadd_rn(sum, __dmul_rn(t, t));
                         }
-                        hit = cand && sum <= a.E2;
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (m) {
-                        unsigned long long base = 0;
-                        if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)__popc(m) * kMult);
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (hit && !a.count_only) {
-                            const unsigned long long at = base + (unsigned long long)__popc(m & lt) * kMult;
-                            if (at < a.cap) a.out[at] = make_uint2(qid, cid);
-                            if (UNI && at + 1 < a.cap) a.out[at + 1] = make_uint2(cid, qid);
-                        }
+                        emit(cand && sum <= a.E2, qid, cid);
                     }
                 }
             }
@@ -1290,6 +1285,19 @@ KernelFn pick(bool f32, bool uni, bool cell) {
     if (f32 && cell) return uni ? join_kernel<D, true, true, 1> : join_kernel<D, true, false, 1>;
     if (f32) return uni ? join_kernel<D, true, true, 0> : join_kernel<D, true, false, 0>;
     return uni ? join_kernel<D, false, true, 0> : join_kernel<D, false, false, 0>;
+}
+
+// The high-dimensional kernel evaluates 12 (d <= 12) or 16 coordinates.
+template <int G4>
+KernelFn pick_hd(bool f32, bool uni) {
+    if (f32) return uni ? hd_join_kernel<true, true, G4> : hd_join_kernel<true, false, G4>;
+    return uni ? hd_join_kernel<false, true, G4> : hd_join_kernel<false, false, G4>;
+}
+
+KernelFn pick_hd_kernel(int d, bool f32, bool uni) {
+    if (d <= 12) return pick_hd<3>(f32, uni);
+    if (d <= kMaxPointDim) return pick_hd<4>(f32, uni);
+    return nullptr;
 }
 
 KernelFn pick_kernel(int d, bool f32, bool uni, bool cell) {
@@ -1551,7 +1559,7 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
         a.ptsd = static_cast<const double *>(ix.ptsd.p);
         a.dfull = ix.dfull;
         a.rsd = f32 ? ix.rsd32 : ix.rsd64;
-        a.sm_queries = round16(kQueryBlock * a.rsd * esz);
+        a.sm_queries = round16(kQueryBlock * 4 * ((ix.dfull + 3) / 4) * 8);
         a.sm_warp = a.sm_ranges + a.sm_queries;
     }
     return SJ_OK;
@@ -1569,10 +1577,8 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     const bool f32 = a.f32 != 0;
     const bool uni = cfg.unicomp != 0;
 
-    KernelFn fn = ix.dfull > kMaxDim
-                      ? (f32 ? (uni ? hd_join_kernel<true, true> : hd_join_kernel<true, false>)
-                             : (uni ? hd_join_kernel<false, true> : hd_join_kernel<false, false>))
-                      : pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
+    KernelFn fn = ix.dfull > kMaxDim ? pick_hd_kernel(ix.dfull, f32, uni)
+                                     : pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
     int dev = 0;
     SJ_CUDA_TRY(cudaGetDevice(&dev));
