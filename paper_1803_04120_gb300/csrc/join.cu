@@ -51,7 +51,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "sj_internal.cuh"
+#include "join_dev.cuh"
 
 namespace sj {
 
@@ -139,27 +139,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Packed FP32 pair arithmetic (sm_100+ f32x2 instructions), round to nearest.
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2_pack(float a, float b) {
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2_t r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
-    f2_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
 // The exact predicate of Section III in FP64: every operation rounded to
 // nearest on its own, no contraction.  Kept out of line so that the FP64
 // instructions run only for the pairs that need them.
@@ -185,77 +164,9 @@ __device__ __forceinline__ bool exact_member(const double *__restrict__ a,
     return s <= E2;
 }
 
-// Row templates of the search, precomputed on the host per (d, UNICOMP)
-// and read with one load per template.  Entry t describes template t
-// relative to the query cell c:
-//   bits 0-1  x range: 0 the home cell only, 1 x - 1 only, 2 x + 1 only,
-//             3 x - 1 .. x + 1;
-//   bits 2-5  gate: the template is active when bit `gate` of the cell's
-//             odd-coordinate mask is set (gate < 8), always (gate = 8);
-//   bits 6-19 offset + 1 of dimensions 2..d (2 bits each).
-//   UNICOMP: t = 0 home cell; t = 1, 2 stage 0 (x - 1, x + 1); then, for
-//   stage k = 1..d-1, 2 * 3^(k-1) rows with dimension k at c_k -+ 1,
-//   dimensions 1..k-1 anywhere in c -+ 1, dimensions above k equal to c.
-//   Stage k is active when c_k is odd (Section V-B, generalised to n
-//   dimensions).  Full search: t in [0, 3^(d-1)) enumerates all rows.
+// The row-template table (entry format in join_dev.cuh).
 constexpr int kTemplateEntries = 6576;   // sum over d = 1..8 of both tables
 __device__ uint32_t g_templates[kTemplateEntries];
-
-template <int D, bool UNI>
-__device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, const JoinArgs &a,
-                                       int32_t &xlo, int32_t &xhi, int32_t *b) {
-    const uint32_t e = __ldg(&a.tmpl[t]);
-    const uint32_t gate = (e >> 2) & 15u;
-    if (gate < 8 && !((odd >> gate) & 1u)) return false;
-    const uint32_t xm = e & 3u;
-    xlo = c[0] + (xm == 2 ? 1 : (xm == 0 ? 0 : -1));
-    xhi = c[0] + (xm == 1 ? -1 : (xm == 0 ? 0 : 1));
-#pragma unroll
-    for (int j = 1; j < D; ++j) b[j] = c[j] + (int32_t)((e >> (6 + 2 * (j - 1))) & 3u) - 1;
-    if (xlo < 0) xlo = 0;
-    if (xhi > a.ng[0] - 1) xhi = a.ng[0] - 1;
-    if (xlo > xhi) return false;
-#pragma unroll
-    for (int j = 1; j < D; ++j) {
-        if (b[j] < 0 || b[j] >= a.ng[j]) return false;
-        const uint32_t w = a.M[(uint64_t)j * a.mwords + ((uint32_t)b[j] >> 5)];
-        if (!((w >> (b[j] & 31)) & 1u)) return false;   // M_j: no point in that slab
-    }
-    return true;
-}
-
-// First position in B[0, n) whose value is >= key.
-__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *__restrict__ B, uint32_t n,
-                                                    uint64_t key) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(&B[mid]) < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// First cell in [0, n) whose coordinate tuple is not below (b_{D-1}, ...,
-// b_1, x), compared from dimension D down to dimension 1: the order of the
-// linear ids, for grids whose linear ids do not fit in 64 bits.
-template <int D>
-__device__ __forceinline__ uint32_t lower_bound_tuple(const int32_t *__restrict__ cc, uint32_t n,
-                                                      const int32_t *b, int32_t x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        const int32_t *t = cc + (uint64_t)mid * D;
-        int cmp = 0;
-#pragma unroll
-        for (int j = D - 1; j >= 0; --j) {
-            const int32_t tj = __ldg(&t[j]);
-            const int32_t kj = j ? b[j] : x;
-            if (cmp == 0) cmp = tj < kj ? -1 : (tj > kj ? 1 : 0);
-        }
-        if (cmp < 0) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
 // Per-item header kept in shared memory (one per item slot).
 struct ItemHdr {
@@ -443,93 +354,6 @@ __device__ __forceinline__ bool fetch_item(Pipe &st, const JoinArgs &a, uint32_t
     ++st.grab_pos;
     it = a.items[item];
     return true;
-}
-
-// Candidate ranges of a query cell with coordinates c (odd: their parity
-// bits): one entry per row template that survives the M_j clip and holds
-// points, written to rt as (first record, running candidate count); K is
-// the number of candidates.
-// Under UNICOMP the table holds the home row (template 0), the two stage-0
-// cells (1, 2; gate 0) and, per stage k = 1 .. D-1, 2 * 3^(k-1) rows from
-// template 3^(k-1) + 2 on (gate k).  Only the stages whose gate coordinate
-// is odd take part, so the lanes are mapped onto those templates alone:
-// at 6-D about 123 of 245, half the passes.
-template <int D>
-__device__ __forceinline__ int active_template(uint32_t odd, uint32_t r) {
-    if (r == 0) return 0;
-    --r;
-    if (odd & 1u) {
-        if (r < 2) return 1 + (int)r;
-        r -= 2;
-    }
-    uint32_t p = 1;   // 3^(k-1)
-#pragma unroll
-    for (int k = 1; k < D; ++k) {
-        if ((odd >> k) & 1u) {
-            if (r < 2 * p) return (int)(p + 2 + r);
-            r -= 2 * p;
-        }
-        p *= 3;
-    }
-    return -1;
-}
-
-template <int D>
-__device__ __forceinline__ uint32_t active_templates(uint32_t odd) {
-    uint32_t n = 1 + ((odd & 1u) ? 2u : 0u), p = 1;
-#pragma unroll
-    for (int k = 1; k < D; ++k) {
-        if ((odd >> k) & 1u) n += 2 * p;
-        p *= 3;
-    }
-    return n;
-}
-
-template <int D, bool UNI>
-__device__ __forceinline__ void build_ranges(const int32_t *c, uint32_t odd, const JoinArgs &a,
-                                             uint32_t n_cells, int lane, uint2 *rt,
-                                             uint32_t &nranges, uint32_t &K) {
-    nranges = 0;
-    K = 0;
-    const int n_t = UNI ? (int)active_templates<D>(odd) : a.n_templates;
-    for (int t0 = 0; t0 < n_t; t0 += 32) {
-        const int t = UNI ? (t0 + lane < n_t ? active_template<D>(odd, (uint32_t)(t0 + lane)) : -1)
-                          : (t0 + lane < n_t ? t0 + lane : -1);
-        uint32_t beg = 0, len = 0;
-        int32_t xlo, xhi, b[D];
-        if (t >= 0 && row_of<D, UNI>(t, c, odd, a, xlo, xhi, b)) {
-            uint64_t base = 0;
-#pragma unroll
-            for (int j = 1; j < D; ++j) base += (uint64_t)b[j] * a.stride[j];
-            const uint64_t id_lo = base + (uint64_t)xlo, id_hi = base + (uint64_t)xhi;
-            uint32_t e;
-            if (a.dense) {
-                beg = __ldg(&a.lut[id_lo]);
-                e = __ldg(&a.lut[id_hi + 1]);
-            } else if (a.tuple) {
-                const uint32_t hl = lower_bound_tuple<D>(a.cc, n_cells, b, xlo);
-                const uint32_t hh = lower_bound_tuple<D>(a.cc, n_cells, b, xhi + 1);
-                beg = __ldg(&a.G[hl]);
-                e = __ldg(&a.G[hh]);
-            } else {
-                const uint32_t hl = lower_bound_u64(a.B, n_cells, id_lo);
-                const uint32_t hh = lower_bound_u64(a.B, n_cells, id_hi + 1);
-                beg = __ldg(&a.G[hl]);
-                e = __ldg(&a.G[hh]);
-            }
-            len = e - beg;
-        }
-        const unsigned nz = __ballot_sync(0xffffffffu, len > 0);
-        uint32_t incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (len > 0) rt[nranges + __popc(nz & ((1u << lane) - 1u))] = make_uint2(beg, K + incl);
-        nranges += __popc(nz);
-        K += __shfl_sync(0xffffffffu, incl, 31);
-    }
 }
 
 // Builds ranges, header and staged queries of item `it` in item slot `sl`.
@@ -1045,238 +869,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     }
 }
 
-// The exact predicate for the high-dimensional kernel's rechecks: a
-// function of its own, so that the main kernels' non-inlined recheck keeps
-// its register budget.
-__device__ __noinline__ bool exact_member_hd(const double *__restrict__ a,
-                                             const double *__restrict__ b, int d, double E2) {
-    double s = 0.0;
-    for (int j = 0; j < d; ++j) {
-        const double t = __dsub_rn(a[j], b[j]);
-        s = __dadd_rn(s, __dmul_rn(t, t));
-    }
-    return s <= E2;
-}
-
-// High-dimensional search (points of more than kMaxDim dimensions): the
-// grid covers kHdGridDims of them.  A warp takes one work item at a time,
-// builds its candidate ranges like the main kernel, stages the item's
-// queries (records of all dfull coordinates) in shared memory, and lets each
-// lane take every 32nd candidate of each range, read straight from the
-// cell-ordered records in global memory, and compare it with every query.
-// FP32: the difference-form sum against [lo32, hi32] (margin.cu), values in
-// between rechecked with the exact FP64 predicate on the input points, in a
-// warp-uniform branch; FP64: the exact predicate on the FP64 records.  Hits
-// are written after one atomic reservation per query and 32 candidates.
-// There are no waits, so no time limits.
-template <bool F32, bool UNI, int G4>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
-    hd_join_kernel(const JoinArgs a, const uint32_t *counts) {
-    // DW = 4 G4 >= d coordinates take part; those past d are zero on both
-    // sides, and an exact zero term leaves every sum (FP32 or FP64) unchanged
-    constexpr int K = kHdGridDims;
-    constexpr int DW = 4 * G4;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    unsigned char *wbase = smem + (size_t)warp * a.sm_warp;
-    uint2 *rt = reinterpret_cast<uint2 *>(wbase);
-    // staged queries: DW values each, as (q, q) float pairs (FP32) or doubles
-    unsigned char *qs = wbase + a.sm_ranges;
-    const int dd = a.dfull, rs = a.rsd;
-    const uint32_t n_cells = *a.ccells;
-    uint32_t item_end = a.item_end;
-    if (counts[1] < item_end) item_end = counts[1];
-    const unsigned lt = (1u << lane) - 1u;
-    constexpr unsigned long long kMult = UNI ? 2ull : 1ull;
-    unsigned long long evals = 0, rechecks = 0;
-
-    // one classified hit per lane: reservation by ballot, then the writes
-    auto emit = [&](bool hit, uint32_t qid, uint32_t cid) {
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (!m) return;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)__popc(m) * kMult);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (hit && !a.count_only) {
-            const unsigned long long at = base + (unsigned long long)__popc(m & lt) * kMult;
-            if (at < a.cap) a.out[at] = make_uint2(qid, cid);
-            if (UNI && at + 1 < a.cap) a.out[at + 1] = make_uint2(cid, qid);
-        }
-    };
-
-    for (;;) {
-        uint32_t pos = 0;
-        if (lane == 0) pos = atomicAdd(a.work, 1u);
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        const uint64_t item = (uint64_t)a.item_begin + (uint64_t)pos * a.item_stride;
-        if (item >= item_end) break;
-        const uint2 it = a.items[item];
-        const uint32_t h = it.x;
-        const uint32_t cbeg = __ldg(&a.qG[h]), cend = __ldg(&a.qG[h + 1]);
-        const uint32_t home_len = cend - cbeg;
-        const uint32_t ql0 = it.y * kQueryBlock;
-        const uint32_t q0 = cbeg + ql0;
-        const uint32_t nq = min((uint32_t)kQueryBlock, cend - q0);
-        int32_t c[K];
-        uint32_t odd = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            c[j] = __ldg(&a.qcc[(uint64_t)h * K + j]);
-            odd |= ((uint32_t)c[j] & 1u) << j;
-        }
-        __syncwarp();   // the previous item's ranges and queries are no longer read
-        uint32_t nranges, kc;
-        build_ranges<K, UNI>(c, odd, a, n_cells, lane, rt, nranges, kc);
-        uint32_t qid_l = 0;
-        if (lane < (int)nq) {
-            if (F32) {
-                const float *r = a.recd32 + (size_t)(q0 + lane) * rs;
-                f2_t *qd = reinterpret_cast<f2_t *>(qs) + (size_t)lane * DW;
-#pragma unroll
-                for (int j = 0; j < DW; ++j) {
-                    const float v = j < dd ? r[j] : 0.0f;
-                    qd[j] = f2_pack(v, v);
-                }
-                qid_l = __float_as_uint(r[dd]);
-            } else {
-                const double *r = a.recd64 + (size_t)(q0 + lane) * rs;
-                double *qd = reinterpret_cast<double *>(qs) + (size_t)lane * DW;
-#pragma unroll
-                for (int j = 0; j < DW; ++j) qd[j] = j < dd ? r[j] : 0.0;
-                qid_l = (uint32_t)__double_as_longlong(r[dd]);
-            }
-        }
-        __syncwarp();
-        if (lane == 0)
-            evals += UNI ? (uint64_t)nq * (kc - home_len) + (uint64_t)nq * (home_len - 1) -
-                               (uint64_t)nq * ql0 - (uint64_t)nq * (nq - 1) / 2
-                         : (uint64_t)nq * kc;
-        if (UNI) {
-            // the self-pair of every query, once
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)nq);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (!a.count_only && lane < (int)nq && base + lane < a.cap)
-                a.out[base + lane] = make_uint2(qid_l, qid_l);
-        }
-        uint32_t kstart = 0;
-        for (uint32_t ri = 0; ri < nranges; ++ri) {
-            const uint2 rg = rt[ri];
-            const uint32_t len = rg.y - kstart;
-            if (F32) {
-                // two candidates per lane (p and p + 32), packed as f32x2
-                for (uint32_t p0 = 0; p0 < len; p0 += 64) {
-                    uint32_t cid[2] = {0xffffffffu, 0xffffffffu}, kp[2];
-                    bool valid[2];
-                    float4 y4[2][G4];
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const uint32_t p = p0 + 32 * h2 + lane;
-                        valid[h2] = p < len;
-                        kp[h2] = kstart + p;
-#pragma unroll
-                        for (int g = 0; g < G4; ++g) y4[h2][g] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (valid[h2]) {
-                            const float *r = a.recd32 + (size_t)(rg.x + p) * rs;
-#pragma unroll
-                            for (int g = 0; g < G4; ++g) y4[h2][g] = *reinterpret_cast<const float4 *>(r + 4 * g);
-                            cid[h2] = __float_as_uint(r[dd]);
-                        }
-                    }
-                    f2_t yy[DW];
-#pragma unroll
-                    for (int g = 0; g < G4; ++g) {
-                        const float4 u = y4[0][g], v = y4[1][g];
-                        const int j = 4 * g;
-                        yy[j] = f2_pack(j < dd ? u.x : 0.f, j < dd ? v.x : 0.f);
-                        yy[j + 1] = f2_pack(j + 1 < dd ? u.y : 0.f, j + 1 < dd ? v.y : 0.f);
-                        yy[j + 2] = f2_pack(j + 2 < dd ? u.z : 0.f, j + 2 < dd ? v.z : 0.f);
-                        yy[j + 3] = f2_pack(j + 3 < dd ? u.w : 0.f, j + 3 < dd ? v.w : 0.f);
-                    }
-                    const f2_t neg1 = f2_pack(-1.0f, -1.0f);
-                    for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
-                        const ulonglong2 *qd =
-                            reinterpret_cast<const ulonglong2 *>(reinterpret_cast<const f2_t *>(qs) + (size_t)qi * DW);
-                        f2_t acc = f2_pack(0.0f, 0.0f);
-#pragma unroll
-                        for (int j2 = 0; j2 < DW / 2; ++j2) {
-                            const ulonglong2 q2 = qd[j2];   // (q_j, q_j), (q_j+1, q_j+1)
-                            // fl(q - y) on both halves, then the running fma sum
-                            const f2_t t0 = f2_fma(yy[2 * j2], neg1, q2.x);
-                            acc = f2_fma(t0, t0, acc);
-                            const f2_t t1 = f2_fma(yy[2 * j2 + 1], neg1, q2.y);
-                            acc = f2_fma(t1, t1, acc);
-                        }
-                        float sv[2];
-                        f2_unpack(acc, sv[0], sv[1]);
-                        bool hit[2], band[2];
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            // in the home cell under UNICOMP only candidates after the query
-                            const bool cand =
-                                valid[h2] && (!UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi);
-                            hit[h2] = cand && sv[h2] <= a.hi32;
-                            band[h2] = hit[h2] && !(sv[h2] <= a.lo32);
-                        }
-                        if (__any_sync(0xffffffffu, band[0] || band[1])) {
-#pragma unroll
-                            for (int h2 = 0; h2 < 2; ++h2) {
-                                if (band[h2]) {
-                                    hit[h2] = exact_member_hd(a.ptsd + (size_t)qid * dd,
-                                                              a.ptsd + (size_t)cid[h2] * dd, dd, a.E2);
-                                    ++rechecks;
-                                }
-                            }
-                        }
-                        emit(hit[0], qid, cid[0]);
-                        emit(hit[1], qid, cid[1]);
-                    }
-                }
-            } else {
-                for (uint32_t p0 = 0; p0 < len; p0 += 32) {
-                    const uint32_t p = p0 + lane;
-                    const bool valid = p < len;
-                    const uint32_t kpos = kstart + p;   // position in the item's candidate list
-                    double y[DW];
-                    uint32_t cid = 0xffffffffu;
-#pragma unroll
-                    for (int j = 0; j < DW; ++j) y[j] = 0.0;
-                    if (valid) {
-                        const double *r = a.recd64 + (size_t)(rg.x + p) * rs;
-#pragma unroll
-                        for (int j = 0; j < DW; ++j)
-                            if (j < dd) y[j] = r[j];
-                        cid = (uint32_t)__double_as_longlong(r[dd]);
-                    }
-                    for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
-                        const bool cand = valid && (!UNI || kpos >= home_len || kpos > ql0 + qi);
-                        const double *qd = reinterpret_cast<const double *>(qs) + (size_t)qi * DW;
-                        // the exact predicate, in dimension order (zero terms add nothing)
-                        double sum = 0.0;
-#pragma unroll
-                        for (int j = 0; j < DW; ++j) {
-                            const double t = __dsub_rn(qd[j], y[j]);
-                            sum = __dadd_rn(sum, __dmul_rn(t, t));
-                        }
-                        emit(cand && sum <= a.E2, qid, cid);
-                    }
-                }
-            }
-            kstart = rg.y;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rechecks += __shfl_xor_sync(0xffffffffu, rechecks, o);
-    if (lane == 0) {
-        if (evals) atomicAdd(&a.counter[1], evals);
-        if (rechecks) atomicAdd(&a.counter[2], rechecks);
-    }
-}
-
-typedef void (*KernelFn)(const JoinArgs, const uint32_t *);
+typedef JoinKernelFn KernelFn;
 
 // The FP32 kernels come in a grid-frame and a cell-frame variant, so that
 // each inlines one candidate transform only.
@@ -1285,19 +878,6 @@ KernelFn pick(bool f32, bool uni, bool cell) {
     if (f32 && cell) return uni ? join_kernel<D, true, true, 1> : join_kernel<D, true, false, 1>;
     if (f32) return uni ? join_kernel<D, true, true, 0> : join_kernel<D, true, false, 0>;
     return uni ? join_kernel<D, false, true, 0> : join_kernel<D, false, false, 0>;
-}
-
-// The high-dimensional kernel evaluates 12 (d <= 12) or 16 coordinates.
-template <int G4>
-KernelFn pick_hd(bool f32, bool uni) {
-    if (f32) return uni ? hd_join_kernel<true, true, G4> : hd_join_kernel<true, false, G4>;
-    return uni ? hd_join_kernel<false, true, G4> : hd_join_kernel<false, false, G4>;
-}
-
-KernelFn pick_hd_kernel(int d, bool f32, bool uni) {
-    if (d <= 12) return pick_hd<3>(f32, uni);
-    if (d <= kMaxPointDim) return pick_hd<4>(f32, uni);
-    return nullptr;
 }
 
 KernelFn pick_kernel(int d, bool f32, bool uni, bool cell) {
@@ -1392,7 +972,7 @@ const void *multi_join_fn() { return reinterpret_cast<const void *>(multi_join_k
 
 namespace {
 
-// Entry t of the template table of (d, UNICOMP); see g_templates.
+// Entry t of the template table of (d, UNICOMP) (format in join_dev.cuh).
 uint32_t template_entry(int d, bool uni, uint32_t t) {
     uint32_t pow3[kMaxDim + 1];
     pow3[0] = 1;
@@ -1577,7 +1157,7 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     const bool f32 = a.f32 != 0;
     const bool uni = cfg.unicomp != 0;
 
-    KernelFn fn = ix.dfull > kMaxDim ? pick_hd_kernel(ix.dfull, f32, uni)
+    KernelFn fn = ix.dfull > kMaxDim ? hd_kernel_fn(ix.dfull, f32, uni)   // hd_join.cu
                                      : pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
     int dev = 0;

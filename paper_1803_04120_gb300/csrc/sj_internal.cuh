@@ -1,16 +1,28 @@
 // sj_internal.cuh -- internal declarations of the GB300 self-join library.
 //
 // Layout of the library:
-//   scan.cu     device-wide exclusive scan (u32) used by the index build
-//   sort.cu     LSD radix sort of (u64 key, u32 value) for grids too large
-//               for the dense cell table
-//   index.cu    grid index build (Section IV-B, IV-C): bounds, cell ids,
-//               counting or radix sort by cell, B / G / A / M_j, cell-ordered
-//               FP32 and FP64 point records, work items
-//   join.cu     the persistent search-and-refine kernel (Section IV-D, IV-E,
-//               V-B) in both precision modes
-//   api.cu      the C ABI of include/sj.h: contexts, batching (Section V-A),
-//               results, statistics, the serving loop
+//   scan.cu      device-wide exclusive scan (u32) used by the index build
+//   sort.cu      LSD radix sort of (u64 key, u32 value) for grids too large
+//                for the dense cell table
+//   index.cu     grid index build (Section IV-B, IV-C): bounds, cell ids,
+//                counting, radix or coordinate-tuple sort by cell, B / G / A /
+//                M_j, cell-ordered FP32 and FP64 point records, work items;
+//                the projected grid of points with more than 8 dimensions
+//   margin.cu    the proven FP32 filter margins (grid frame, cell frame,
+//                difference form)
+//   join_dev.cuh device helpers shared by the search kernels (row templates,
+//                candidate ranges, packed FP32 pairs)
+//   join.cu      the persistent search-and-refine kernel (Section IV-D, IV-E,
+//                V-B) in both precision modes, and its launches
+//   hd_join.cu   the search kernel for 9 to 16 dimensions
+//   brute.cu     the index-free comparator
+//   engine.cu    many joins in one persistent launch, replayed as a CUDA graph
+//   serve.cu     the serving loop (continuous batching of join requests)
+//   tune.cu      the launch tuner
+//   shard.cu     one join split over ranks
+//   noalloc.cu   the join without allocation
+//   api.cu       the C ABI of include/sj.h: contexts, batching (Section V-A),
+//                results, statistics
 #pragma once
 
 #include <cuda_runtime.h>
@@ -238,6 +250,11 @@ struct MultiJobs {
     JoinArgs job[kMultiJobs];
 };
 static_assert(sizeof(MultiJobs) <= 32000, "multi-join table exceeds the kernel parameter limit");
+
+// A search-and-refine kernel: (arguments, device counters |G| and items).
+typedef void (*JoinKernelFn)(const JoinArgs, const uint32_t *);
+// The kernel for points of d = 9..16 dimensions (hd_join.cu), null otherwise.
+JoinKernelFn hd_kernel_fn(int d, bool f32, bool uni);
 
 sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                          uint32_t item_end, uint2 *out, uint64_t cap,
