@@ -115,3 +115,14 @@ def test_highdim_wide_range_and_limits():
         assert ei.value.status == sj.SJ_EINVAL
         res = ctx.sj_selfjoin_multi([(pts, 1.0), (pts[:, :3].copy(), 0.5)], raise_errors=False)
         assert ctx.last_multi_status == [sj.SJ_EINVAL, sj.SJ_OK] and res[0] is None
+
+
+@pytest.mark.parametrize("d,m", [(10, 2), (12, 2), (9, 3)])
+def test_highdim_unit_lattice_closed_form(d, m):
+    # spacing 1, eps = 1: every point, itself and its axis neighbours
+    pts = np.stack(np.meshgrid(*[np.arange(m, dtype=np.float64)] * d, indexing="ij"), -1).reshape(-1, d)
+    total = m ** d + 2 * d * (m - 1) * m ** (d - 1)
+    for prec in (sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64):
+        for uni in (True, False):
+            with sj.Context(prec=prec, unicomp=uni) as ctx:
+                assert len(ctx.sj_selfjoin(pts, 1.0)) == total, (d, m, prec, uni)

@@ -103,6 +103,19 @@ def test_unit_lattice_closed_form(d, m):
         assert np.all(deg[interior] == 2 * d + 1)
 
 
+@pytest.mark.parametrize("d,m", [(10, 2), (12, 2), (9, 3)])
+def test_unit_lattice_closed_form_beyond_8_dimensions(d, m):
+    # the brute-force definition, which checks the joins of more than 8
+    # dimensions, against the same closed form
+    pts = lattice(m, d)
+    bf = orc.bruteforce(pts, 1.0)
+    assert bf.size == m ** d + 2 * d * (m - 1) * m ** (d - 1)
+    i, j = keys_to_pairs(bf)
+    # every member pair differs by exactly 1 in one coordinate, or is a self-pair
+    diff = np.abs(pts[i] - pts[j]).sum(axis=1)
+    assert np.all((diff == 0) | (diff == 1))
+
+
 @pytest.mark.parametrize("d,m", [(2, 6), (3, 4)])
 def test_lattice_just_below_spacing_gives_only_self_pairs(d, m):
     pts = lattice(m, d, spacing=1.0, origin=-3.0)
