@@ -43,3 +43,49 @@ def test_no_device_is_an_error_not_a_fallback():
         pytest.skip("a GPU is present")
     with pytest.raises(sj.SJError):
         sj.Context()
+
+
+def test_header_is_plain_c_and_struct_sizes_match_the_binding(tmp_path):
+    """include/sj.h compiles as C99 (no C++ in the boundary), and the sizes
+    of its structs equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "sj.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu\\n", sizeof(sj_config), sizeof(sj_stats),\n'
+        "         sizeof(sj_index_desc), sizeof(sj_job), sizeof(sj_serve_info));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [ctypes.sizeof(t) for t in (sj.sj_config, sj.sj_stats, sj.sj_index_desc, sj.sj_job,
+                                       sj.sj_serve_info)]
+    assert got == want
+
+
+def test_reference_arm_prints_its_json_line():
+    """bench.py --impl reference times the CPU oracle and prints one JSON
+    line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "config", "impl", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
