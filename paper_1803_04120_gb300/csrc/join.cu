@@ -573,10 +573,11 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         for (uint32_t qi = 0; qi < nq; ++qi) {
             float sv[CPL];
             eval_query<D, NP>(qbase + (size_t)qi * a.qrs, z, qq2, sv);
+            const uint32_t bit = 1u << qi;
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
-                m[s] |= (sv[s] <= hi32 ? 1u : 0u) << qi;
-                if (D <= 3) b[s] |= (sv[s] > lo32 ? 1u : 0u) << qi;
+                if (sv[s] <= hi32) m[s] |= bit;
+                if (D <= 3 && sv[s] > lo32) b[s] |= bit;
             }
         }
         uint32_t any = 0;
