@@ -680,9 +680,11 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t_all), 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD + " (bounded query sample per step)"},
+        "config": {"workload": WORKLOAD, "n": 2_000_000, "dims": list(DIMS),
+                   "eps": [round(c["eps"], 6) for c, _ in data],
+                   "precision": "FP64 (the definition; the CPU oracle)", "unicomp": False},
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": desc},
+                         "sample": "bounded query sample per step: " + desc},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
