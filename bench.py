@@ -14,17 +14,21 @@ Printed JSON line (rank 0):
                of every pair inside the timed region)
   fp64         the plain FP64 GPU join on the same inputs (same metric)
   roofline     the search-and-refine kernel of the dominant launch against
-               max(FLOPs / FP32 peak, bytes / HBM bandwidth)
-  cpu_baseline the CPU oracle on the host cores, on a bounded sample
+               max(FLOPs / FP32 peak, bytes / HBM bandwidth), the FP32 peak
+               measured by the library's FMA-chain kernel in this run
+  cpu_baseline the CPU oracle on the host cores: a fixed query sample per d,
+               grid build timed apart, extrapolated to the whole job
+  streamed_10M 10,000,000 uniform points, d = 2..6, 128 neighbours, result
+               buffers capped at 2 GB: pairs streamed to pinned host memory
   skew         clustered 5,000,000 points (d = 2, 3, eps = 0.5): device join
                with the tuned launch parameters against the fixed defaults
   ablation     the join kernel with and without UNICOMP, and the indexed
                join against the index-free brute-force comparator
-  serving      a stream of join requests (n log-uniform in [1e3, 1e6],
-               d in 2..6, 8..128 mean neighbours) through sj_submit/sj_poll,
-               all at once (saturated) and with Poisson arrivals at half the
-               saturated rate: p50/p99 latency and pairs/s, against the same
-               requests joined one at a time through sj_selfjoin
+  serving      10,000 join requests (n log-uniform in [1e3, 1e6], d in
+               2..6, 8..128 mean neighbours) through sj_submit/sj_poll, all
+               at once (saturated) and with Poisson arrivals swept over
+               0.25..1 of the saturated rate: p50/p99 latency and pairs/s,
+               against requests joined one at a time through sj_selfjoin
 --impl reference times the CPU oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -71,6 +75,16 @@ def profiled_traffic(d: int):
     return int(t.group(1))
 
 
+DATA = "synthetic (seeded uniform, stands in for the paper's Syn- datasets)"
+
+
+def bench_config(data):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": WORKLOAD, "n": 2_000_000, "dims": list(DIMS),
+            "eps": [round(c["eps"], 6) for c, _ in data],
+            "l2": "GPU arm: flushed between timed steps (512 MiB write); CPU arm: n/a"}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm, src = 6800.0, "fallback"
@@ -86,6 +100,25 @@ def peaks():
     # FP32 (CUDA-core) peak: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
     fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     return hbm, src, fp32_tflops
+
+
+def fp32_rate(dev: int):
+    """FP32 fused multiply-add rate of the GPU (library kernel, CUDA events),
+    scalar fma.rn.f32 and packed fma.rn.f32x2, with the SM clocks sampled
+    meanwhile; None when the measurement fails."""
+    from paper_1803_04120_gb300 import sj
+    clk = ClockSampler(dev)
+    clk.start()
+    try:
+        sc, sc_ms = sj.sj_fp32_fma_rate(dev, packed=False)
+        pk, pk_ms = sj.sj_fp32_fma_rate(dev, packed=True)
+    except Exception:
+        clk.stop()
+        return None
+    c = clk.stop()
+    return {"scalar_tflops": round(sc, 2), "packed_tflops": round(pk, 2),
+            "packed_over_scalar": round(pk / sc, 3), "scalar_ms": round(sc_ms, 3),
+            "packed_ms": round(pk_ms, 3), "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")}
 
 
 class ClockSampler:
@@ -152,29 +185,52 @@ def workload():
 
 # ---------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_sample(data, budget_s: float):
-    """Times the oracle's grid search on a sample of query points of every
-    dataset; returns (pairs/s, cores, description)."""
+# Query points per dimension of the oracle's timed sample (the same in the
+# reference arm and in the GPU arm's cpu_baseline): about a second of
+# search on 16 cores each, with the grid build timed apart.
+ORACLE_SAMPLE = {2: 400_000, 3: 200_000, 4: 80_000, 5: 30_000, 6: 16_000}
+
+
+def oracle_build_seconds(data):
+    """Grid build time of the oracle per dataset: a search pass with a
+    single query is the build alone."""
+    from oracle import oracle as orc
+    out = {}
+    for cfg, pts in data:
+        t0 = time.perf_counter()
+        orc.grid_neighbor_counts(pts, cfg["eps"], np.zeros(1, dtype=np.uint32))
+        out[cfg["d"]] = time.perf_counter() - t0
+    return out
+
+
+def oracle_sample(data, build_s):
+    """One timed pass of the CPU oracle (Algorithm 1's grid search, exact FP64
+    predicate, all host cores) over a fixed query sample of every dataset.
+    Each pass builds the grid and searches the sample; the query phase is
+    the pass minus the build time.  The whole-job rate extrapolates every
+    dataset to all of its points: sum of pairs x n/m over sum of
+    (build + query time x n/m)."""
     from oracle import oracle as orc
     cores = orc.default_threads()
-    tot_pairs, tot_time, desc = 0, 0.0, []
-    per = budget_s / len(data)
+    job_pairs = job_time = q_pairs = q_time = 0.0
     for cfg, pts in data:
-        n = pts.shape[0]
-        rng = np.random.default_rng(cfg["d"])
-        m = 2000
-        while True:
-            q = np.sort(rng.choice(n, size=min(m, n), replace=False)).astype(np.uint32)
-            t0 = time.perf_counter()
-            offs, _ = orc.grid_neighbors(pts, cfg["eps"], q, nthreads=cores)
-            dt = time.perf_counter() - t0
-            if dt > per * 0.3 or m >= n:
-                break
-            m = int(min(n, m * max(2.0, per * 0.5 / max(dt, 1e-3))))
-        tot_pairs += int(offs[-1])
-        tot_time += dt
-        desc.append(f"d={cfg['d']}: {len(q)} queries")
-    return tot_pairs / tot_time, cores, "; ".join(desc) + " (grid build included)"
+        n, d = pts.shape
+        m = min(n, ORACLE_SAMPLE[d])
+        q = np.sort(np.random.default_rng(100 + d).choice(n, size=m, replace=False)).astype(np.uint32)
+        t0 = time.perf_counter()
+        offs = orc.grid_neighbor_counts(pts, cfg["eps"], q, nthreads=cores)
+        tq = max(time.perf_counter() - t0 - build_s[d], 1e-6)
+        pairs = float(offs[-1])
+        q_pairs += pairs
+        q_time += tq
+        job_pairs += pairs * n / m
+        job_time += build_s[d] + tq * n / m
+    sample = ("fixed query sample per d (" +
+              ", ".join(f"d={cfg['d']}: {min(p.shape[0], ORACLE_SAMPLE[cfg['d']]):,}" for cfg, p in data) +
+              " of 2,000,000 points); grid build timed apart; value extrapolates each d to all points")
+    return {"value": job_pairs / job_time, "query_pairs_per_s": q_pairs / q_time,
+            "build_s": {str(d): round(t, 3) for d, t in build_s.items()},
+            "cores": cores, "sample": sample, "pass_s": q_time + sum(build_s.values())}
 
 
 # ---------------------------------------------------------------- skew
@@ -413,14 +469,25 @@ def _pct(v, q):
     return round(float(np.percentile(np.asarray(v) * 1e3, q)), 3)
 
 
-def serving_bench(dev: int, n_req: int, seed: int = 5):
-    """The request stream through the serving loop, saturated and Poisson,
-    against one-at-a-time joins of the same requests."""
+SWEEP = (0.25, 0.5, 0.75, 1.0)
+
+
+def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
+    """The request stream of n_req self-joins through the serving loop:
+    all at once (saturated), then Poisson arrivals swept over fractions of
+    the saturated request rate; against one-at-a-time joins of the first
+    baseline_req requests through sj_selfjoin (plain FP64 and FP32).
+    Request r takes the first n_r points of one of four pooled uniform sets
+    of its dimension (10,000 independent sets of up to 1e6 points would not
+    fit in host memory); every request is joined in full."""
     import threading
     from paper_1803_04120_gb300 import sj
 
     reqs = datagen.serving_requests(n_req, seed, rate_hz=1.0)
-    pts = [datagen.uniform(r["n"], r["d"], r["seed"]) for r in reqs]
+    pools = {d: [datagen.uniform(1_000_000, d, seed=9000 + 10 * d + k) for k in range(4)]
+             for d in range(2, 7)}
+    pts = [pools[r["d"]][k % 4][: r["n"]] for k, r in enumerate(reqs)]
+    nb = min(baseline_req, n_req)
 
     def one_at_a_time(prec):
         with sj.Context(prec=prec, device=dev) as c:
@@ -428,7 +495,7 @@ def serving_bench(dev: int, n_req: int, seed: int = 5):
             c.sj_result_free(r)
             lat, tot = [], 0
             t0 = time.perf_counter()
-            for p, q in zip(pts, reqs):
+            for p, q in zip(pts[:nb], reqs[:nb]):
                 t = time.perf_counter()
                 r = c.sj_selfjoin_raw(p, q["eps"])
                 tot += c.sj_result_count(r)
@@ -468,27 +535,32 @@ def serving_bench(dev: int, n_req: int, seed: int = 5):
         wall = max(td for _, (ts, ta, td) in got) - min(ts for _, (ts, ta, td) in got)
         return sum(c for c, _ in got), wall, lat
 
-    run([0.0] * n_req)                    # untimed pass: pinned result buffers, pool
+    run([0.0] * nb)                       # untimed pass: pinned result buffers, pool
     p_sat, wall_sat, lat_sat = run([0.0] * n_req)
-    assert p_sat == tot64
-    rate = 0.5 * n_req / wall_sat
-    arrivals = [r["arrival_s"] for r in datagen.serving_requests(n_req, seed, rate_hz=rate)]
-    p_poi, wall_poi, lat_poi = run(arrivals)
-    assert p_poi == tot64
+    assert n_req > nb or p_sat == tot64
+    rate_sat = n_req / wall_sat
+    sweep = []
+    for f in SWEEP:
+        arrivals = [r["arrival_s"] for r in datagen.serving_requests(n_req, seed, rate_hz=f * rate_sat)]
+        p_poi, wall_poi, lat_poi = run(arrivals)
+        assert p_poi == p_sat
+        sweep.append({"load": f, "offered_req_per_s": round(f * rate_sat, 1),
+                      "req_per_s": round(n_req / wall_poi, 1),
+                      "pairs_per_s": round(p_poi / wall_poi, 1),
+                      "p50_ms": _pct(lat_poi, 50), "p99_ms": _pct(lat_poi, 99)})
     info = ctx.sj_serve_stats()
     ctx.close()
     return {
-        "requests": n_req, "pairs": tot64,
+        "requests": n_req, "pairs": p_sat,
         "request_mix": "n log-uniform [1e3,1e6], d uniform {2..6}, eps for U[8,128] mean neighbours, "
-                       "uniform [0,100]^d (seeded)",
-        "saturated": {"pairs_per_s": round(p_sat / wall_sat, 1), "req_per_s": round(n_req / wall_sat, 1),
+                       "uniform [0,100]^d: the first n points of one of four pooled seeded sets per d",
+        "saturated": {"pairs_per_s": round(p_sat / wall_sat, 1), "req_per_s": round(rate_sat, 1),
                       "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99)},
-        "poisson": {"rate_hz": round(rate, 1), "pairs_per_s": round(p_poi / wall_poi, 1),
-                    "p50_ms": _pct(lat_poi, 50), "p99_ms": _pct(lat_poi, 99)},
-        "one_at_a_time_fp64": {"pairs_per_s": round(tot64 / wall64, 1), "p50_ms": _pct(lat64, 50),
-                               "p99_ms": _pct(lat64, 99)},
-        "one_at_a_time_fp32": {"pairs_per_s": round(tot32 / wall32, 1), "p50_ms": _pct(lat32, 50),
-                               "p99_ms": _pct(lat32, 99)},
+        "sweep": sweep,
+        "one_at_a_time_fp64": {"requests": nb, "pairs_per_s": round(tot64 / wall64, 1),
+                               "p50_ms": _pct(lat64, 50), "p99_ms": _pct(lat64, 99)},
+        "one_at_a_time_fp32": {"requests": nb, "pairs_per_s": round(tot32 / wall32, 1),
+                               "p50_ms": _pct(lat32, 50), "p99_ms": _pct(lat32, 99)},
         "speedup_vs_plain_one_at_a_time": round((p_sat / wall_sat) / (tot64 / wall64), 2),
         "waves": info["waves"], "max_wave": info["max_wave"],
         "max_concurrent_waves": info["max_concurrent_waves"], "overflow_reruns": info["overflow_reruns"],
@@ -496,6 +568,51 @@ def serving_bench(dev: int, n_req: int, seed: int = 5):
         "lane_ms": {"bounds": round(info["ms_bounds"], 1), "graph": round(info["ms_graph"], 1),
                     "output": round(info["ms_output"], 1)},
     }
+
+
+# ---------------------------------------------------------------- streamed 10M
+
+def stream_bench(dev: int, reps: int):
+    """10,000,000 uniform points for d = 2..6 with 128 mean neighbours (about
+    1.3e9 pairs each), device result buffers capped at 2 GB: the pairs stream
+    to pinned host memory in batches (Section V-A), each batch's kernel
+    overlapped with the previous batch's copy.  End-to-end pairs/s (host
+    points in, every pair delivered to the host), the batch count, and the
+    join kernels' share of the wall time."""
+    from paper_1803_04120_gb300 import sj
+
+    out = []
+    with sj.Context(device=dev, out_cap_bytes=2 << 30, profile=True) as ctx:
+        for d in DIMS:
+            cfg = datagen.config3(d)
+            pts = datagen.make_points(cfg)
+            got = [0]
+
+            def cb(k):
+                got[0] += k
+                return False
+
+            ctx.sj_selfjoin_stream(pts, cfg["eps"], cb, copy=False)    # warm-up (tunes)
+            best, st, kms = None, None, 0.0
+            for _ in range(reps):
+                got[0] = 0
+                ctx.sj_profile_read()
+                t0 = time.perf_counter()
+                ctx.sj_selfjoin_stream(pts, cfg["eps"], cb, copy=False)
+                t = time.perf_counter() - t0
+                ms, _ = ctx.sj_profile_read()
+                if best is None or t < best:
+                    best, st, kms = t, ctx.sj_last_stats(), ms
+            pairs = got[0]
+            out.append({"d": d, "n": cfg["n"], "eps": round(cfg["eps"], 6), "pairs": pairs,
+                        "batches": st["batches"], "retries": st["retries"],
+                        "wall_ms": round(best * 1e3, 2), "pairs_per_s": round(pairs / best, 1),
+                        "join_kernels_ms": round(kms, 2),
+                        "d2h_gb_per_s": round(8 * pairs / best / 1e9, 1)})
+    return {"workload": "uniform 10,000,000 points in [0,100]^d, d=2..6, eps for 128 mean "
+                        "neighbours, out_cap_bytes = 2 GB, sj_selfjoin_stream (host points in, "
+                        "pairs to pinned host memory)", "per_d": out,
+            "pairs_per_s": round(sum(r["pairs"] for r in out) / sum(r["wall_ms"] / 1e3 for r in out), 1)}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -579,8 +696,11 @@ def run_gpu(args):
     e2e_value = pairs_step / (sum(e2e_times) / len(e2e_times))
     h2d = sum(p.nbytes for _, p in data)
 
-    # roofline of the join kernel, per launch, per d
-    hbm, psrc, fp32 = peaks()
+    # roofline of the join kernel, per launch, per d; the FP32 peak is the
+    # FMA rate measured here (scalar and packed f32x2, the faster one)
+    hbm, psrc, fp32_derived = peaks()
+    fma = fp32_rate(dev)
+    fp32 = max(fma["scalar_tflops"], fma["packed_tflops"]) if fma else fp32_derived
     roof_all = []
     for (cfg, pts), (ms, nl), st, cnt in zip(data, prof, stats, counts):
         d = cfg["d"]
@@ -603,8 +723,10 @@ def run_gpu(args):
                     traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
                                    "(profiles/join_kernel_uniform2M.md); null when the kernel changed",
                     kernel=f"join_kernel d={dom['d']}",
-                    peak_source=("fp32: 152 SMs x 128 lanes x 2 x max SM clock" if dom["bound"] == "alu"
-                                 else f"hbm_gbs {psrc}"),
+                    peak_source=(("measured: FP32 FMA chains on every SM (sj_fp32_fma_rate), faster of "
+                                  "scalar and f32x2" if fma else
+                                  "derived: 152 SMs x 128 lanes x 2 x max SM clock")
+                                 if dom["bound"] == "alu" else f"hbm_gbs {psrc}"),
                     all_launches_frac=round(sum(r["roofline_ms"] for r in roof_all)
                                             / sum(r["kernel_ms"] for r in roof_all), 4))
 
@@ -612,11 +734,8 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic (seeded uniform, stands in for the paper's Syn- datasets)",
-        "config": {"workload": WORKLOAD, "n": 2_000_000, "dims": list(DIMS),
-                   "eps": [round(c["eps"], 6) for c, _ in data], "pairs_per_step": pairs_step,
-                   "precision": "FP32 filter with proven margin + FP64 recheck (exact set)",
-                   "unicomp": True, "l2": "flushed between steps (512 MiB write)"},
+        "data": DATA, "config": bench_config(data), "pairs_per_step": pairs_step,
+        "precision": "FP32 filter with proven margin + FP64 recheck (exact set), UNICOMP",
         "fp64": {"value": round(fp64_value, 1), "unit": UNIT,
                  "ms_per_step": round(sum(t64) / len(t64), 4), "speedup_fp32": round(value / fp64_value, 2)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -624,6 +743,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": roofline,
         "roofline_all": roof_all,
+        "fp32_peak": dict(fma or {}, derived_tflops=round(fp32_derived, 1)),
         "clocks": clocks,
     }
     for c in ctx32:
@@ -631,6 +751,8 @@ def run_gpu(args):
     ctx64.close()
     del outs
     torch.cuda.empty_cache()
+    if not args.no_stream:
+        line["streamed_10M"] = stream_bench(dev, max(1, min(args.steps, 3)))
     if args.serve_requests > 0:
         line["serving"] = serving_bench(dev, args.serve_requests)
     if not args.no_skew:
@@ -642,9 +764,11 @@ def run_gpu(args):
     if not args.no_highdim:
         line["highdim"] = highdim_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_cpu:
-        v, cores, desc = cpu_oracle_sample(data, args.cpu_budget)
-        line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": desc}
+        r = oracle_sample(data, oracle_build_seconds(data))
+        line["cpu_baseline"] = {"value": round(r["value"], 1), "unit": UNIT, "cores": r["cores"],
+                                "kind": "oracle", "sample": r["sample"],
+                                "query_pairs_per_s": round(r["query_pairs_per_s"], 1),
+                                "build_s": r["build_s"]}
     return line
 
 
@@ -660,31 +784,34 @@ def replica_value(ms_local: float, pairs_per_step: int, device: str):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle alone, each step one timed pass over
+    the fixed query sample of every dataset (oracle_sample), on all host
+    cores.  Under torchrun only rank 0 runs."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     data = workload()
-    vals = []
-    cores, desc = None, None
+    build_s = oracle_build_seconds(data)
     for _ in range(args.warmup):
-        cpu_oracle_sample(data, 2.0)
-    t_all = []
+        oracle_sample(data, build_s)
+    vals, qvals, t_all, r = [], [], [], None
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        v, cores, desc = cpu_oracle_sample(data, args.cpu_budget / max(1, args.steps))
+        r = oracle_sample(data, build_s)
         t_all.append(time.perf_counter() - t0)
-        vals.append(v)
+        vals.append(r["value"])
+        qvals.append(r["query_pairs_per_s"])
     value = statistics.mean(vals)
     return {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t_all), 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "n": 2_000_000, "dims": list(DIMS),
-                   "eps": [round(c["eps"], 6) for c, _ in data],
-                   "precision": "FP64 (the definition; the CPU oracle)", "unicomp": False},
-        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "bounded query sample per step: " + desc},
+        "data": DATA, "impl": "reference", "config": bench_config(data),
+        "precision": "FP64 (the definition; the CPU oracle, Algorithm 1 without UNICOMP)",
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"],
+                         "query_pairs_per_s": round(statistics.mean(qvals), 1),
+                         "build_s": r["build_s"]},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -697,9 +824,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
-    ap.add_argument("--serve-requests", type=int, default=300,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the serving stream (0: skip)")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="skip the streamed 10,000,000-point workloads")
     ap.add_argument("--no-skew", action="store_true", help="skip the clustered workload")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the UNICOMP and brute-force comparisons")
@@ -720,7 +848,7 @@ def main():
         # whole-job value is the sum over ranks of pairs over the max time
         # (the serving and clustered sections are single-GPU measurements)
         args.serve_requests, args.no_skew, args.no_ablation, args.no_frames = 0, True, True, True
-        args.no_highdim = True
+        args.no_highdim = args.no_stream = True
         import torch.distributed as dist
         dist.init_process_group("nccl")
         args.no_cpu = args.no_cpu or rank != 0

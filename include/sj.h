@@ -154,7 +154,19 @@ typedef struct {
     int32_t wpb;             /* warps per block (1, 2, 4 or 8) */
     int32_t slots;           /* work items a warp holds at once (1 or 2) */
     int32_t frame;           /* sj_frame; default SJ_FRAME_AUTO */
-    int32_t reserved[2];
+    int32_t wait_ms;         /* limit of every bounded wait inside the search
+                                kernel (a warp waiting for its staged
+                                candidate copies), in ms; 0 (default): 2000.
+                                A wait that expires ends the call with
+                                SJ_ETIMEOUT and leaves the context usable. */
+    int32_t test_stall;      /* test hook, 0 (default) in normal use.  1: in
+                                every single-join search launch of this
+                                context, warp 0 of block 0 never issues its
+                                first candidate copy, so its wait for that
+                                copy expires after wait_ms (no copy is in
+                                flight for it) and the call returns
+                                SJ_ETIMEOUT.  Lets a test drive the time-out
+                                path without any fault. */
 } sj_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -261,6 +273,17 @@ SJ_API sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
 SJ_API sj_status sj_fp32_margin_diff(int d, double eps, const double *fmin,
                                      const double *fmax, float *lo, float *hi);
 
+/* Measured FP32 rate of this GPU, the denominator of the search kernel's
+ * roofline (the paper has no counterpart; it measures on other hardware).
+ * Runs independent FP32 fused multiply-add chains on every SM of `device`
+ * at full occupancy, scalar fma.rn.f32 (packed = 0) or packed
+ * fma.rn.f32x2 (packed = 1), and reports the best of five timed launches:
+ * *tflops counts two FLOPs per FMA lane, *ms is that launch's time.
+ * Allocates a small device buffer (one float per thread) and a stream for
+ * the call.  Errors: SJ_EINVAL for NULL outputs or a negative device,
+ * SJ_ECUDA when the device or a launch fails. */
+SJ_API sj_status sj_fp32_fma_rate(int device, int packed, double *tflops, double *ms);
+
 /* ------------------------------------------------------------------ */
 /* Self-join.                                                         */
 /* ------------------------------------------------------------------ */
@@ -345,8 +368,9 @@ SJ_API sj_status sj_selfjoin_stream(sj_ctx *ctx, const double *pts, uint64_t n, 
  *   stream   a cudaStream_t (NULL: legacy default stream); the call waits
  *            for it before returning;
  *   msg      optional buffer of msg_len bytes for an error message.
- * Limits: n <= 65536 points, d in [1, 8], and the grid (Section IV-B) at
- * most 2^20 cells, else SJ_ERANGE; host pointers are rejected with
+ * Limits: n <= 65536 points, d in [1, 8], and at most 2^20 grid cells of
+ * side ~eps over the points' bounding box, else SJ_ERANGE; host pointers
+ * are rejected with
  * SJ_EINVAL.  The region's device address is looked up on the first call on
  * each device (make that first call before any stream capture).  Calls share
  * the region: they are serialised within the process, and work that

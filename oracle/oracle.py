@@ -205,6 +205,19 @@ def grid_neighbors(points, eps: float, queries, nthreads: int | None = None):
     return offs, ids
 
 
+def grid_neighbor_counts(points, eps: float, queries, nthreads: int | None = None):
+    """offsets[nq+1] of the neighbour lists of the listed queries (the counts
+    only): one grid build and one search pass, nothing copied out."""
+    p = _pts(points)
+    n, d = p.shape
+    q = np.ascontiguousarray(queries, dtype=np.uint32)
+    offs = np.zeros(q.shape[0] + 1, dtype=np.uint64)
+    _check(_load().sj_oracle_grid_neighbors(_ptr(p), n, d, float(eps), nthreads or default_threads(),
+                                            _ptr(q), q.shape[0], _ptr(offs), None, 0),
+           "grid_neighbor_counts")
+    return offs
+
+
 def grid_cells(points, eps: float):
     """(|g_j| per dimension, linear cell id of every point) of the grid of
     Section IV-B as the oracle builds it."""

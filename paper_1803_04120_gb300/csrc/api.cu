@@ -214,6 +214,8 @@ JoinLaunch default_launch(const sj_ctx *ctx) {
     l.eb = ctx->cfg.staging > 0 ? ctx->cfg.staging : 0;
     l.wpb = ctx->cfg.wpb > 0 ? ctx->cfg.wpb : 0;
     l.slots = ctx->cfg.slots > 0 ? ctx->cfg.slots : 0;
+    l.timeout_ns = ctx->cfg.wait_ms > 0 ? (uint64_t)ctx->cfg.wait_ms * 1000000ull : 0;
+    l.stall = ctx->cfg.test_stall ? 1 : 0;
     return l;
 }
 
@@ -608,6 +610,7 @@ sj_status sj_create(const sj_config *cfg, sj_ctx **out) {
     if (c.prec != SJ_PREC_FP64 && c.prec != SJ_PREC_FP32_RECHECK) return SJ_EINVAL;
     if (c.lookup < SJ_LOOKUP_AUTO || c.lookup > SJ_LOOKUP_COORDS) return SJ_EINVAL;
     if (c.frame < SJ_FRAME_AUTO || c.frame > SJ_FRAME_CELL) return SJ_EINVAL;
+    if (c.wait_ms < 0) return SJ_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
         cudaGetLastError();

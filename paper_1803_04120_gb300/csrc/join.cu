@@ -789,8 +789,11 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                     st.rcur = 0;
                     continue;
                 }
-                issue_chunk<CB>(ws, ps, st.p_chunk, st.issued % nbuf, st.rcur, rec, rsb, lane,
-                                a.sm_chunk);
+                // test hook: one warp never issues its first chunk, so its
+                // wait for that chunk runs out (no copy is in flight for it)
+                if (!(a.stall && st.issued == 0 && blockIdx.x == 0 && warp == 0))
+                    issue_chunk<CB>(ws, ps, st.p_chunk, st.issued % nbuf, st.rcur, rec, rsb, lane,
+                                    a.sm_chunk);
                 ++st.issued;
                 ++st.p_chunk;
             }
@@ -1129,7 +1132,8 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     a.slots = (cfg.slots == 1 || cfg.slots == 2) ? cfg.slots : slots_for(d, f32);
     a.sm_warp = 64 + round16(a.slots * (int)sizeof(ItemHdr)) + a.slots * a.sm_ranges +
                 a.slots * a.sm_queries + a.nbuf * a.sm_chunk + a.sm_emit;
-    a.timeout_ns = 2000000000ull;
+    a.timeout_ns = cfg.timeout_ns > 0 ? cfg.timeout_ns : 2000000000ull;
+    a.stall = cfg.stall;
     a.d = d;
     a.f32 = f32 ? 1 : 0;
     a.dcounts = n_items_dev(q) - 1;

@@ -15,10 +15,10 @@
 // not use the array's name as a device address: the address is obtained with
 // cudaGetSymbolAddress on the first call on each device (with that device
 // current) and cached.  All calls share the region and it keeps the previous
-// call's contents; the build clears what must start at zero.  Calls are
-// serialised on the host by a mutex and each call waits for its own stream,
-// but work that overlaps on the GPU with a call from another process or with
-// a stream the caller keeps running into the same region would race.
+// call's contents; the build clears what must start at zero.  Two calls
+// whose work overlapped on the GPU would race on the region, so the library
+// serialises them: a host mutex, held until the call's stream has finished.
+// (Each process has its own copy of the region in its own CUDA context.)
 #include <cmath>
 #include <cstdio>
 #include <cstring>

@@ -216,7 +216,8 @@ struct JoinArgs {
     int eb;                         // emission staging entries
     int nbuf;                       // chunk ring depth (2..8)
     int slots;                      // item slots per warp (1 or 2)
-    uint64_t timeout_ns;
+    uint64_t timeout_ns;            // limit of each bounded mbarrier wait
+    int stall;                      // test hook: warp 0 of block 0 skips its first copy
     // multi-join launches: the dimension and precision of this job and its
     // device counters (|G|, work items) in place of the kernel argument
     int d;
@@ -240,6 +241,8 @@ struct JoinLaunch {
     int nbuf = 0;                   // chunk ring depth; 0: by dimension and precision
     int eb = 0;                     // staged pairs per warp (128..1024); 0: by dimension
     int slots = 0;                  // item slots per warp (1 or 2); 0: by dimension
+    uint64_t timeout_ns = 0;        // bounded waits; 0: 2 s
+    int stall = 0;                  // test hook (sj_config.test_stall)
 };
 
 // Job table of a multi-join launch, passed in the kernel parameters.

@@ -9,6 +9,13 @@ splitmix64 output for state ``seed * G + (sub << 40) + (k + 1) * G`` with
 come out on any machine and any chunking.  A uniform double in [0, 1) is
 ``(z >> 11) * 2^-53``.
 
+Every derived value (Gaussian deviates, log-uniform draws, the epsilon of a
+target neighbour count) is computed with IEEE-exact operations only (+, -, *,
+/, sqrt, frexp, ldexp) through the series in ``_ln``, ``_exp`` and ``_root``,
+never with the platform's libm: the same bits come out on x86-64 and on
+AArch64, so expected values stored by the oracle on one machine hold on the
+other.
+
 Workloads (the paper's synthetic datasets, Section VI-A: coordinates i.i.d.
 uniform in [0, 100]^n, FP64):
   * ``uniform(n, d, seed)`` -- the Syn- datasets.
@@ -23,8 +30,6 @@ uniform in [0, 100]^n, FP64):
     uneven size and dimension with Poisson arrivals.
 """
 from __future__ import annotations
-
-import math
 
 import numpy as np
 
@@ -67,15 +72,99 @@ def uniform(n: int, d: int, seed: int, lo: float = 0.0, hi: float = 100.0) -> np
     return (lo + u * (hi - lo)).reshape(n, d)
 
 
+_LN2 = 0.6931471805599453          # ln 2 rounded to double
+_SQRT_HALF = 0.7071067811865476    # sqrt(1/2) rounded to double
+_PI = 3.141592653589793            # pi rounded to double
+
+
+def _ln(x) -> np.ndarray:
+    """Natural logarithm of positive finite doubles from IEEE-exact steps:
+    x = m 2^e with m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(t) with
+    t = (m - 1) / (m + 1), |t| <= 0.1716, summed as the odd series to the
+    t^25 term (remainder below 1e-20)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    small = m < _SQRT_HALF
+    m = np.where(small, m * 2.0, m)
+    e = np.where(small, e - 1, e).astype(np.float64)
+    t = (m - 1.0) / (m + 1.0)
+    t2 = t * t
+    acc = np.full_like(t, 1.0 / 25.0)
+    for k in range(11, -1, -1):
+        acc = acc * t2 + 1.0 / (2 * k + 1)
+    return 2.0 * t * acc + e * _LN2
+
+
+def _exp(x) -> np.ndarray:
+    """exp of doubles in about [-700, 700] from IEEE-exact steps: x = k ln 2
+    + r with |r| <= ln 2, exp(r) as its Taylor series to the r^24 term
+    (remainder below 1e-24), then scaled by 2^k exactly."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.floor(x / _LN2 + 0.5)
+    r = x - k * _LN2
+    acc = np.ones_like(r)
+    for n in range(24, 0, -1):
+        acc = acc * (r / float(n)) + 1.0
+    return np.ldexp(acc, k.astype(np.int64))
+
+
+def _root(x: float, d: int) -> float:
+    """x^(1/d) for x > 0: a start from _exp(_ln(x) / d), then Newton steps
+    y <- y - (y^d - x) / (d y^(d-1)) in plain arithmetic."""
+    y = float(_exp(_ln(x) / d))
+    for _ in range(4):
+        yd1 = 1.0
+        for _ in range(d - 1):
+            yd1 *= y
+        y = y - (yd1 * y - x) / (d * yd1)
+    return y
+
+
+def normals(seed: int, sub: int, count: int) -> np.ndarray:
+    """``count`` standard normal deviates by Marsaglia's polar method on the
+    uniform streams (seed, sub) and (seed, sub + 1): pairs (v1, v2) uniform
+    in [-1, 1)^2 are kept when 0 < s = v1^2 + v2^2 < 1 and give
+    v1 f, v2 f with f = sqrt(-2 ln s / s)."""
+    need = (count + 1) // 2
+    parts, got, start = [], 0, 0
+    while got < need:
+        cnt = int((need - got) * 1.3) + 1024
+        v1 = 2.0 * unit(seed, sub, cnt, start) - 1.0
+        v2 = 2.0 * unit(seed, sub + 1, cnt, start) - 1.0
+        s = v1 * v1 + v2 * v2
+        ok = (s > 0.0) & (s < 1.0)
+        v1, v2, s = v1[ok], v2[ok], s[ok]
+        f = np.sqrt(-2.0 * _ln(s) / s)
+        parts.append(np.stack([v1 * f, v2 * f], axis=1).reshape(-1))
+        got += int(ok.sum())
+        start += cnt
+    return np.concatenate(parts)[:count]
+
+
 def ball_volume(d: int) -> float:
-    """Volume of the unit ball in d dimensions, pi^(d/2) / Gamma(d/2 + 1)."""
-    return math.pi ** (d / 2.0) / math.gamma(d / 2.0 + 1.0)
+    """Volume of the unit ball in d dimensions, pi^(d/2) / Gamma(d/2 + 1):
+    pi^k / k! for d = 2k, 2^(k+1) pi^k / (2k+1)!! for d = 2k + 1."""
+    v = 1.0
+    if d % 2 == 0:
+        for i in range(1, d // 2 + 1):
+            v = v * _PI / i
+    else:
+        v = 2.0
+        for i in range(1, d // 2 + 1):
+            v = v * 2.0 * _PI / (2 * i + 1)
+    return v
 
 
 def eps_for_neighbors(n: int, d: int, k: float, side: float = 100.0) -> float:
     """epsilon with ball volume x density = k (self excluded)."""
-    rho = n / side ** d
-    return (k / (ball_volume(d) * rho)) ** (1.0 / d)
+    sd = 1.0
+    for _ in range(d):
+        sd *= side
+    rho = n / sd
+    return _root(k / (ball_volume(d) * rho), d)
+
+
+_LN50 = 3.912023005428146          # ln 50 rounded to double
 
 
 def clustered(n: int, d: int, seed: int, clusters: int = 1000,
@@ -85,14 +174,10 @@ def clustered(n: int, d: int, seed: int, clusters: int = 1000,
     (the cluster widths stay in [0.1, 5])."""
     centres = unit(seed, 1, clusters * d).reshape(clusters, d) * side
     lu = unit(seed, 2, clusters)
-    sigma = np.exp(math.log(0.1) + lu * (math.log(5.0) - math.log(0.1)))
+    sigma = 0.1 * _exp(lu * _LN50)          # log-uniform in [0.1, 5)
     n_cl = int(round(n * frac_clustered))
     which = np.minimum((unit(seed, 3, n_cl) * clusters).astype(np.int64), clusters - 1)
-    # Box-Muller on pairs of uniforms
-    m = n_cl * d
-    u1 = unit(seed, 4, m)
-    u2 = unit(seed, 5, m)
-    g = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+    g = normals(seed, 4, n_cl * d)
     pts_cl = centres[which] + g.reshape(n_cl, d) * sigma[which][:, None]
     pts_bg = unit(seed, 6, (n - n_cl) * d).reshape(n - n_cl, d) * side
     pts = np.concatenate([pts_cl, pts_bg], axis=0)
@@ -107,9 +192,10 @@ def serving_requests(count: int, seed: int, rate_hz: float = 1000.0,
     [n_lo, n_hi], d uniform in {2..6}, k uniform in [8, 128] nominal
     neighbours, points uniform in [0, 100]^d drawn from the request's seed."""
     u = unit(seed, 10, 4 * count).reshape(count, 4)
-    gaps = -np.log1p(-u[:, 0]) / rate_hz
+    gaps = -_ln(1.0 - u[:, 0]) / rate_hz
     arrivals = np.cumsum(gaps)
-    ns = np.exp(math.log(n_lo) + u[:, 1] * (math.log(n_hi) - math.log(n_lo))).astype(np.int64)
+    l_lo, l_hi = float(_ln(n_lo)), float(_ln(n_hi))
+    ns = _exp(l_lo + u[:, 1] * (l_hi - l_lo)).astype(np.int64)
     ds = 2 + np.minimum((u[:, 2] * 5).astype(np.int64), 4)
     ks = 8.0 + u[:, 3] * 120.0
     out = []

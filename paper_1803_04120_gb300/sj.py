@@ -36,7 +36,7 @@ ABI_FUNCTIONS = (
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
     "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
-    "sj_fp32_margin_diff",
+    "sj_fp32_margin_diff", "sj_fp32_fma_rate",
 )
 
 
@@ -55,7 +55,7 @@ class sj_config(ctypes.Structure):
                 ("serve_mem_bytes", ctypes.c_uint64), ("grab", ctypes.c_int32),
                 ("nbuf", ctypes.c_int32), ("staging", ctypes.c_int32), ("wpb", ctypes.c_int32),
                 ("slots", ctypes.c_int32), ("frame", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("wait_ms", ctypes.c_int32), ("test_stall", ctypes.c_int32)]
 
 
 class sj_index_desc(ctypes.Structure):
@@ -148,6 +148,8 @@ def load(build: bool = True):
                                       ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+            "sj_fp32_fma_rate": (i32, [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin_diff": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]),
             "sj_fp32_margin_frame": (i32, [i32, f64, P, P, i32, ctypes.POINTER(ctypes.c_float),
@@ -226,7 +228,8 @@ class Context:
                  device: int = 0, lookup: int = SJ_LOOKUP_AUTO, profile: bool = False,
                  max_inflight: int = 64, serve_mem_bytes: int = 8 << 30, autotune: bool = True,
                  grab: int = -1, nbuf: int = -1, staging: int = -1, wpb: int = -1,
-                 slots: int = -1, frame: int = SJ_FRAME_AUTO):
+                 slots: int = -1, frame: int = SJ_FRAME_AUTO, wait_ms: int = 0,
+                 test_stall: bool = False):
         lib = load()
         cfg = sj_config()
         lib.sj_config_default(ctypes.byref(cfg))
@@ -235,7 +238,7 @@ class Context:
         cfg.device, cfg.lookup, cfg.profile = device, lookup, int(profile)
         cfg.max_inflight, cfg.serve_mem_bytes, cfg.autotune = max_inflight, serve_mem_bytes, int(autotune)
         cfg.grab, cfg.nbuf, cfg.staging, cfg.wpb, cfg.slots = grab, nbuf, staging, wpb, slots
-        cfg.frame = frame
+        cfg.frame, cfg.wait_ms, cfg.test_stall = frame, int(wait_ms), int(bool(test_stall))
         h = ctypes.c_void_p()
         st = lib.sj_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != SJ_OK:
@@ -357,11 +360,15 @@ class Context:
                     "sj_selfjoin_count")
         return int(cnt.value)
 
-    def sj_selfjoin_stream(self, points, eps: float, callback) -> None:
-        """callback(pairs: np.ndarray (k, 2) uint32) per batch; return True to stop."""
+    def sj_selfjoin_stream(self, points, eps: float, callback, copy: bool = True) -> None:
+        """callback(pairs: np.ndarray (k, 2) uint32) per batch, or callback(k)
+        with the batch's pair count only when copy is False; return True to
+        stop."""
         p, n, d, keep = _points_ptr(points)
 
         def tramp(ptr, k, user):
+            if not copy:
+                return 1 if callback(int(k)) else 0
             arr = np.ctypeslib.as_array(ptr, shape=(int(k) * 2,)).reshape(-1, 2).copy()
             return 1 if callback(arr) else 0
 
@@ -571,6 +578,17 @@ def sj_fp32_margin_diff(d: int, eps: float, fmin, fmax):
     st = lib.sj_fp32_margin_diff(d, float(eps), fmin.ctypes.data, fmax.ctypes.data,
                                  ctypes.byref(lo), ctypes.byref(hi))
     return st, lo.value, hi.value
+
+
+def sj_fp32_fma_rate(device: int = 0, packed: bool = True):
+    """(TFLOP/s, ms) of FP32 fused multiply-add chains on every SM of the
+    device: scalar fma.rn.f32 or packed fma.rn.f32x2 (two FLOPs per lane)."""
+    lib = load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib.sj_fp32_fma_rate(int(device), int(bool(packed)), ctypes.byref(tf), ctypes.byref(ms))
+    if st != SJ_OK:
+        raise SJError(st, "sj_fp32_fma_rate failed")
+    return tf.value, ms.value
 
 
 def sj_shard_bounds(item_block, rank: int, world: int):

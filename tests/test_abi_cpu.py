@@ -89,3 +89,8 @@ def test_reference_arm_prints_its_json_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    # the same workload description as the GPU arm prints
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == json.loads(json.dumps(bench.bench_config(bench.workload())))
+    assert set(line["cpu_baseline"]["build_s"]) == {"2", "3", "4", "5", "6"}

@@ -1,6 +1,6 @@
-"""Many joins in one pass (sj_selfjoin_multi) and the serving loop
-(sj_submit / sj_poll): every job's pair set must equal the oracle's (small
-jobs) or the single-join path's (larger jobs), whatever wave it ran in."""
+"""Many joins in one pass (sj_selfjoin_multi), the serving loop
+(sj_submit / sj_poll) and one join split over ranks: every job's pair set
+must equal the oracle's, whatever wave or shard it ran in."""
 import threading
 
 import numpy as np
@@ -60,7 +60,7 @@ def test_multi_many_waves_and_large_jobs():
         for (pts, eps), r in zip(jobs[:-2], res[:-2]):
             assert np.array_equal(keys(r), oracle_keys(pts, eps))
         for (pts, eps), r in zip(jobs[-2:], res[-2:]):
-            assert np.array_equal(keys(r), keys(ctx.sj_selfjoin(pts, eps)))
+            assert np.array_equal(keys(r), oracle_keys(pts, eps))
 
 
 def test_multi_overflow_rerun_and_standalone():
@@ -112,7 +112,8 @@ def test_multi_sorted_results():
 
 def test_serving_mix_equals_alone():
     """Requests submitted from several threads, admitted in waves on two
-    lanes: each result equals the same join run alone."""
+    lanes: each result equals the oracle's pair set and the same join run
+    alone."""
     jobs = mixed_jobs(5, 48, n_lo=100, n_hi=20000)
     jobs += [(datagen.uniform(400000, 2, seed=11), datagen.eps_for_neighbors(400000, 2, 64))]
     with sj.Context(max_inflight=16, serve_mem_bytes=2 << 30) as ctx:
@@ -139,10 +140,12 @@ def test_serving_mix_equals_alone():
         info = ctx.sj_serve_stats()
         assert info["completed"] == len(jobs) and info["queued"] == 0 and info["inflight"] == 0
         assert info["graph_launches"] >= 1 and info["lanes"] == 2
-        # the same requests alone
+        # the oracle, and the same requests alone
         for k, (pts, eps) in enumerate(jobs):
+            want = oracle_keys(pts, eps)
+            assert np.array_equal(keys(results[k]), want), k
             alone = ctx.sj_selfjoin(pts, eps)
-            assert np.array_equal(keys(results[k]), keys(alone)), k
+            assert np.array_equal(keys(alone), want), k
         # a consumed ticket is gone
         with pytest.raises(sj.SJError) as ei:
             ctx.sj_poll(tickets[0])
@@ -207,7 +210,7 @@ def test_tuner_keeps_results():
 def test_shards_partition_the_join(world):
     """One join split over `world` ranks (run one after another on this GPU;
     no rank waits on another): the shards are disjoint and their union is
-    the full pair set."""
+    the oracle's pair set."""
     torch = pytest.importorskip("torch")
     cases = [(datagen.uniform(60000, 3, seed=41), 2.5),
              (datagen.clustered(80000, 2, seed=42), 0.3),
@@ -215,9 +218,7 @@ def test_shards_partition_the_join(world):
     with sj.Context() as ctx:
         for pts_np, eps in cases:
             pts = torch.from_numpy(pts_np).cuda()
-            n_full = ctx.sj_selfjoin_count(pts, eps)
-            full = torch.empty((n_full, 2), dtype=torch.int32, device="cuda")
-            ctx.sj_selfjoin_device(pts, eps, full)
+            want = oracle_keys(pts_np, eps)
             parts, total = [], 0
             for r in range(world):
                 cnt = ctx.sj_selfjoin_shard_device(pts, eps, r, world, None, raise_overflow=False)
@@ -225,9 +226,9 @@ def test_shards_partition_the_join(world):
                 assert ctx.sj_selfjoin_shard_device(pts, eps, r, world, out) == cnt
                 parts.append(keys(out[:cnt].cpu().numpy()))
                 total += cnt
-            assert total == n_full
+            assert total == want.size
             got = np.sort(np.concatenate(parts))
-            assert np.array_equal(got, keys(full.cpu().numpy()))
+            assert np.array_equal(got, want)
         with pytest.raises(sj.SJError) as ei:
             ctx.sj_selfjoin_shard_device(pts, eps, world, world, None)
         assert ei.value.status == sj.SJ_EINVAL

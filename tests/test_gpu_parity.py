@@ -293,73 +293,6 @@ def test_unicomp_halves_evaluations():
     assert 2 * ea == eb - n
 
 
-# ------------------------------------------------------------------ full size
-
-@pytest.mark.slow
-@pytest.mark.parametrize("d", [2, 3, 4, 5, 6])
-def test_config2_full_size_sampled(d):
-    torch = pytest.importorskip("torch")
-    cfg = datagen.config2(d)
-    pts = datagen.make_points(cfg)
-    n, eps = cfg["n"], cfg["eps"]
-    with sj.Context() as ctx:
-        d_pts = torch.from_numpy(pts).cuda()
-        cnt = ctx.sj_selfjoin_count(d_pts, eps)
-        out = torch.empty((cnt, 2), dtype=torch.int32, device="cuda")
-        assert ctx.sj_selfjoin_device(d_pts, eps, out) == cnt
-    i = out[:, 0].to(torch.int64) & 0xffffffff
-    j = out[:, 1].to(torch.int64) & 0xffffffff
-    # self pairs, symmetry, no duplicates
-    assert int((i == j).sum()) == n
-    k1 = torch.sort((i << 32) | j).values
-    k2 = torch.sort((j << 32) | i).values
-    assert torch.equal(k1, k2)
-    assert int((k1[1:] == k1[:-1]).sum()) == 0
-    # sampled queries against the oracle, neighbour list by neighbour list
-    rng = np.random.default_rng(d)
-    q = np.sort(rng.choice(n, size=300, replace=False)).astype(np.uint32)
-    offs, ids = orc.grid_neighbors(pts, eps, q)
-    keys = k1.cpu().numpy().view(np.uint64)
-    for t, qq in enumerate(q):
-        lo = np.searchsorted(keys, np.uint64(int(qq) << 32))
-        hi = np.searchsorted(keys, np.uint64((int(qq) + 1) << 32))
-        got = (keys[lo:hi] & np.uint64(0xffffffff)).astype(np.uint32)
-        assert np.array_equal(got, ids[offs[t]:offs[t + 1]]), (d, int(qq))
-    # degree sum statistics: realised mean within 10% of 64 (boundary effects)
-    mean = (cnt - n) / n
-    assert 0.7 * 64 < mean < 1.02 * 64
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("d", [2])
-def test_config3_full_size_streamed_digest(d):
-    """10,000,000 points, 128 mean neighbours, result device buffers capped at
-    2 GB: the pairs stream to the host in batches (Section V-A); count,
-    per-point degree and the order-independent pair hash must equal the
-    oracle's."""
-    cfg = datagen.config3(d)
-    pts = datagen.make_points(cfg)
-    n, eps = cfg["n"], cfg["eps"]
-    deg = np.zeros(n, dtype=np.int64)
-    acc = {"count": 0, "hash": 0}
-
-    def cb(pairs):
-        keys = (pairs[:, 0].astype(np.uint64) << np.uint64(32)) | pairs[:, 1].astype(np.uint64)
-        acc["hash"] = (acc["hash"] + orc.pair_hash(keys)) % (1 << 64)
-        acc["count"] += len(pairs)
-        deg[:] += np.bincount(pairs[:, 0], minlength=n)
-        return False
-
-    with sj.Context(out_cap_bytes=2 << 30) as ctx:
-        ctx.sj_selfjoin_stream(pts, eps, cb)
-        st = ctx.sj_last_stats()
-    assert st["batches"] >= 6
-    o_count, o_deg, o_hash = orc.grid_digest(pts, eps)
-    assert acc["count"] == o_count == st["pairs"]
-    assert acc["hash"] == o_hash
-    assert np.array_equal(deg, o_deg.astype(np.int64))
-
-
 def test_wide_grid_uses_the_cell_frame_and_grid_frame_falls_back():
     """A range of 5e6 against eps = 1: the grid frame has no usable FP32
     margin and computes in FP64 (no rechecks); the automatic choice takes the
