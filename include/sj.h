@@ -398,7 +398,8 @@ SJ_API void sj_result_free(sj_result *r);                     /* NULL is ignored
  * is one of them.  The ranks' outputs are disjoint and their union is the
  * full result; summing the counts (one all-reduce) is the only exchange.
  * Shards are contiguous ranges of work items (cell, block of 32 points)
- * cut at cell starts, balanced by query blocks (see sj_shard_bounds).
+ * cut at cell starts, balanced by the estimated search cost of the items
+ * (see sj_shard_bounds_cost; the costs are computed on the device).
  * Arguments and errors as sj_selfjoin_device, plus SJ_EINVAL unless
  * 0 <= rank < world. */
 SJ_API sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, int d,
@@ -411,6 +412,18 @@ SJ_API sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64
  * forward to the next cell start (or n).  The ranks' ranges tile [0, n). */
 SJ_API sj_status sj_shard_bounds(const uint32_t *item_block, uint64_t n_items, int rank,
                                  int world, uint64_t *lo, uint64_t *hi);
+
+/* The cost-balanced shard rule of sj_selfjoin_shard_device on host arrays:
+ * item_cost[k] is the estimated search cost of work item k (the device
+ * uses K (q + 20) + 2000 with K the item's candidate points and q its query
+ * points).  With C the total cost, the bound between ranks r - 1 and r is
+ * the cell start whose exclusive cost prefix is nearest to C r / w (of the
+ * two starts around the first item whose prefix reaches C r / w; the later
+ * on a tie).  The ranks' ranges tile [0, n), and a rank's cost exceeds
+ * C / w by at most the cost of one cell. */
+SJ_API sj_status sj_shard_bounds_cost(const uint32_t *item_block, const uint64_t *item_cost,
+                                      uint64_t n_items, int rank, int world, uint64_t *lo,
+                                      uint64_t *hi);
 
 /* ------------------------------------------------------------------ */
 /* Many joins at once.                                                */

@@ -272,20 +272,53 @@ sj_status join_once(Error &err, sj_ctx *ctx, const Index &ix, uint32_t ib, uint3
     return SJ_OK;
 }
 
-// Pair-count estimate from a systematic sample of the work items.
-sj_status estimate_pairs(Error &err, sj_ctx *ctx, const Index &ix, cudaStream_t s,
-                         uint64_t *est) {
+// Pair-count estimates of S equal segments of the work items, each from a
+// systematic sample (every stride-th item, about 16384 sampled items in
+// all): the S count-only launches run back to back on s, each into its
+// own counters, with one read-back at the end.  Pair density varies along
+// the cell order (cells at the boundary of the data have fewer
+// neighbours), so the batches are later cut at equal estimated pairs, not
+// at equal item counts.
+sj_status estimate_segments(Error &err, sj_ctx *ctx, const Index &ix, cudaStream_t s, uint32_t S,
+                            std::vector<double> &seg) {
     const uint32_t ni = ix.n_items;
-    uint32_t stride = ni > 16384 ? ni / 16384 : 1;
-    unsigned long long r[3];
-    SJ_TRY(join_once(err, ctx, ix, 0, ni, stride, nullptr, 0, 1, s, r));
-    if (stride == 1) {
-        *est = r[0];
-    } else {
-        const uint64_t sampled = (ni + stride - 1) / stride;
-        *est = (uint64_t)((double)r[0] * (double)ni / (double)sampled);
-    }
-    return SJ_OK;
+    const uint32_t stride = ni > 16384 ? ni / 16384 : 1;
+    seg.assign(S, 0.0);
+    DevBuf ctr;
+    SJ_TRY(dev_alloc(err, ctr, (size_t)S * 4 * sizeof(unsigned long long), s));
+    unsigned long long *c = static_cast<unsigned long long *>(ctr.p);
+    unsigned long long *m = misc_dev(ctx);
+    auto run = [&]() -> sj_status {
+        SJ_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)S * 4 * sizeof(unsigned long long), s));
+        SJ_CUDA_TRY(cudaMemsetAsync(m, 0, kMiscWords * sizeof(unsigned long long), s));
+        JoinLaunch l = launch_cfg(ctx);
+        l.item_stride = stride;
+        for (uint32_t q = 0; q < S; ++q) {
+            const uint32_t lo = (uint32_t)((uint64_t)ni * q / S), hi = (uint32_t)((uint64_t)ni * (q + 1) / S);
+            if (hi <= lo) continue;
+            SJ_TRY(launch_join(err, ix, l, lo, hi, nullptr, 0, c + 4 * q,
+                               reinterpret_cast<uint32_t *>(m + kMiscWork),
+                               reinterpret_cast<uint32_t *>(m + kMiscError), 1, s, nullptr, nullptr));
+        }
+        std::vector<unsigned long long> h((size_t)S * 4);
+        SJ_CUDA_TRY(cudaMemcpyAsync(h.data(), c, h.size() * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s));
+        SJ_CUDA_TRY(cudaMemcpyAsync(ctx->h_misc, m, kMiscWords * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s));
+        SJ_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((uint32_t)ctx->h_misc[kMiscError] & kErrTimeout)
+            return fail(err, SJ_ETIMEOUT, "a bounded device wait expired in the join kernel");
+        for (uint32_t q = 0; q < S; ++q) {
+            const uint32_t lo = (uint32_t)((uint64_t)ni * q / S), hi = (uint32_t)((uint64_t)ni * (q + 1) / S);
+            if (hi <= lo) continue;
+            const uint64_t sampled = (hi - lo + stride - 1) / stride;
+            seg[q] = (double)h[4 * q] * (double)(hi - lo) / (double)sampled;
+        }
+        return SJ_OK;
+    };
+    const sj_status st = run();
+    dev_free(ctr, s);
+    return st;
 }
 
 // Where the batches of a host-output join go.
@@ -320,18 +353,53 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     cudaStream_t s = ctx->s_main, sc = ctx->s_copy;
     SJ_TRY(read_counts(err, ix, s));
     const uint32_t ni = ix.n_items;
-    double t_est = now_ms();
-    uint64_t est = 0;
-    SJ_TRY(estimate_pairs(err, ctx, ix, s, &est));
-    (void)t_est;
-    ctx->stats.estimate = est;
     const uint64_t cap_total = ctx->cfg.out_cap_bytes ? ctx->cfg.out_cap_bytes : (2ull << 30);
     const uint64_t bufcap_max = std::max<uint64_t>(cap_total / 16, 4096);  // pairs per buffer
+    const uint64_t min_nb = (uint64_t)std::max(1, ctx->cfg.min_batches);
+    auto batches_for = [&](uint64_t e) {
+        const uint64_t padded = e + e / 8 + 4096;
+        uint64_t b = std::max<uint64_t>((padded + bufcap_max - 1) / bufcap_max, min_nb);
+        return std::min<uint64_t>(b, ni ? ni : 1);
+    };
+    // one sampled estimate; when the result needs more than the minimum
+    // number of batches, a second one by segments (enough to follow the
+    // density along the cell order, each still sampling about 256 items or
+    // more) to cut the batches at equal estimated pairs
+    std::vector<double> seg;
+    SJ_TRY(estimate_segments(err, ctx, ix, s, 1, seg));
+    uint32_t S = 1;
+    if (batches_for((uint64_t)seg[0]) > min_nb) {
+        S = std::max<uint32_t>(1, std::min<uint32_t>(64, ni / 4096));
+        if (S > 1) SJ_TRY(estimate_segments(err, ctx, ix, s, S, seg));
+    }
+    double est_d = 0;
+    for (double v : seg) est_d += v;
+    const uint64_t est = (uint64_t)est_d;
+    ctx->stats.estimate = est;
     const uint64_t padded = est + est / 8 + 4096;
-    uint64_t nb = (padded + bufcap_max - 1) / bufcap_max;
-    nb = std::max<uint64_t>(nb, (uint64_t)std::max(1, ctx->cfg.min_batches));
-    nb = std::min<uint64_t>(nb, ni ? ni : 1);
+    const uint64_t nb = batches_for(est);
     uint64_t bufcap = std::min<uint64_t>(bufcap_max, padded / nb + padded / (4 * nb) + 65536);
+    // batch b covers items [cut[b], cut[b+1]): equal estimated pairs, the
+    // cumulative estimate interpolated linearly inside a segment
+    std::vector<uint32_t> cut(nb + 1, 0);
+    cut[nb] = ni;
+    {
+        double acc = 0;
+        uint32_t q = 0;
+        for (uint64_t b = 1; b < nb; ++b) {
+            const double target = est_d * (double)b / (double)nb;
+            while (q < S && acc + seg[q] < target) acc += seg[q++];
+            uint32_t x;
+            if (q >= S) {
+                x = ni;
+            } else {
+                const double lo = (double)ni * q / S, hi = (double)ni * (q + 1) / S;
+                const double f = seg[q] > 0 ? (target - acc) / seg[q] : 0.0;
+                x = (uint32_t)std::min<double>(hi, lo + f * (hi - lo));
+            }
+            cut[b] = std::max(cut[b - 1], std::min(x, ni));
+        }
+    }
 
     DevBuf dbuf[2];
     SJ_TRY(dev_alloc(err, dbuf[0], bufcap * 8, s));
@@ -377,7 +445,7 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     std::vector<std::pair<uint32_t, uint32_t>> retry;
     std::vector<uint64_t> cb_pending;   // batch whose staged pairs await the callback
     uint64_t cb_count[2] = {0, 0};
-    auto item_lo = [&](uint64_t b) { return (uint32_t)((uint64_t)ni * b / nb); };
+    auto item_lo = [&](uint64_t b) { return cut[b]; };
     uint64_t batches_done = 0;
 
     auto launch_batch = [&](uint64_t b) -> sj_status {
@@ -795,7 +863,7 @@ sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, i
     st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix);
     double t1 = now_ms();
     uint32_t lo = 0, hi = 0;
-    if (st == SJ_OK) st = shard_items(sc.err, ix, rank, world, s, &lo, &hi);
+    if (st == SJ_OK) st = shard_items(sc.err, ix, ctx->cfg.unicomp != 0, rank, world, s, &lo, &hi);
     if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, d_pairs, cap_pairs, count, s, 0, lo, hi);
     free_index(ix, s);
     ctx->stats.ms_index = t1 - t0;

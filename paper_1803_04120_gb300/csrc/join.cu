@@ -26,10 +26,13 @@
 //        as one add and d fused multiply-adds on packed f32x2 pairs (two
 //        candidates per instruction).  s is compared with the proven margin
 //        [lo32, hi32] computed on the host (margin.cu): per candidate slot
-//        each lane keeps a 32-bit mask of the queries within hi32.  Hits
-//        above lo32 (the band) are recomputed with the exact FP64
-//        predicate, in a warp-uniform branch around a non-inlined function
-//        so that the slow FP64 pipe of GB300 sees only the real rechecks.
+//        each lane keeps a 32-bit mask of the queries within hi32, and the
+//        largest value among its hits.  Only when that maximum exceeds
+//        lo32 (a hit in the band: a few in 1e4) are the chunk's hits
+//        re-evaluated to find the band ones, which the exact FP64
+//        predicate decides, in a warp-uniform branch around a non-inlined
+//        function so that the slow FP64 pipe of GB300 sees only the real
+//        rechecks.
 //        FP64 mode: the exact predicate for every candidate.
 //   5. emits: FP32 mode under UNICOMP: the self-pair of every query once
 //      per item, then each hit (p, q) gives (p, q) and (q, p), and in the
@@ -566,18 +569,23 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
             st.fill += nq;
         }
         // 1. comparison: bit qi of m[s] = candidate slot s is within hi32 of
-        //    query qi; at low d also the band bits (above lo32) on the way
+        //    query qi.  mx keeps the largest value of a hit, so that one
+        //    predicated max per comparison tells whether any hit of the
+        //    lane lies in the band above lo32 (rare: a few in 1e4 hits)
         uint32_t m[CPL], b[CPL];
 #pragma unroll
         for (int s = 0; s < CPL; ++s) m[s] = b[s] = 0u;
+        float mx = -INFINITY;
         for (uint32_t qi = 0; qi < nq; ++qi) {
             float sv[CPL];
             eval_query<D, NP>(qbase + (size_t)qi * a.qrs, z, qq2, sv);
             const uint32_t bit = 1u << qi;
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
-                if (sv[s] <= hi32) m[s] |= bit;
-                if (D <= 3 && sv[s] > lo32) b[s] |= bit;
+                if (sv[s] <= hi32) {
+                    m[s] |= bit;
+                    mx = fmaxf(mx, sv[s]);
+                }
             }
         }
         uint32_t any = 0;
@@ -597,8 +605,9 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
             }
         }
         // 3. band: values above lo32 are decided by the exact FP64
-        //    predicate (at high d the rare hits are re-evaluated to find them)
-        if (D > 3) {
+        //    predicate.  Only in a chunk where some hit lies in the band are
+        //    the hits re-evaluated to find which ones
+        if (__any_sync(0xffffffffu, mx > lo32)) {
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
                 uint32_t w = m[s];

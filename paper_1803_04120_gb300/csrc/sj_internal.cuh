@@ -269,9 +269,10 @@ sj_status block_shape(Error &err, const void *fn, int sm_warp, int force_wpb, in
 // predicate; *d_counter accumulates the member count.
 sj_status brute_join(Error &err, const double *d_pts, uint64_t n, int d, double eps, uint2 *out,
                      uint64_t cap, unsigned long long *d_counter, cudaStream_t s);
-// Work-item range [lo, hi) of shard `rank` of `world` (shard.cu): the
-// nominal split of the items moved forward to cell starts.  Synchronises s.
-sj_status shard_items(Error &err, const Index &ix, int rank, int world, cudaStream_t s,
+// Work-item range [lo, hi) of shard `rank` of `world` (shard.cu): equal
+// shares of the estimated search cost, each bound moved forward to a cell
+// start.  Synchronises s.
+sj_status shard_items(Error &err, const Index &ix, bool uni, int rank, int world, cudaStream_t s,
                       uint32_t *lo, uint32_t *hi);
 // Launch tuner (tune.cu): on a miss times sampled count-only launches of ix
 // and stores the fastest (grab, ring depth, warps per block) for the key

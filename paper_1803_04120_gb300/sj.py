@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "sj_selfjoin_count", "sj_selfjoin_stream", "sj_result_count", "sj_result_pairs",
     "sj_result_free", "sj_last_stats", "sj_profile_read", "sj_submit", "sj_poll",
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
-    "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds",
+    "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds", "sj_shard_bounds_cost",
     "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
     "sj_fp32_margin_diff", "sj_fp32_fma_rate",
 )
@@ -161,6 +161,8 @@ def load(build: bool = True):
             "sj_serve_stats": (i32, [P, ctypes.POINTER(sj_serve_info)]),
             "sj_selfjoin_shard_device": (i32, [P, P, u64, i32, f64, i32, i32, P, u64,
                                                ctypes.POINTER(ctypes.c_uint64), P]),
+            "sj_shard_bounds_cost": (i32, [P, P, u64, i32, i32, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_uint64)]),
             "sj_shard_bounds": (i32, [P, u64, i32, i32, ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_uint64)]),
             "sj_selfjoin_bruteforce_device": (i32, [P, P, u64, i32, f64, P, u64,
@@ -600,6 +602,23 @@ def sj_shard_bounds(item_block, rank: int, world: int):
                              int(world), ctypes.byref(lo), ctypes.byref(hi))
     if st != SJ_OK:
         raise SJError(st, "sj_shard_bounds")
+    return int(lo.value), int(hi.value)
+
+
+def sj_shard_bounds_cost(item_block, item_cost, rank: int, world: int):
+    """(lo, hi) work-item range of a shard balanced by per-item costs, from
+    host arrays (no device)."""
+    lib = load()
+    a = np.ascontiguousarray(item_block, dtype=np.uint32)
+    c = np.ascontiguousarray(item_cost, dtype=np.uint64)
+    if a.shape != c.shape:
+        raise ValueError("item_block and item_cost differ in length")
+    lo, hi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = lib.sj_shard_bounds_cost(ctypes.c_void_p(a.ctypes.data) if a.size else None,
+                                  ctypes.c_void_p(c.ctypes.data) if c.size else None, a.size,
+                                  int(rank), int(world), ctypes.byref(lo), ctypes.byref(hi))
+    if st != SJ_OK:
+        raise SJError(st, "sj_shard_bounds_cost")
     return int(lo.value), int(hi.value)
 
 
