@@ -528,11 +528,14 @@ typedef struct {
     int32_t inflight;          /* admitted requests now */
     int32_t lanes;             /* waves that may run at the same time */
     int32_t max_concurrent_waves; /* most waves seen running at once */
-    int32_t reserved;
+    int32_t tuned_keys;        /* tuner keys (d, precision, points-per-cell
+                                  bucket) the lanes tuned after a wave */
     /* host wall time summed over the lanes' waves (ms): points to the device
      * and the bounds pass, the graph replay (index build + join), the result
      * copies to the host */
     double ms_bounds, ms_graph, ms_output;
+    uint64_t tuned_jobs;       /* requests joined with the tuner's launch
+                                  parameters (autotune = 1) */
 } sj_serve_info;
 
 SJ_API sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out);

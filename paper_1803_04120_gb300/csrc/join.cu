@@ -216,6 +216,8 @@ __device__ __forceinline__ WarpSmem carve(unsigned char *base, const JoinArgs &a
 struct Pipe {
     uint32_t grab_pos, grab_end;   // work-cursor positions taken by this warp
     uint32_t issued, consumed;     // chunks
+    uint32_t p_slot, c_slot;       // ring slots of the next issue / consume
+    uint32_t c_phase;              // mbarrier phase parity of the next consume
     uint32_t prod_seq, cons_seq;   // item sequence numbers (slot = seq & smask)
     uint32_t p_chunk, c_chunk;
     uint32_t rcur;                 // producer's range cursor
@@ -312,10 +314,11 @@ __device__ __forceinline__ void load_candidates(const unsigned char *buf, int rs
 }
 
 // s32 for one staged query record against this lane's candidates:
-// fl(|z_q|^2 + |z_p|^2) then d fused multiply-adds with m_j = -2 z_p,j.
-template <int D, int NP>
+// fl(|z_q|^2 + |z_p|^2) then d fused multiply-adds with m_j = -2 z_p,j;
+// with SHIFT, fl(s32 + shift) (a packed pair added to both values).
+template <int D, int NP, bool SHIFT = false>
 __device__ __forceinline__ void eval_query(const float *qd, const f2_t (*z)[D], const f2_t *qq2,
-                                           float *sv) {
+                                           float *sv, f2_t shift = 0ull) {
     // record: m_0 .. m_{d-1}, pp, id (16-byte loads, broadcast to the warp)
     constexpr int V = (D + 2 + 3) / 4;
     float r[4 * V];
@@ -339,7 +342,10 @@ __device__ __forceinline__ void eval_query(const float *qd, const f2_t (*z)[D], 
         for (int cp = 0; cp < NP; ++cp) acc[cp] = f2_fma(mj, z[cp][j], acc[cp]);
     }
 #pragma unroll
-    for (int cp = 0; cp < NP; ++cp) f2_unpack(acc[cp], sv[2 * cp], sv[2 * cp + 1]);
+    for (int cp = 0; cp < NP; ++cp) {
+        if (SHIFT) acc[cp] = f2_add(acc[cp], shift);
+        f2_unpack(acc[cp], sv[2 * cp], sv[2 * cp + 1]);
+    }
 }
 
 // Takes the next work item for this warp; false when none is left.
@@ -451,27 +457,30 @@ __device__ __forceinline__ void issue_chunk(const WarpSmem &ws, int sl, uint32_t
     const uint32_t k0 = ch * CB;
     const uint32_t k1 = min(K, k0 + CB);
     unsigned char *buf = ws.ring + (size_t)r * sm_chunk;
-    while (rcur < nranges && rt[rcur].y <= k0) ++rcur;
     // earlier generic-proxy reads of this buffer precede the async-proxy writes
     fence_proxy_async_smem();
     if (lane == 0) mbar_arrive_expect_tx(&ws.bar[r], (k1 - k0) * rsb);
     __syncwarp();
-    for (uint32_t r0 = rcur; r0 < nranges; r0 += 32) {
+    // rcur is the first range that ends after k0 (ranges end at increasing
+    // flat positions); lane l looks at range rcur + l, and the ranges that
+    // end by k1 are skipped for the next chunk with one ballot
+    for (uint32_t r0 = rcur;; r0 += 32) {
         const uint32_t rr = r0 + lane;
-        bool starts_before = false;
-        if (rr < nranges) {
-            const uint2 rg = rt[rr];
-            const uint32_t fs = (rr == 0) ? 0u : rt[rr - 1].y;
-            const uint32_t fe = rg.y;
-            starts_before = fs < k1;
-            if (starts_before && fe > k0) {
-                const uint32_t lo = fs > k0 ? fs : k0;
-                const uint32_t hi = fe < k1 ? fe : k1;
-                bulk_g2s(buf + (size_t)(lo - k0) * rsb, rec + (size_t)(rg.x + (lo - fs)) * rsb,
-                         (hi - lo) * rsb, &ws.bar[r]);
-            }
+        const bool valid = rr < nranges;
+        const uint2 rg = valid ? rt[rr] : make_uint2(0u, 0xffffffffu);
+        uint32_t fs = __shfl_up_sync(0xffffffffu, rg.y, 1);
+        if (lane == 0) fs = rr == 0 ? 0u : rt[rr - 1].y;
+        const uint32_t fe = rg.y;
+        if (valid && fs < k1 && fe > k0) {
+            const uint32_t lo = fs > k0 ? fs : k0;
+            const uint32_t hi = fe < k1 ? fe : k1;
+            bulk_g2s(buf + (size_t)(lo - k0) * rsb, rec + (size_t)(rg.x + (lo - fs)) * rsb,
+                     (hi - lo) * rsb, &ws.bar[r]);
         }
-        if (__ballot_sync(0xffffffffu, starts_before) != 0xffffffffu) break;
+        const unsigned done = __ballot_sync(0xffffffffu, valid && fe <= k1);
+        rcur = r0 + __popc(done);
+        // all 32 ranges end by k1: the chunk may cover more, look at the next 32
+        if (done != 0xffffffffu) break;
     }
 }
 
@@ -518,18 +527,6 @@ __device__ __forceinline__ void put_hits(uint32_t (&m)[CPL], const uint32_t (&ci
     }
 }
 
-// Clears up to c hits of this lane, in the order put_hits takes them.
-template <int CPL>
-__device__ __forceinline__ void drop_hits(uint32_t (&m)[CPL], uint32_t c) {
-#pragma unroll
-    for (int s = 0; s < CPL; ++s) {
-        while (c && m[s]) {
-            m[s] &= m[s] - 1;
-            --c;
-        }
-    }
-}
-
 // Compares chunk `ch` (in ring slot r) of the item in slot `sl` with the
 // item's queries and stages the pairs found.  FR: the FP32 record frame,
 // 0 grid, 1 cell, 2 read from the arguments at run time (multi-join).
@@ -569,23 +566,30 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
             st.fill += nq;
         }
         // 1. comparison: bit qi of m[s] = candidate slot s is within hi32 of
-        //    query qi.  mx keeps the largest value of a hit, so that one
-        //    predicated max per comparison tells whether any hit of the
-        //    lane lies in the band above lo32 (rare: a few in 1e4 hits)
+        //    query qi.  Each value is compared through dv = s32 - h with h
+        //    the float just above hi32 (two packed subtractions per query):
+        //    the sign of an IEEE difference is exact, so s32 <= hi32 iff dv
+        //    is negative, and one funnel shift moves that sign bit into the
+        //    mask (queries taken from the last to the first, so that query
+        //    qi ends at bit qi).  Near the threshold dv is exact (Sterbenz),
+        //    so a hit lies in the band above lo32 iff dv > lo32 - h, which
+        //    for negative floats is an integer comparison of their bits: mn,
+        //    the smallest bit pattern, tells whether the lane has such a hit
+        //    (rare: a few in 1e4 hits).  Non-hits have non-negative dv and
+        //    bit patterns above every hit's.
         uint32_t m[CPL], b[CPL];
 #pragma unroll
         for (int s = 0; s < CPL; ++s) m[s] = b[s] = 0u;
-        float mx = -INFINITY;
-        for (uint32_t qi = 0; qi < nq; ++qi) {
+        const float h1 = __int_as_float(__float_as_int(hi32) + 1);
+        const f2_t mh = f2_pack(-h1, -h1);
+        int mn = 0x7fffffff;
+        for (int qi = (int)nq - 1; qi >= 0; --qi) {
             float sv[CPL];
-            eval_query<D, NP>(qbase + (size_t)qi * a.qrs, z, qq2, sv);
-            const uint32_t bit = 1u << qi;
+            eval_query<D, NP, true>(qbase + (size_t)qi * a.qrs, z, qq2, sv, mh);
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
-                if (sv[s] <= hi32) {
-                    m[s] |= bit;
-                    mx = fmaxf(mx, sv[s]);
-                }
+                m[s] = __funnelshift_l(__float_as_uint(sv[s]), m[s], 1);
+                mn = min(mn, __float_as_int(sv[s]));
             }
         }
         uint32_t any = 0;
@@ -607,7 +611,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         // 3. band: values above lo32 are decided by the exact FP64
         //    predicate.  Only in a chunk where some hit lies in the band are
         //    the hits re-evaluated to find which ones
-        if (__any_sync(0xffffffffu, mx > lo32)) {
+        if (__any_sync(0xffffffffu, mn < __float_as_int(lo32 - h1))) {
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
                 uint32_t w = m[s];
@@ -640,13 +644,14 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                 }
             }
         }
-        // 4. emission.  The hits go out in (t, lane) order: the t-th hit of
-        //    every lane that has one goes to consecutive slots, so one store
-        //    instruction writes consecutive words (no shared-memory bank
-        //    conflicts, coalesced global stores); the order of pairs in the
-        //    output is free.  A chunk with many pairs reserves its output
-        //    once and writes it straight to global memory; a chunk with few
-        //    is staged, so the same-address reservations stay rare.
+        // 4. emission (the order of pairs in the output is free).  A chunk
+        //    with many pairs reserves its output once and writes it straight
+        //    to global memory in (t, lane) order: the t-th hit of every lane
+        //    that has one goes to consecutive slots, so each store
+        //    instruction writes consecutive words (coalesced).  A chunk with
+        //    few pairs is staged in shared memory, each lane at its prefix
+        //    position, so that the same-address reservations stay rare (one
+        //    per flush of the staging area).
         constexpr uint32_t kPP = UNI ? 2u : 1u;
         uint32_t left = 0;
 #pragma unroll
@@ -663,18 +668,32 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                 put_hits<CPL, UNI, true>(m, cid, qid_l, left, base, a.out, a.cap, lane);
             return;
         }
-        const uint32_t kPer = (uint32_t)a.eb / (32u * kPP);
-        while (__any_sync(0xffffffffu, left)) {
-            const uint32_t c = left < kPer ? left : kPer;
-            const uint32_t total = __reduce_add_sync(0xffffffffu, c) * kPP;
-            if (st.fill + total > (uint32_t)a.eb) flush(st, ws, a, lane);
-            if (!a.count_only)
-                put_hits<CPL, UNI, false>(m, cid, qid_l, c, st.fill, ws.emit, 0, lane);
-            else
-                drop_hits<CPL>(m, c);
-            left -= c;
-            st.fill += total;
+        // fewer than kDirectPairs pairs: staged, each lane writing its own
+        // hits at its exclusive prefix position (one warp scan)
+        uint32_t incl = left;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
+        const uint32_t total = hits * kPP;
+        if (st.fill + total > (uint32_t)a.eb) flush(st, ws, a, lane);
+        if (!a.count_only) {
+            uint32_t pos = st.fill + kPP * (incl - left);
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                uint32_t w = m[s];
+                while (w) {
+                    const uint32_t q = __ffs(w) - 1;
+                    w &= w - 1;
+                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + D + 1]);
+                    ws.emit[pos] = make_uint2(qid, cid[s]);
+                    if (UNI) ws.emit[pos + 1] = make_uint2(cid[s], qid);
+                    pos += kPP;
+                }
+            }
+        }
+        st.fill += total;
     } else {
         double y[CPL][D];
         uint32_t cid[CPL];
@@ -757,6 +776,7 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     Pipe st;
     st.grab_pos = st.grab_end = 0;
     st.issued = st.consumed = 0;
+    st.p_slot = st.c_slot = st.c_phase = 0;
     st.prod_seq = st.cons_seq = 0;
     st.p_chunk = st.c_chunk = 0;
     st.rcur = 0;
@@ -801,15 +821,16 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                 // test hook: one warp never issues its first chunk, so its
                 // wait for that chunk runs out (no copy is in flight for it)
                 if (!(a.stall && st.issued == 0 && blockIdx.x == 0 && warp == 0))
-                    issue_chunk<CB>(ws, ps, st.p_chunk, st.issued % nbuf, st.rcur, rec, rsb, lane,
+                    issue_chunk<CB>(ws, ps, st.p_chunk, (int)st.p_slot, st.rcur, rec, rsb, lane,
                                     a.sm_chunk);
                 ++st.issued;
                 ++st.p_chunk;
+                st.p_slot = st.p_slot + 1 == nbuf ? 0u : st.p_slot + 1;
             }
             if (st.consumed == st.issued) break;
             // consumer
-            const int r = st.consumed % nbuf;
-            if (!mbar_wait_bounded(&ws.bar[r], (st.consumed / nbuf) & 1u, a.timeout_ns)) {
+            const int r = (int)st.c_slot;
+            if (!mbar_wait_bounded(&ws.bar[r], st.c_phase, a.timeout_ns)) {
                 failed = true;
                 if (lane == 0) atomicOr(a.error, kErrTimeout);
                 // let the other copies in flight land before leaving
@@ -821,6 +842,10 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                                            rechecks);
             ++st.consumed;
             ++st.c_chunk;
+            if (++st.c_slot == nbuf) {
+                st.c_slot = 0;
+                st.c_phase ^= 1u;
+            }
             if (st.c_chunk == ws.hdr[st.cons_seq & smask].nchunks) {
                 ++st.cons_seq;
                 st.c_chunk = 0;

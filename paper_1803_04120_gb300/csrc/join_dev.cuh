@@ -46,7 +46,7 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
 //   Stage k is active when c_k is odd (Section V-B, generalised to n
 //   dimensions).  Full search: t in [0, 3^(d-1)) enumerates all rows.
 template <int D, bool UNI>
-__device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, const JoinArgs &a,
+__device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, uint32_t occ, const JoinArgs &a,
                                        int32_t &xlo, int32_t &xhi, int32_t *b) {
     const uint32_t e = __ldg(&a.tmpl[t]);
     const uint32_t gate = (e >> 2) & 15u;
@@ -60,11 +60,8 @@ __device__ __forceinline__ bool row_of(int t, const int32_t *c, uint32_t odd, co
     if (xhi > a.ng[0] - 1) xhi = a.ng[0] - 1;
     if (xlo > xhi) return false;
 #pragma unroll
-    for (int j = 1; j < D; ++j) {
-        if (b[j] < 0 || b[j] >= a.ng[j]) return false;
-        const uint32_t w = a.M[(uint64_t)j * a.mwords + ((uint32_t)b[j] >> 5)];
-        if (!((w >> (b[j] & 31)) & 1u)) return false;   // M_j: no point in that slab
-    }
+    for (int j = 1; j < D; ++j)
+        if (!((occ >> (3 * (j - 1) + ((e >> (6 + 2 * (j - 1))) & 3u))) & 1u)) return false;
     return true;
 }
 
@@ -147,13 +144,31 @@ __device__ __forceinline__ void build_ranges(const int32_t *c, uint32_t odd, con
                                              uint32_t &nranges, uint32_t &K) {
     nranges = 0;
     K = 0;
+    // slab occupancy c_j - 1, c_j, c_j + 1 of dimensions 2..D (in the grid
+    // and marked in M_j): bit 3 (j - 1) + offset + 1, one lane per bit
+    uint32_t occ;
+    {
+        bool ok = false;
+        if (lane < 3 * (D - 1)) {
+            const int j = 1 + lane / 3;
+            int32_t cj = 0;
+#pragma unroll
+            for (int jj = 1; jj < D; ++jj) if (jj == j) cj = c[jj];
+            const int32_t bj = cj + lane % 3 - 1;
+            if (bj >= 0 && bj < a.ng[j]) {
+                const uint32_t w = __ldg(&a.M[(uint64_t)j * a.mwords + ((uint32_t)bj >> 5)]);
+                ok = (w >> (bj & 31)) & 1u;
+            }
+        }
+        occ = __ballot_sync(0xffffffffu, ok);
+    }
     const int n_t = UNI ? (int)active_templates<D>(odd) : a.n_templates;
     for (int t0 = 0; t0 < n_t; t0 += 32) {
         const int t = UNI ? (t0 + lane < n_t ? active_template<D>(odd, (uint32_t)(t0 + lane)) : -1)
                           : (t0 + lane < n_t ? t0 + lane : -1);
         uint32_t beg = 0, len = 0;
         int32_t xlo, xhi, b[D];
-        if (t >= 0 && row_of<D, UNI>(t, c, odd, a, xlo, xhi, b)) {
+        if (t >= 0 && row_of<D, UNI>(t, c, odd, occ, a, xlo, xhi, b)) {
             uint64_t base = 0;
 #pragma unroll
             for (int j = 1; j < D; ++j) base += (uint64_t)b[j] * a.stride[j];

@@ -36,15 +36,29 @@ struct TuneVal {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, TuneVal> g_tune;
 
-constexpr uint32_t kTuneMinItems = 4096;      // smaller joins keep the defaults
 constexpr uint32_t kTuneSampleItems = 24576;  // items per timed launch
 constexpr uint64_t kTuneMaxOutBytes = 512ull << 20;  // above: time count-only launches
 
 }  // namespace
 
+int tune_bucket_ppc(double points_per_cell) {
+    return (int)std::lround(std::log2(std::max(1.0, points_per_cell)));
+}
+
 int tune_bucket(const Index &ix) {
-    const double per = ix.n_cells ? (double)ix.g.n / (double)ix.n_cells : 1.0;
-    return (int)std::lround(std::log2(std::max(1.0, per)));
+    return tune_bucket_ppc(ix.n_cells ? (double)ix.g.n / (double)ix.n_cells : 1.0);
+}
+
+bool tune_lookup(int d, bool f32, bool uni, int bucket, JoinLaunch &l) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(d, f32 ? 1 : 0, uni ? 1 : 0, bucket));
+    if (it == g_tune.end()) return false;
+    l.grab = it->second.grab;
+    l.nbuf = it->second.nbuf;
+    l.wpb = it->second.wpb;
+    l.eb = it->second.eb;
+    l.slots = it->second.slots;
+    return true;
 }
 
 sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned) {

@@ -139,7 +139,7 @@ def test_serving_mix_equals_alone():
             results[k] = pairs
         info = ctx.sj_serve_stats()
         assert info["completed"] == len(jobs) and info["queued"] == 0 and info["inflight"] == 0
-        assert info["graph_launches"] >= 1 and info["lanes"] == 2
+        assert info["graph_launches"] >= 1 and info["lanes"] == 4
         # the oracle, and the same requests alone
         for k, (pts, eps) in enumerate(jobs):
             want = oracle_keys(pts, eps)
@@ -204,6 +204,26 @@ def test_tuner_keeps_results():
         n = c1.sj_selfjoin_count(pts, 0.5)
         assert c1.sj_last_stats()["tuned"] == 1
         assert n == len(r0)
+
+
+def test_multi_join_takes_the_tuned_launch_parameters():
+    """With autotune, the first call tunes the keys its large jobs meet
+    (after their results are out) and the second call runs those jobs with
+    the tuned parameters; both equal the oracle."""
+    jobs = [(datagen.uniform(n, d, seed=300 + d), datagen.eps_for_neighbors(n, d, 32))
+            for n, d in ((300000, 2), (250000, 3), (200000, 4), (150000, 5))]
+    want = [oracle_keys(p, e) for p, e in jobs]
+    with sj.Context(autotune=True) as ctx:
+        for rep in range(2):
+            res = ctx.sj_selfjoin_multi(jobs)
+            for r, w in zip(res, want):
+                assert np.array_equal(keys(r), w)
+        assert ctx.sj_last_stats()["tuned"] >= 1
+    with sj.Context(autotune=False) as ctx:
+        res = ctx.sj_selfjoin_multi(jobs)
+        assert ctx.sj_last_stats()["tuned"] == 0
+        for r, w in zip(res, want):
+            assert np.array_equal(keys(r), w)
 
 
 @pytest.mark.parametrize("world", [2, 3, 5])
