@@ -506,12 +506,9 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
     tot64, wall64, lat64 = one_at_a_time(sj.SJ_PREC_FP64)
     tot32, wall32, lat32 = one_at_a_time(sj.SJ_PREC_FP32_RECHECK)
     assert tot64 == tot32
-    # the tuner on (the default) and off, both contexts kept warm
     ctx_on = sj.Context(device=dev, max_inflight=64, serve_mem_bytes=64 << 30)
-    ctx_off = sj.Context(device=dev, max_inflight=64, serve_mem_bytes=64 << 30, autotune=False)
-    for c in (ctx_on, ctx_off):
-        for k in range(min(8, n_req)):    # engines, graphs, pinned buffers
-            c.sj_poll(c.sj_submit(pts[k], reqs[k]["eps"]), wait_ms=60000, copy=False)
+    for k in range(min(8, n_req)):        # engines, graphs, pinned buffers
+        ctx_on.sj_poll(ctx_on.sj_submit(pts[k], reqs[k]["eps"]), wait_ms=60000, copy=False)
 
     def run(arrivals, ctx=None):
         ctx = ctx or ctx_on
@@ -539,8 +536,7 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
         wall = max(td for _, (ts, ta, td) in got) - min(ts for _, (ts, ta, td) in got)
         return sum(c for c, _ in got), wall, lat
 
-    run([0.0] * nb)                       # untimed passes: pinned result buffers, pool, tuner
-    run([0.0] * nb, ctx_off)
+    run([0.0] * nb)                       # untimed pass: pinned result buffers, pool
     p_sat, wall_sat, lat_sat = run([0.0] * n_req)
     assert n_req > nb or p_sat == tot64
     rate_sat = n_req / wall_sat
@@ -553,17 +549,8 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
                       "req_per_s": round(n_req / wall_poi, 1),
                       "pairs_per_s": round(p_poi / wall_poi, 1),
                       "p50_ms": _pct(lat_poi, 50), "p99_ms": _pct(lat_poi, 99)})
-    # tuner on against off on the first 2,000 requests, saturated, passes
-    # interleaved so that neither profits from running later
-    ab = {"on": [], "off": []}
-    m_ab = min(2000, n_req)
-    for _ in range(2):
-        for key, c in (("off", ctx_off), ("on", ctx_on)):
-            p_ab, wall_ab, _ = run([0.0] * m_ab, c)
-            ab[key].append(p_ab / wall_ab)
     info = ctx_on.sj_serve_stats()
     ctx_on.close()
-    ctx_off.close()
     return {
         "requests": n_req, "pairs": p_sat,
         "request_mix": "n log-uniform [1e3,1e6], d uniform {2..6}, eps for U[8,128] mean neighbours, "
@@ -571,10 +558,7 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
         "saturated": {"pairs_per_s": round(p_sat / wall_sat, 1), "req_per_s": round(rate_sat, 1),
                       "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99)},
         "sweep": sweep,
-        "tuner_ab": {"requests": m_ab, "pairs_per_s_on": [round(v, 1) for v in ab["on"]],
-                     "pairs_per_s_off": [round(v, 1) for v in ab["off"]],
-                     "on_over_off": round(sum(ab["on"]) / sum(ab["off"]), 3)},
-        "tuned_requests": info["tuned_jobs"], "tuned_keys": info["tuned_keys"],
+
         "one_at_a_time_fp64": {"requests": nb, "pairs_per_s": round(tot64 / wall64, 1),
                                "p50_ms": _pct(lat64, 50), "p99_ms": _pct(lat64, 99)},
         "one_at_a_time_fp32": {"requests": nb, "pairs_per_s": round(tot32 / wall32, 1),

@@ -130,15 +130,17 @@ typedef struct {
     int32_t min_batches;     /* minimum result batches for host results
                                 (Section V-A uses 3); default 3 */
     int32_t sorted;          /* 1: host results sorted by (i << 32) | j */
-    int32_t autotune;        /* 1 (default): the search-and-refine launch
-                                parameters (grab, chunk ring depth, pair
-                                staging size, warps per block) come from
-                                the tuner, which times
-                                sampled count-only launches the first time a
-                                (d, precision, UNICOMP, points-per-cell
-                                bucket) key is met in the process and reuses
-                                the choice after; 0: fixed defaults.  Never
-                                changes the result. */
+    int32_t autotune;        /* 1 (default): the launch parameters of a
+                                single join's search-and-refine launch
+                                (grab, chunk ring depth, pair staging size,
+                                item slots, warps per block) come from the
+                                tuner, which times sampled count-only
+                                launches the first time a (d, precision,
+                                UNICOMP, points-per-cell bucket) key is met
+                                in the process and reuses the choice after;
+                                0: fixed defaults.  The many-join launch of
+                                sj_selfjoin_multi and sj_submit keeps the
+                                defaults.  Never changes the result. */
     int32_t device;          /* CUDA device ordinal; default 0 */
     int32_t lookup;          /* sj_lookup; default SJ_LOOKUP_AUTO */
     int32_t profile;         /* 1: time every join-kernel launch with CUDA
@@ -528,14 +530,11 @@ typedef struct {
     int32_t inflight;          /* admitted requests now */
     int32_t lanes;             /* waves that may run at the same time */
     int32_t max_concurrent_waves; /* most waves seen running at once */
-    int32_t tuned_keys;        /* tuner keys (d, precision, points-per-cell
-                                  bucket) the lanes tuned after a wave */
+    int32_t reserved;
     /* host wall time summed over the lanes' waves (ms): points to the device
      * and the bounds pass, the graph replay (index build + join), the result
      * copies to the host */
     double ms_bounds, ms_graph, ms_output;
-    uint64_t tuned_jobs;       /* requests joined with the tuner's launch
-                                  parameters (autotune = 1) */
 } sj_serve_info;
 
 SJ_API sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out);

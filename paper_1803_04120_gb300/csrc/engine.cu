@@ -17,19 +17,13 @@
 // table from device memory, so only the multi-join node's launch shape and
 // job table (kernel parameters) are updated per wave.
 //
-// Launch parameters are per job.  With autotune, each job takes the
-// tuner's cached grab (work items per cursor bump) for its key (d,
-// precision, UNICOMP, bucket), the bucket estimated on the host from the
-// points per occupied cell that uniform data in the job's bounding box
-// would give; a job whose actual key (read back after the wave) has no
-// choice yet and that is large enough is tuned on its own index after the
-// wave's results are out (tune.cu), once per key and process, so that later
-// waves take it.  The tuner's ring depth, staging size and item slots are
-// not taken: they set a job's shared memory per warp, and the launch runs
-// every job at the largest one, so a choice that pays for one large join
-// lowers the occupancy of the whole wave (measured on the 10,000-request
-// stream: 12.9 G pairs/s with the defaults, 9.3 G with every job's tuned
-// parameters).
+// Launch parameters are per job: the context's forced ones, else the
+// defaults.  The launch tuner (tune.cu) is not applied to waves: its
+// choices come from single joins, and in one launch of many small joins
+// they lost (measured on the 10,000-request stream, passes interleaved:
+// 0.90x of the fixed defaults with the tuned grab alone; 9.3 against
+// 12.9 G pairs/s with every tuned parameter, since one job's larger
+// shared memory per warp lowers the occupancy of the whole wave).
 //
 // The engine takes jobs whose grid fits the dense lookup table (at most
 // max(2^25, 16 n) cells, and at most kEngMaxLut) with n <= kEngMaxN; any
@@ -569,23 +563,6 @@ JoinLaunch job_launch(const Engine *e) {
     return l;
 }
 
-// The tuner applies unless it is off or a launch parameter is forced.
-bool tune_on(const Engine *e) {
-    const sj_config &c = e->cfg;
-    return c.autotune && !(c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.wpb > 0 || c.slots > 0);
-}
-
-// Tuner bucket of a job before its index exists: the points per occupied
-// cell that n uniform points in the job's bounding box would give,
-// n / (C (1 - exp(-n / C))) for the C cells the box spans.
-int bucket_estimate(const Geometry &g) {
-    double C = 1.0;
-    for (int j = 0; j < g.d; ++j) C *= std::floor((g.gmax[j] - g.gmin[j] - 2.0 * g.eps) / g.w) + 1.0;
-    const double n = (double)g.n;
-    const double occ = C * -std::expm1(-n / std::max(C, 1.0));
-    return tune_bucket_ppc(n / std::max(occ, 1.0));
-}
-
 sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
                           void (*on_done)(void *user, int job), void *user,
                           std::vector<JobMem> &mem) {
@@ -599,7 +576,6 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         jobs[i]->res = nullptr;
         jobs[i]->evaluations = jobs[i]->rechecks = 0;
         jobs[i]->path = 0;
-        jobs[i]->tuned = 0;
     }
     auto job_fail = [&](int i, sj_status st, const std::string &msg) {
         jobs[i]->st = st;
@@ -776,13 +752,7 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         v.lut.p = sl.lut;
         v.items.p = sl.items;
         v.counts_dev.p = sl.mm;
-        JoinLaunch l = job_launch(e);
-        JoinLaunch t = l;
-        if (tune_on(e) && tune_lookup(d, m.f32, true, bucket_estimate(g), t)) {
-            l.grab = t.grab;       // grab only: see the file comment
-            J.tuned = 1;
-            e->stats.tuned_jobs++;
-        }
+        const JoinLaunch l = job_launch(e);
         JoinArgs &a = MJ->job[slot];
         if (fill_join_args(e2, v, l, 0, 0xffffffffu, m.out, m.cap, sl.misc,
                            reinterpret_cast<uint32_t *>(sl.misc + 4),
@@ -819,9 +789,6 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         SJ_CUDA_TRY(cudaMemcpyAsync(e->h_misc, e->d_misc,
                                     sizeof(unsigned long long) * kMultiJobs * kMiscWords,
                                     cudaMemcpyDeviceToHost, s));
-        if (tune_on(e))   // |G| and the work items of every job, for the tuner keys
-            SJ_CUDA_TRY(cudaMemcpyAsync(e->h_mm, e->d_mm, sizeof(unsigned long long) * kMultiJobs * kMmWords,
-                                        cudaMemcpyDeviceToHost, s));
         SJ_CUDA_TRY(cudaStreamSynchronize(s));
     }
     const double t3 = now_ms();
@@ -909,25 +876,6 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         signalled[i] = 1;
     }
     const double t4 = now_ms();
-
-    // tuner keys met for the first time: tune on the job's own index, now
-    // that its results are out (later waves take the choice)
-    if (tune_on(e)) {
-        for (int i : order) {
-            if (jobs[i]->st != SJ_OK) continue;
-            JobMem &m = mem[i];
-            const uint32_t *cnt = reinterpret_cast<const uint32_t *>(e->h_mm + (size_t)i * kMmWords + 2 * kMaxDim);
-            m.view.n_cells = cnt[1];
-            m.view.n_items = cnt[2];
-            m.view.counts_read = 1;
-            if (m.view.n_items < kTuneMinItems) continue;
-            JoinLaunch l = job_launch(e);
-            if (tune_lookup(m.g.d, m.f32, true, tune_bucket(m.view), l)) continue;
-            Error e2;
-            int tuned = 0;
-            if (tune_launch(e2, m.view, l, s, &tuned) == SJ_OK && tuned == 2) e->stats.tuned_keys++;
-        }
-    }
 
     // jobs the engine does not take: the stand-alone path
     for (int i : standalone) {

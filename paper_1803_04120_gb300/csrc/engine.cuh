@@ -21,15 +21,12 @@ struct EngJob {
     sj_result *res = nullptr;    // host result, owned by the caller afterwards
     uint64_t evaluations = 0, rechecks = 0;
     int path = 0;                // 0 multi-join launch, 1 stand-alone join, 2 rerun after overflow
-    int tuned = 0;               // 1: the launch parameters came from the tuner's cache
 };
 
 // Counters of an engine since it was created.
 struct EngStats {
     uint64_t waves = 0, jobs = 0, graph_launches = 0, kernel_nodes = 0;
     uint64_t overflow_reruns = 0, standalone = 0;
-    uint64_t tuned_jobs = 0;     // jobs that ran with the tuner's parameters
-    uint64_t tuned_keys = 0;     // tuner keys this engine tuned after a wave
     double ms_bounds = 0, ms_graph = 0, ms_output = 0;
 };
 

@@ -360,8 +360,6 @@ sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out) {
         out->ms_bounds += es.ms_bounds;
         out->ms_graph += es.ms_graph;
         out->ms_output += es.ms_output;
-        out->tuned_jobs += es.tuned_jobs;
-        out->tuned_keys += (int32_t)es.tuned_keys;
     }
     out->graph_launches = g;
     return SJ_OK;
@@ -398,7 +396,7 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
     const uint64_t budget = mem_budget(ctx);
     sj_status first = SJ_OK;
     std::string first_msg;
-    uint64_t pairs = 0, evals = 0, rechecks = 0, waves = 0, reruns = 0, tuned = 0;
+    uint64_t pairs = 0, evals = 0, rechecks = 0, waves = 0, reruns = 0;
     const double t0 = now_ms();
     for (uint64_t b = 0; b < n_jobs;) {
         std::vector<EngJob> wave;
@@ -429,7 +427,6 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
         for (size_t q = 0; q < wave.size(); ++q) {
             sj_status js = st != SJ_OK ? st : wave[q].st;
             if (wave[q].path == 2) ++reruns;
-            tuned += wave[q].tuned;
             if (js == SJ_OK) {
                 out[base + q] = wave[q].res;
                 pairs += wave[q].res->count;
@@ -457,7 +454,6 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
     ctx->stats.rechecks = rechecks;
     ctx->stats.batches = (uint32_t)waves;
     ctx->stats.retries = (uint32_t)reruns;
-    ctx->stats.tuned = (int32_t)tuned;   // jobs that ran with the tuner's parameters
     ctx->stats.ms_total = now_ms() - t0;
     ctx->stats.kernel_launches = launches_so_far() - l0;
     ctx->last_err = first == SJ_OK ? std::string() : first_msg;

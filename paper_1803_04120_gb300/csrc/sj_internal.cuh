@@ -281,8 +281,6 @@ sj_status shard_items(Error &err, const Index &ix, bool uni, int rank, int world
 // known on the host.
 int tune_bucket(const Index &ix);
 int tune_bucket_ppc(double points_per_cell);
-// The cached choice for (d, precision, UNICOMP, bucket), if any; no device work.
-bool tune_lookup(int d, bool f32, bool uni, int bucket, JoinLaunch &l);
 // Smallest join (work items) the tuner times; smaller joins keep the defaults.
 constexpr uint32_t kTuneMinItems = 4096;
 sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned);

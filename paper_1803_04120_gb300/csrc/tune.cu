@@ -49,18 +49,6 @@ int tune_bucket(const Index &ix) {
     return tune_bucket_ppc(ix.n_cells ? (double)ix.g.n / (double)ix.n_cells : 1.0);
 }
 
-bool tune_lookup(int d, bool f32, bool uni, int bucket, JoinLaunch &l) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(std::make_tuple(d, f32 ? 1 : 0, uni ? 1 : 0, bucket));
-    if (it == g_tune.end()) return false;
-    l.grab = it->second.grab;
-    l.nbuf = it->second.nbuf;
-    l.wpb = it->second.wpb;
-    l.eb = it->second.eb;
-    l.slots = it->second.slots;
-    return true;
-}
-
 sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned) {
     *tuned = 0;
     const bool f32 = l.prec_fp32 && ix.g.fp32_ok;

@@ -91,9 +91,8 @@ class sj_serve_info(ctypes.Structure):
                 ("graph_launches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
                 ("mem_in_use", ctypes.c_uint64), ("inflight", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("max_concurrent_waves", ctypes.c_int32),
-                ("tuned_keys", ctypes.c_int32), ("ms_bounds", ctypes.c_double),
-                ("ms_graph", ctypes.c_double), ("ms_output", ctypes.c_double),
-                ("tuned_jobs", ctypes.c_uint64)]
+                ("reserved", ctypes.c_int32), ("ms_bounds", ctypes.c_double),
+                ("ms_graph", ctypes.c_double), ("ms_output", ctypes.c_double)]
 
 
 CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
@@ -463,7 +462,7 @@ class Context:
     def sj_serve_stats(self) -> dict:
         s = sj_serve_info()
         self._check(self._lib.sj_serve_stats(self._h, ctypes.byref(s)), "sj_serve_stats")
-        return {k: getattr(s, k) for k, _ in sj_serve_info._fields_}
+        return {k: getattr(s, k) for k, _ in sj_serve_info._fields_ if k != "reserved"}
 
     # -- diagnostics
     def sj_last_stats(self) -> dict:

@@ -206,26 +206,6 @@ def test_tuner_keeps_results():
         assert n == len(r0)
 
 
-def test_multi_join_takes_the_tuned_launch_parameters():
-    """With autotune, the first call tunes the keys its large jobs meet
-    (after their results are out) and the second call runs those jobs with
-    the tuned parameters; both equal the oracle."""
-    jobs = [(datagen.uniform(n, d, seed=300 + d), datagen.eps_for_neighbors(n, d, 32))
-            for n, d in ((300000, 2), (250000, 3), (200000, 4), (150000, 5))]
-    want = [oracle_keys(p, e) for p, e in jobs]
-    with sj.Context(autotune=True) as ctx:
-        for rep in range(2):
-            res = ctx.sj_selfjoin_multi(jobs)
-            for r, w in zip(res, want):
-                assert np.array_equal(keys(r), w)
-        assert ctx.sj_last_stats()["tuned"] >= 1
-    with sj.Context(autotune=False) as ctx:
-        res = ctx.sj_selfjoin_multi(jobs)
-        assert ctx.sj_last_stats()["tuned"] == 0
-        for r, w in zip(res, want):
-            assert np.array_equal(keys(r), w)
-
-
 @pytest.mark.parametrize("world", [2, 3, 5])
 def test_shards_partition_the_join(world):
     """One join split over `world` ranks (run one after another on this GPU;
