@@ -377,17 +377,26 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     const uint64_t est = (uint64_t)est_d;
     ctx->stats.estimate = est;
     const uint64_t padded = est + est / 8 + 4096;
-    const uint64_t nb = batches_for(est);
-    uint64_t bufcap = std::min<uint64_t>(bufcap_max, padded / nb + padded / (4 * nb) + 65536);
-    // batch b covers items [cut[b], cut[b+1]): equal estimated pairs, the
-    // cumulative estimate interpolated linearly inside a segment
+    const uint64_t nb_eq = batches_for(est);
+    uint64_t bufcap = std::min<uint64_t>(bufcap_max, padded / nb_eq + padded / (4 * nb_eq) + 65536);
+    // Batch 0's kernel overlaps no copy, while every later batch's kernel
+    // overlaps the copy of the one before: a small first batch (1/16 of the
+    // estimated pairs, or less) leaves little of the join exposed, and the
+    // rest is cut into nb_eq batches of equal estimated pairs.  Batch b
+    // covers items [cut[b], cut[b+1]); the cumulative estimate is
+    // interpolated linearly inside a segment.
+    const bool lead = nb_eq >= 2 && ni >= 2 * nb_eq + 2;
+    const uint64_t nb = nb_eq + (lead ? 1 : 0);
+    const double f0 = lead ? std::min(1.0 / 16.0, 0.5 / (double)nb_eq) : 0.0;
     std::vector<uint32_t> cut(nb + 1, 0);
     cut[nb] = ni;
     {
         double acc = 0;
         uint32_t q = 0;
         for (uint64_t b = 1; b < nb; ++b) {
-            const double target = est_d * (double)b / (double)nb;
+            const double frac = lead ? f0 + (1.0 - f0) * (double)(b - 1) / (double)nb_eq
+                                     : (double)b / (double)nb;
+            const double target = est_d * frac;
             while (q < S && acc + seg[q] < target) acc += seg[q++];
             uint32_t x;
             if (q >= S) {
