@@ -161,18 +161,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                         const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
                         const ulonglong2 *qd =
                             reinterpret_cast<const ulonglong2 *>(reinterpret_cast<const f2_t *>(qs) + (size_t)qi * DW);
-                        f2_t acc = f2_pack(0.0f, 0.0f);
+                        // two running fma sums, even and odd coordinates,
+                        // added at the end (two independent chains; the
+                        // margin holds for any grouping, margin.cu)
+                        f2_t acc0 = f2_pack(0.0f, 0.0f), acc1 = acc0;
 #pragma unroll
                         for (int j2 = 0; j2 < DW / 2; ++j2) {
                             const ulonglong2 q2 = qd[j2];   // (q_j, q_j), (q_j+1, q_j+1)
-                            // fl(q - y) on both halves, then the running fma sum
+                            // fl(q - y) on both halves
                             const f2_t t0 = f2_fma(yy[2 * j2], neg1, q2.x);
-                            acc = f2_fma(t0, t0, acc);
+                            acc0 = f2_fma(t0, t0, acc0);
                             const f2_t t1 = f2_fma(yy[2 * j2 + 1], neg1, q2.y);
-                            acc = f2_fma(t1, t1, acc);
+                            acc1 = f2_fma(t1, t1, acc1);
                         }
                         float sv[2];
-                        f2_unpack(acc, sv[0], sv[1]);
+                        f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
                         bool hit[2], band[2];
 #pragma unroll
                         for (int h2 = 0; h2 < 2; ++h2) {

@@ -59,11 +59,15 @@
 //
 // Difference form (points of more than 8 dimensions).  The kernel stores
 // y_j = fl32(fl64(x_j - fmin_j)) for every dimension (fmin_j = min_j - eps,
-// X_j = fmax_j - fmin_j) and evaluates
-//     t_j = fl(y_p,j - y_q,j),   s32 = fma(t_{d-1}, t_{d-1}, ... fma(t_0, t_0, 0)).
+// X_j = fmax_j - fmin_j) and evaluates t_j = fl(y_p,j - y_q,j) and s32 as
+// two fma chains, one over the even and one over the odd coordinates,
+//     s_e = fma(t_j, t_j, ... ) (j even),  s_o likewise (j odd),  s32 = fl(s_e + s_o).
 //  (a) |y_j - (x_j - fmin_j)| <= rho_j = X_j (u + v + uv) + 2^-150;
 //  (b) |t_j - Delta_j| <= 2 rho_j + u (|Delta_j| + 2 rho_j);
-//  (c) every term is non-negative, so (1 - g_d) |t|^2 <= s32 <= (1 + g_d) |t|^2.
+//  (c) every term is non-negative, and each t_j^2 passes through at most
+//      ceil(d/2) + 1 <= d roundings (its fma, the later fmas of its chain,
+//      the final add), each a factor within (1 +- u): so
+//      (1 - g_d) |t|^2 <= s32 <= (1 + g_d) |t|^2, for any grouping of the sum.
 // Member: |Delta| <= R2, each |Delta_j| <= R2, so |t| <= R2 + H2 with
 // H2 = |(2 rho_j + u (R2 + 2 rho_j))_j| and hi = (1 + g_d)(R2 + H2)^2.
 // Conversely s32 <= lo = (1 - g_d)(R1 - H1)^2 gives |t| <= T = R1 - H1, each

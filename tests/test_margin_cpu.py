@@ -268,15 +268,20 @@ def test_cell_frame_margin_at_any_extent():
 
 # ---------------------------------------------------------------- difference form (d > 8)
 
-def kernel_s32_diff(p, q, fmin):
-    """s32 of the high-dimensional kernel: fma chain of fl32(y_p - y_q)^2."""
-    acc = F(0)
+def kernel_s32_diff(p, q, fmin, chains=2):
+    """s32 of the high-dimensional kernel: fma chains of fl32(y_p - y_q)^2,
+    coordinate j in chain j mod chains, the chains added at the end (the
+    kernel uses two; one chain is the plain sequential sum)."""
+    acc = [F(0)] * chains
     for j in range(len(p)):
         yp = r32(r64(F(p[j]) - F(fmin[j])))
         yq = r32(r64(F(q[j]) - F(fmin[j])))
         t = r32(yp - yq)
-        acc = r32(t * t + acc)
-    return acc
+        acc[j % chains] = r32(t * t + acc[j % chains])
+    s = acc[0]
+    for a in acc[1:]:
+        s = r32(s + a)
+    return s
 
 
 @pytest.mark.parametrize("d,eps,scale,offset", [
@@ -303,12 +308,13 @@ def test_difference_form_margin_sound_on_threshold_pairs(d, eps, scale, offset):
     checked = 0
     for k, p in enumerate(pts):
         for q in extra[9 * k: 9 * k + 9]:
-            s = kernel_s32_diff(p, q, fmin)
             mem = exact_member(p, q, E2)
-            if s <= F(lo):
-                assert mem, (d, k)
-            if s > F(hi):
-                assert not mem, (d, k)
+            for chains in (2, 1):
+                s = kernel_s32_diff(p, q, fmin, chains)
+                if s <= F(lo):
+                    assert mem, (d, k, chains)
+                if s > F(hi):
+                    assert not mem, (d, k, chains)
             checked += 1
     assert checked == 450
 
