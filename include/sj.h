@@ -30,9 +30,12 @@
  *
  * Conventions for every call:
  *   - `pts` is n x d row-major FP64.  It may be a host or a device pointer;
- *     the library detects which.  The caller keeps ownership; the library
- *     copies what it needs and does not hold the pointer after the call
- *     returns (sj_submit copies the points before it returns).
+ *     the library detects which.  The caller keeps ownership and must not
+ *     change the array until the call returns (nor from a callback the
+ *     call makes): calls that build an index only for themselves read
+ *     device points in place, without a copy.  The library does not hold
+ *     the pointer after the call returns (sj_build_index and sj_submit copy
+ *     the points before they return).
  *   - A pair is two consecutive uint32 values (i, j).  Results returned in
  *     sj_result are library-owned host memory, valid until sj_result_free.
  *   - Pair order is unspecified unless sj_config.sorted = 1, which orders

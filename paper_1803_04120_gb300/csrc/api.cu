@@ -159,6 +159,7 @@ constexpr int kMiscCounter = 0;   // [0..3] pairs, evaluations, rechecks, spare
 constexpr int kMiscWork = 4;      // u32 cursor
 constexpr int kMiscError = 5;     // u32 error word
 constexpr int kMiscWords = 8;
+constexpr int kEarlyCountsWord = 32;   // h_misc words of the early build counters
 
 struct Scoped {
     sj_ctx *ctx;
@@ -227,15 +228,33 @@ JoinLaunch launch_cfg(const sj_ctx *ctx) { return ctx->launch; }
 
 // Launch parameters of the join on ix: the defaults, or with autotune = 1
 // (and no launch parameter forced in the configuration) the tuner's choice for the
-// index's key (one host read of |G| and the work-item count first).
+// index's key (|G| read on the host first, from the mid-build copy when there is one).
 sj_status prepare_launch(Error &err, sj_ctx *ctx, Index &ix, cudaStream_t s) {
     ctx->launch = default_launch(ctx);
     ctx->launch_tuned = 0;
     // the tuned parameters belong to the main kernel, not the one for more
     // than 8 dimensions
     if (!ctx->cfg.autotune || launch_forced(ctx->cfg) || ix.dfull > kMaxDim) return SJ_OK;
-    SJ_TRY(read_counts(err, ix, s));
+    if (!ix.counts_read && ix.early_ev) {
+        // |G| was copied mid-build: wait for that copy only, not the build
+        SJ_CUDA_TRY(cudaEventSynchronize(ix.early_ev));
+        ix.n_cells = ix.early_counts[1];
+    } else {
+        SJ_TRY(read_counts(err, ix, s));
+    }
     return tune_launch(err, ix, ctx->launch, s, &ctx->launch_tuned);
+}
+
+// Build options of a call whose index lives only inside the call: device
+// points are read in place and |G| is copied to the host mid-build.
+BuildOpts call_build_opts(sj_ctx *ctx) {
+    BuildOpts o;
+    o.borrow_pts = true;
+    if (ctx->ev_counts) {
+        o.h_counts = reinterpret_cast<uint32_t *>(ctx->h_misc + kEarlyCountsWord);
+        o.ev_counts = ctx->ev_counts;
+    }
+    return o;
 }
 
 void record_launch(sj_ctx *ctx, const Index &ix) {
@@ -711,7 +730,8 @@ sj_status sj_create(const sj_config *cfg, sj_ctx **out) {
         cudaStreamCreateWithFlags(&ctx->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
         dev_alloc(err, ctx->misc, kMiscWords * sizeof(unsigned long long), ctx->s_main) != SJ_OK ||
         cudaHostAlloc((void **)&ctx->h_misc, 64 * sizeof(unsigned long long), cudaHostAllocPortable) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_counts, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         sj_destroy(ctx);
         return SJ_ENOMEM;
@@ -732,6 +752,7 @@ void sj_destroy(sj_ctx *ctx) {
     dev_free(ctx->misc, ctx->s_main);
     if (ctx->s_main) cudaStreamSynchronize(ctx->s_main);
     if (ctx->h_misc) cudaFreeHost(ctx->h_misc);
+    if (ctx->ev_counts) cudaEventDestroy(ctx->ev_counts);
     for (auto &e : ctx->prof) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
     if (ctx->s_copy) cudaStreamDestroy(ctx->s_copy);
@@ -843,8 +864,9 @@ sj_status sj_selfjoin_device(sj_ctx *ctx, const double *pts, uint64_t n, int d, 
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double t0 = now_ms();
+    const BuildOpts bo = call_build_opts(ctx);
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix, nullptr, &bo);
     double t1 = now_ms();
     if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, d_pairs, cap_pairs, count, s, 0);
     free_index(ix, s);
@@ -868,8 +890,9 @@ sj_status sj_selfjoin_shard_device(sj_ctx *ctx, const double *pts, uint64_t n, i
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double t0 = now_ms();
+    const BuildOpts bo = call_build_opts(ctx);
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ix, nullptr, &bo);
     double t1 = now_ms();
     uint32_t lo = 0, hi = 0;
     if (st == SJ_OK) st = shard_items(sc.err, ix, ctx->cfg.unicomp != 0, rank, world, s, &lo, &hi);
@@ -913,8 +936,10 @@ sj_status sj_join2_device(sj_ctx *ctx, const double *R, uint64_t nR, const doubl
             mm[2 * j] = std::min(mR[2 * j], mS[2 * j]);
             mm[2 * j + 1] = std::max(mR[2 * j + 1], mS[2 * j + 1]);
         }
-        SJ_TRY(build_index(err, static_cast<const double *>(dS.p), nS, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ixS, mm));
-        SJ_TRY(build_index(err, static_cast<const double *>(dR.p), nR, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ixR, mm));
+        BuildOpts bo_in;
+        bo_in.borrow_pts = true;
+        SJ_TRY(build_index(err, static_cast<const double *>(dS.p), nS, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ixS, mm, &bo_in));
+        SJ_TRY(build_index(err, static_cast<const double *>(dR.p), nR, d, eps, ctx->cfg.lookup, ctx->cfg.frame, s, ixR, mm, &bo_in));
         const double t1 = now_ms();
         ctx->stats.ms_index = t1 - t0;
         JoinLaunch l = default_launch(ctx);
@@ -1017,8 +1042,9 @@ sj_status sj_selfjoin_count(sj_ctx *ctx, const double *pts, uint64_t n, int d, d
     if (st != SJ_OK) return sc.done(st);
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
     double t0 = now_ms();
+    const BuildOpts bo = call_build_opts(ctx);
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix, nullptr, &bo);
     if (st == SJ_OK) st = device_join_on(ctx, sc.err, ix, nullptr, 0, count, ctx->s_main, 1);
     free_index(ix, ctx->s_main);
     cudaStreamSynchronize(ctx->s_main);
@@ -1034,8 +1060,9 @@ static sj_status host_join_from_pts(sj_ctx *ctx, const double *pts, uint64_t n, 
     if (st != SJ_OK) return sc.done(st);
     if ((st = set_device(sc.err, ctx->device)) != SJ_OK) return sc.done(st);
     double t0 = now_ms();
+    const BuildOpts bo = call_build_opts(ctx);
     Index ix;
-    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix);
+    st = build_index(sc.err, pts, n, d, eps, ctx->cfg.lookup, ctx->cfg.frame, ctx->s_main, ix, nullptr, &bo);
     double t1 = now_ms();
     if (st == SJ_OK) st = host_join(sc.err, ctx, ix, sink);
     free_index(ix, ctx->s_main);

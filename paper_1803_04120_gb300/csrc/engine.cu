@@ -310,10 +310,9 @@ __global__ void __launch_bounds__(kEngThreads) eng_cells(const EngTable *__restr
     uint32_t s, x, X;
     if (!my_slot(t, s, x, X)) return;
     const EngSlot &e = t->slot[s];
-    const CellParams cp = e.cp;
-    const uint32_t nc = e.counts[1];
-    for (uint64_t h = (uint64_t)x * blockDim.x + threadIdx.x; h < nc; h += (uint64_t)X * blockDim.x)
-        cell_coords(e.pts + (uint64_t)e.A[e.G[h]] * cp.d, h, cp, e.mwords, e.cc, e.M);
+    __shared__ uint32_t sm[kCellsSmemWords];
+    cells_block<true>(e.pts, e.A, e.G, e.B, e.counts[1], (uint64_t)x * blockDim.x + threadIdx.x,
+                      (uint64_t)X * blockDim.x, e.cp, e.mwords, e.cc, e.M, sm);
 }
 
 __global__ void __launch_bounds__(kEngThreads) eng_rec(const EngTable *__restrict__ t) {

@@ -53,15 +53,41 @@ inline CellParams cell_params(const Geometry &g) {
     return cp;
 }
 
+// Cell coordinate in dimension j of a point whose offset from the grid's
+// lower corner is a = fl64(x_j - g_min_j): c_j = floor(q) for q = fl64(a *
+// (1 / w)), clamped to [0, |g_j| - 1].  The floor is taken on q's bits
+// with integer instructions (the FP64 pipe is the bottleneck of the cell
+// pass): q < 1, including -0 and every negative q, gives 0; q >= 2^31
+// exceeds |g_j| - 1 < 2^31; otherwise, with q = m 2^(e - 52) for the 53-bit
+// significand m and exponent e in [0, 30], floor(q) = m >> (52 - e).
+__device__ __forceinline__ int64_t cell_of_offset(double a, int j, const CellParams &cp) {
+    const double q = __dmul_rn(a, cp.inv_w);
+    const uint64_t b = (uint64_t)__double_as_longlong(q);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    int64_t c;
+    if ((b >> 63) != 0 || e < 0)
+        c = 0;
+    else if (e > 30)
+        c = cp.ng[j] - 1;
+    else
+        c = (int64_t)(((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (52 - e));
+    return c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
+}
+
 // Cell coordinate of point p in dimension j: c_j = floor((x_j - g_min_j) *
 // (1 / w)) in FP64, clamped to the grid.  Every part of the index computes
-// a point's cell with this one formula.
+// a point's cell with this one formula (cell_of_offset).
 __device__ __forceinline__ int64_t cell_coord(const double *p, int j, const CellParams &cp) {
-    const double q = __dmul_rn(__dsub_rn(p[j], cp.gmin[j]), cp.inv_w);
-    int64_t c = (int64_t)floor(q);
-    c = c < 0 ? 0 : c;
-    c = c > cp.ng[j] - 1 ? cp.ng[j] - 1 : c;
-    return c;
+    return cell_of_offset(__dsub_rn(p[j], cp.gmin[j]), j, cp);
+}
+
+// FP32 record coordinate of offset a = fl64(x_j - g_min_j) in cell
+// coordinate c: grid frame y = fl32(a); cell frame y = fl32(a - fl64(4 K w))
+// with K = floor(c / 4).
+__device__ __forceinline__ float rec_coord(double a, int64_t c, const CellParams &cp) {
+    double y = a;
+    if (cp.frame == SJ_FRAME_CELL) y = __dsub_rn(a, __dmul_rn((double)(4 * (c >> 2)), cp.w));
+    return __double2float_rn(y);
 }
 
 // Linear cell id of point p: id = sum_j c_j * stride_j (dimension 1 fastest).
@@ -116,24 +142,82 @@ __device__ __forceinline__ void bounds_accumulate(const double *__restrict__ pts
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
-// Cell coordinates of the non-empty cell h, recomputed from one of its
-// points p with the formula of linear_cell (so they agree with the cell's
-// id without 64-bit divisions), and its bits in the occupancy bitmaps M_j
-// (when M is given).
-__device__ __forceinline__ void cell_coords(const double *p, uint64_t h, const CellParams &cp,
-                                            uint32_t mwords, int32_t *__restrict__ cc,
-                                            uint32_t *__restrict__ M) {
+// Shared-memory words for the occupancy bitmaps in cells_block: when all d
+// bitmaps fit (d * mwords words), bits collect per block and are merged
+// into M with one atomicOr per non-zero word and block.
+constexpr uint32_t kCellsSmemWords = 2048;
+
+// Coordinates of the cell with linear id `id` (id = sum_j c_j stride_j with
+// 0 <= c_j < |g_j|, dimension 1 fastest): the mixed-radix digits of id,
+// equal to the coordinates linear_cell combined.
+__device__ __forceinline__ void coords_of_id(uint64_t id, const CellParams &cp, int64_t *c) {
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j) {
         if (j < cp.d) {
-            const int64_t c = cell_coord(p, j, cp);
-            cc[h * cp.d + j] = (int32_t)c;
-            if (M) {
-                uint32_t *w = &M[(uint64_t)j * mwords + (c >> 5)];
-                const uint32_t bit = 1u << (c & 31);
-                if ((*(volatile uint32_t *)w & bit) == 0) atomicOr(w, bit);
+            const uint64_t g = (uint64_t)cp.ng[j];
+            if ((id >> 32) == 0) {
+                const uint32_t r = (uint32_t)id, q = r / (uint32_t)g;
+                c[j] = (int64_t)(r - q * (uint32_t)g);
+                id = q;
+            } else {
+                const uint64_t q = id / g;
+                c[j] = (int64_t)(id - q * g);
+                id = q;
             }
         }
+    }
+}
+
+// Cell coordinates of the non-empty cells h = h0, h0 + step, ... below nc
+// into cc (d per cell), and their bits in the occupancy bitmaps M_j (word
+// j * mwords + c_j / 32).  The coordinates are the digits of the cell's
+// linear id B[h] (FROM_KEY) or, for cells ordered by coordinate tuple (no
+// B), recomputed from one of the cell's points with the formula of
+// linear_cell.  sm: shared memory of kCellsSmemWords words; the bits
+// collect there when the d bitmaps fit.  A word is read before its
+// atomicOr, so that a bit already set costs no atomic (a stale read only
+// costs a redundant one).  Every thread of the block calls this (it has
+// barriers).
+template <bool FROM_KEY>
+__device__ __forceinline__ void cells_block(const double *__restrict__ pts,
+                                            const uint32_t *__restrict__ A,
+                                            const uint32_t *__restrict__ G,
+                                            const uint64_t *__restrict__ B, uint64_t nc,
+                                            uint64_t h0, uint64_t step, const CellParams &cp,
+                                            uint32_t mwords, int32_t *__restrict__ cc,
+                                            uint32_t *__restrict__ M, uint32_t *sm) {
+    const uint64_t mw = (uint64_t)cp.d * mwords;
+    const bool local = mw <= kCellsSmemWords;
+    if (local) {
+        for (uint32_t k = threadIdx.x; k < mw; k += blockDim.x) sm[k] = 0u;
+        __syncthreads();
+    }
+    uint32_t *bits = local ? sm : M;
+    for (uint64_t h = h0; h < nc; h += step) {
+        int64_t c[kMaxDim];
+        if (FROM_KEY) {
+            coords_of_id(B[h], cp, c);
+        } else {
+            const double *p = pts + (uint64_t)A[G[h]] * cp.d;
+#pragma unroll
+            for (int j = 0; j < kMaxDim; ++j)
+                if (j < cp.d) c[j] = cell_coord(p, j, cp);
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxDim; ++j) {
+            if (j < cp.d) {
+                cc[h * cp.d + j] = (int32_t)c[j];
+                uint32_t *w = &bits[(uint64_t)j * mwords + (uint64_t)(c[j] >> 5)];
+                const uint32_t bit = 1u << (c[j] & 31);
+                const uint32_t seen = local ? *w : __ldcg(w);
+                if ((seen & bit) == 0) atomicOr(w, bit);
+            }
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < mw; k += blockDim.x)
+            if (sm[k]) atomicOr(&M[k], sm[k]);
     }
 }
 
@@ -153,12 +237,7 @@ __device__ __forceinline__ void write_rec32(const double *__restrict__ pts,
     for (int j = 0; j < kMaxDim; ++j) {
         if (j < cp.d) {
             const double a = __dsub_rn(p[j], cp.gmin[j]);
-            double y = a;
-            if (cp.frame == SJ_FRAME_CELL) {
-                const int64_t c = cell_coord(p, j, cp);
-                y = __dsub_rn(a, __dmul_rn((double)(4 * (c >> 2)), cp.w));
-            }
-            r[j] = __double2float_rn(y);
+            r[j] = rec_coord(a, cp.frame == SJ_FRAME_CELL ? cell_of_offset(a, j, cp) : 0, cp);
         }
     }
     r[cp.d] = __uint_as_float(i);

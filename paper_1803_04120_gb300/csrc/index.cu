@@ -33,12 +33,29 @@ constexpr int kThreads = 256;
 
 // minmax[2j] = min over points of x_j (order key), minmax[2j+1] = max.
 // flag[0] |= 1 when a coordinate is NaN or infinite.
+// Per-dimension min / max (order keys) and the non-finite flag: each block
+// reduces its share in shared memory, then merges it with one atomic per
+// bound.  MAXD: kMaxDim, or kMaxPointDim for the points of more dimensions.
+template <int MAXD = kMaxDim>
 __global__ void __launch_bounds__(kThreads) bounds_kernel(const double *__restrict__ pts,
                                                           uint64_t n, int d,
                                                           unsigned long long *minmax,
                                                           uint32_t *flag) {
-    bounds_accumulate(pts, n, d, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                      (uint64_t)gridDim.x * blockDim.x, minmax, flag);
+    __shared__ unsigned long long s_mm[2 * MAXD];
+    __shared__ uint32_t s_flag;
+    if (threadIdx.x < 2 * MAXD) s_mm[threadIdx.x] = (threadIdx.x & 1) ? 0ULL : ~0ULL;
+    if (threadIdx.x == 0) s_flag = 0u;
+    __syncthreads();
+    bounds_accumulate<MAXD>(pts, n, d, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (uint64_t)gridDim.x * blockDim.x, s_mm, &s_flag);
+    __syncthreads();
+    if (threadIdx.x < 2 * d) {
+        if (threadIdx.x & 1)
+            atomicMax(&minmax[threadIdx.x], s_mm[threadIdx.x]);
+        else
+            atomicMin(&minmax[threadIdx.x], s_mm[threadIdx.x]);
+    }
+    if (threadIdx.x == 0 && s_flag) atomicOr(flag, s_flag);
 }
 
 __global__ void init_minmax_kernel(unsigned long long *minmax, int d, uint32_t *flag) {
@@ -61,6 +78,69 @@ __global__ void __launch_bounds__(kThreads) cell_kernel(const double *__restrict
         val[i] = atomicAdd(&count[id], 1u);
     else
         val[i] = (uint32_t)i;
+}
+
+// Linear cell id of each point, its rank inside its cell (dense count
+// table) and its FP32 record in point order (tmp, rs floats per point):
+// the offset x_j - g_min_j is computed once for the cell coordinate and
+// the record coordinate.
+__global__ void __launch_bounds__(kThreads) cell_rec_kernel(const double *__restrict__ pts,
+                                                            uint64_t n, CellParams cp, int rs,
+                                                            uint64_t *__restrict__ key,
+                                                            uint32_t *__restrict__ val,
+                                                            uint32_t *__restrict__ count,
+                                                            float *__restrict__ tmp) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *p = pts + i * cp.d;
+    float r[kMaxDim + 4];
+    uint64_t id = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxDim + 4; ++j) r[j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) {
+        if (j < cp.d) {
+            const double a = __dsub_rn(p[j], cp.gmin[j]);
+            const int64_t c = cell_of_offset(a, j, cp);
+            id += (uint64_t)c * cp.stride[j];
+            r[j] = rec_coord(a, c, cp);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j <= kMaxDim; ++j)
+        if (j == cp.d) r[j] = __uint_as_float((uint32_t)i);
+    float4 *o = reinterpret_cast<float4 *>(tmp + i * rs);
+#pragma unroll
+    for (int v = 0; v < (kMaxDim + 4) / 4; ++v)
+        if (4 * v < rs) o[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+    key[i] = id;
+    val[i] = atomicAdd(&count[id], 1u);
+}
+
+// Counting-sort scatter with the FP32 records: A[lut[id] + rank] = i, the
+// sorted key and the point's record (rs floats, a multiple of 4) alongside.
+__global__ void __launch_bounds__(kThreads) scatter_rec_kernel(const uint64_t *__restrict__ key,
+                                                               const uint32_t *__restrict__ rank,
+                                                               const uint32_t *__restrict__ lut,
+                                                               uint64_t n, const float *__restrict__ tmp,
+                                                               int rs, uint32_t *__restrict__ A,
+                                                               uint64_t *__restrict__ skey,
+                                                               float *__restrict__ rec) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t id = key[i];
+    const uint64_t pos = lut[id] + rank[i];
+    A[pos] = (uint32_t)i;
+    skey[pos] = id;
+    const float4 *src = reinterpret_cast<const float4 *>(tmp + i * rs);
+    float4 *dst = reinterpret_cast<float4 *>(rec + pos * rs);
+    float4 r[(kMaxDim + 4) / 4];
+#pragma unroll
+    for (int v = 0; v < (kMaxDim + 4) / 4; ++v)
+        if (4 * v < rs) r[v] = src[v];
+#pragma unroll
+    for (int v = 0; v < (kMaxDim + 4) / 4; ++v)
+        if (4 * v < rs) dst[v] = r[v];
 }
 
 // Counting-sort scatter: A[lut[id] + rank] = i, sorted key alongside.
@@ -102,16 +182,20 @@ __global__ void __launch_bounds__(kThreads) rle_kernel(const uint64_t *__restric
     if (k == 0) G[*n_cells] = (uint32_t)n;
 }
 
+// Cell coordinates and M_j of every non-empty cell (cells_block), grid-stride
+// over the |G| cells counted on the device.
+template <bool FROM_KEY>
 __global__ void __launch_bounds__(kThreads) cells_kernel(const double *__restrict__ pts,
                                                          const uint32_t *__restrict__ A,
                                                          const uint32_t *__restrict__ G,
+                                                         const uint64_t *__restrict__ B,
                                                          const uint32_t *__restrict__ n_cells,
                                                          CellParams cp, uint32_t mwords,
                                                          int32_t *__restrict__ cc,
                                                          uint32_t *__restrict__ M) {
-    uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= *n_cells) return;
-    cell_coords(pts + (uint64_t)A[G[h]] * cp.d, h, cp, mwords, cc, M);
+    __shared__ uint32_t sm[kCellsSmemWords];
+    cells_block<FROM_KEY>(pts, A, G, B, *n_cells, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                          (uint64_t)gridDim.x * blockDim.x, cp, mwords, cc, M, sm);
 }
 
 // FP32 record: y_j = fl32(x_j - g_min_j) for j < d, then the point id.
@@ -214,14 +298,6 @@ struct DimVals {
     double v[kMaxPointDim];
 };
 
-__global__ void __launch_bounds__(kThreads) bounds_full_kernel(const double *__restrict__ pts,
-                                                               uint64_t n, int d,
-                                                               unsigned long long *minmax,
-                                                               uint32_t *flag) {
-    bounds_accumulate<kMaxPointDim>(pts, n, d, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                    (uint64_t)gridDim.x * blockDim.x, minmax, flag);
-}
-
 // proj[i][t] = x_i[gdim[t]]: the grid dimensions of every point.
 struct GridDims {
     int v[kMaxDim];
@@ -251,6 +327,14 @@ __global__ void __launch_bounds__(kThreads) recd32_kernel(const double *__restri
 }
 
 inline unsigned grid_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// Blocks of a grid-stride kernel over n elements: enough for full occupancy
+// (eight blocks of kThreads per SM), fewer when n is small.
+inline unsigned grid_stride_blocks(uint64_t n) {
+    const uint64_t want = 8ull * (uint64_t)sm_count(-1);
+    const uint64_t need = (n + kThreads - 1) / kThreads;
+    return (unsigned)(need < want ? (need ? need : 1) : want);
+}
 
 }  // namespace
 
@@ -293,7 +377,24 @@ sj_status geometry_from_bounds(Error &err, const unsigned long long *mm, int d, 
     return SJ_OK;
 }
 
+// True when p is 8-byte aligned device (or managed) memory of the current
+// device, so that the index kernels may read it in place.
+static bool device_array_here(const void *p) {
+    if (reinterpret_cast<uintptr_t>(p) & 7u) return false;
+    cudaPointerAttributes at;
+    int dev = -1;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 void free_index(Index &ix, cudaStream_t s) {
+    if (ix.pts_borrowed) {
+        ix.pts = DevBuf();
+        ix.pts_borrowed = 0;
+    }
     DevBuf *all[] = {&ix.pts, &ix.rec32, &ix.rec64, &ix.A,          &ix.B,
                      &ix.G,   &ix.cc,    &ix.M,     &ix.lut,        &ix.items,
                      &ix.counts_dev,     &ix.ptsd,  &ix.recd32,     &ix.recd64};
@@ -312,10 +413,7 @@ sj_status bounds_of(Error &err, const double *d_pts, uint64_t n, int d, cudaStre
     unsigned long long *d_minmax = static_cast<unsigned long long *>(scratch.p);
     uint32_t *d_flag = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxDim);
     init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_flag); note_launch();
-    int blocks = 2 * sm_count(-1);
-    const uint64_t need = (n + kThreads - 1) / kThreads;
-    if ((uint64_t)blocks > need) blocks = (int)need;
-    bounds_kernel<<<blocks, kThreads, 0, s>>>(d_pts, n, d, d_minmax, d_flag); note_launch();
+    bounds_kernel<><<<grid_stride_blocks(n), kThreads, 0, s>>>(d_pts, n, d, d_minmax, d_flag); note_launch();
     unsigned long long h[2 * kMaxDim + 8];
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_minmax, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -342,25 +440,21 @@ static sj_status build_index_hd(Error &err, const double *pts_any, uint64_t n, i
     DevBuf full, proj, scratch;
     auto cleanup = [&]() { dev_free(full, s); dev_free(proj, s); dev_free(scratch, s); };
     sj_status st = SJ_OK;
-#define SJ_H(expr) do { st = (expr); if (st != SJ_OK) { cleanup(); return st; } } while (0)
-#define SJ_HC(expr) do { cudaError_t e__ = (expr); if (e__ != cudaSuccess) { set_cuda_error(err, e__, #expr, __FILE__, __LINE__); cleanup(); return err.st; } } while (0)
-    SJ_H(dev_alloc(err, full, n * d * sizeof(double), s));
-    SJ_HC(cudaMemcpyAsync(full.p, pts_any, n * d * sizeof(double), cudaMemcpyDefault, s));
+#define SJ_HDT(expr) do { st = (expr); if (st != SJ_OK) { cleanup(); return st; } } while (0)
+#define SJ_HDC(expr) do { cudaError_t e__ = (expr); if (e__ != cudaSuccess) { set_cuda_error(err, e__, #expr, __FILE__, __LINE__); cleanup(); return err.st; } } while (0)
+    SJ_HDT(dev_alloc(err, full, n * d * sizeof(double), s));
+    SJ_HDC(cudaMemcpyAsync(full.p, pts_any, n * d * sizeof(double), cudaMemcpyDefault, s));
     const double *pts = static_cast<const double *>(full.p);
-    SJ_H(dev_alloc(err, scratch, (2 * kMaxPointDim) * sizeof(unsigned long long) + 64, s));
+    SJ_HDT(dev_alloc(err, scratch, (2 * kMaxPointDim) * sizeof(unsigned long long) + 64, s));
     unsigned long long *d_minmax = static_cast<unsigned long long *>(scratch.p);
     uint32_t *d_flag = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxPointDim);
     init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_flag); note_launch();
-    {
-        int blocks = 2 * sm_count(-1);
-        const uint64_t need = (n + kThreads - 1) / kThreads;
-        if ((uint64_t)blocks > need) blocks = (int)need;
-        bounds_full_kernel<<<blocks, kThreads, 0, s>>>(pts, n, d, d_minmax, d_flag); note_launch();
-    }
-    SJ_HC(cudaGetLastError());
+    bounds_kernel<kMaxPointDim><<<grid_stride_blocks(n), kThreads, 0, s>>>(pts, n, d, d_minmax, d_flag);
+    note_launch();
+    SJ_HDC(cudaGetLastError());
     unsigned long long h[2 * kMaxPointDim + 8];
-    SJ_HC(cudaMemcpyAsync(h, d_minmax, sizeof(h), cudaMemcpyDeviceToHost, s));
-    SJ_HC(cudaStreamSynchronize(s));
+    SJ_HDC(cudaMemcpyAsync(h, d_minmax, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SJ_HDC(cudaStreamSynchronize(s));
     if (reinterpret_cast<const uint32_t *>(h + 2 * kMaxPointDim)[0] & 1u) {
         cleanup();
         return fail(err, SJ_EINVAL, "non-finite coordinate");
@@ -389,10 +483,10 @@ static sj_status build_index_hd(Error &err, const double *pts_any, uint64_t n, i
         mm[2 * t] = h[2 * gd.v[t]];
         mm[2 * t + 1] = h[2 * gd.v[t] + 1];
     }
-    SJ_H(dev_alloc(err, proj, n * k * sizeof(double), s));
+    SJ_HDT(dev_alloc(err, proj, n * k * sizeof(double), s));
     project_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, d, k, gd, static_cast<double *>(proj.p));
     note_launch();
-    SJ_HC(cudaGetLastError());
+    SJ_HDC(cudaGetLastError());
     Index inner;
     st = build_index(err, static_cast<const double *>(proj.p), n, k, eps, lookup_mode, SJ_FRAME_GRID,
                      s, inner, mm);
@@ -432,14 +526,14 @@ static sj_status build_index_hd(Error &err, const double *pts_any, uint64_t n, i
     g.fp32_ok = fp32_margin_diff(d, eps, fmin, fmax, &g.lo32, &g.hi32) ? 1 : 0;  // margin.cu
     g.frame = SJ_FRAME_GRID;
     ix.bytes += ix.ptsd.bytes + ix.recd32.bytes;
-#undef SJ_H
-#undef SJ_HC
+#undef SJ_HDT
+#undef SJ_HDC
     return SJ_OK;
 }
 
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
                       int lookup_mode, int frame_mode, cudaStream_t s, Index &ix,
-                      const unsigned long long *given_mm) {
+                      const unsigned long long *given_mm, const BuildOpts *opt) {
     if (d > kMaxDim && d <= kMaxPointDim && !given_mm && pts_any && n && eps > 0.0 &&
         std::isfinite(eps))
         return build_index_hd(err, pts_any, n, d, eps, lookup_mode, s, ix);
@@ -455,9 +549,15 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     g.E2 = eps * eps;
     g.w = eps * (1.0 + std::ldexp(1.0, -16));
 
-    // 1. points to the device (the index keeps its own copy)
-    SJ_TRY(dev_alloc(err, ix.pts, n * d * sizeof(double), s));
-    SJ_CUDA_TRY(cudaMemcpyAsync(ix.pts.p, pts_any, n * d * sizeof(double), cudaMemcpyDefault, s));
+    // 1. points on the device: the caller's array when it may be borrowed,
+    // else a copy the index owns
+    if (opt && opt->borrow_pts && device_array_here(pts_any)) {
+        ix.pts.p = const_cast<double *>(pts_any);
+        ix.pts_borrowed = 1;
+    } else {
+        SJ_TRY(dev_alloc(err, ix.pts, n * d * sizeof(double), s));
+        SJ_CUDA_TRY(cudaMemcpyAsync(ix.pts.p, pts_any, n * d * sizeof(double), cudaMemcpyDefault, s));
+    }
     const double *pts = static_cast<const double *>(ix.pts.p);
 
     // bounds
@@ -472,12 +572,7 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
         for (int k = 0; k < 2 * kMaxDim; ++k) h_mm[k] = given_mm[k];
     } else {
         init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_counts); note_launch();
-        {
-            int blocks = 2 * sm_count(-1);
-            uint64_t need = (n + kThreads - 1) / kThreads;
-            if ((uint64_t)blocks > need) blocks = (int)need;
-            bounds_kernel<<<blocks, kThreads, 0, s>>>(pts, n, d, d_minmax, d_counts); note_launch();
-        }
+        bounds_kernel<><<<grid_stride_blocks(n), kThreads, 0, s>>>(pts, n, d, d_minmax, d_counts); note_launch();
         SJ_CUDA_TRY(cudaGetLastError());
         SJ_CUDA_TRY(cudaMemcpyAsync(h_mm, d_minmax, sizeof(h_mm), cudaMemcpyDeviceToHost, s));
         SJ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -502,10 +597,12 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
 
     const CellParams cp = cell_params(g);
 
-    DevBuf key, val, skey_buf, head;
+    ix.rs32 = (d + 1 + 3) / 4 * 4;
+    ix.rs64 = (d + 1 + 1) / 2 * 2;
+    DevBuf key, val, skey_buf, head, rtmp;
     auto cleanup = [&]() {
         dev_free(key, s); dev_free(val, s); dev_free(skey_buf, s); dev_free(head, s);
-        dev_free(scratch, s);
+        dev_free(rtmp, s); dev_free(scratch, s);
     };
     sj_status st = SJ_OK;
 #define SJ_B(expr) do { st = (expr); if (st != SJ_OK) { cleanup(); return st; } } while (0)
@@ -518,16 +615,23 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
         SJ_B(dev_alloc(err, ix.lut, (g.grid_cells + 1) * sizeof(uint32_t), s));
         uint32_t *lut = static_cast<uint32_t *>(ix.lut.p);
         SJ_BC(cudaMemsetAsync(lut, 0, (g.grid_cells + 1) * sizeof(uint32_t), s));
-        cell_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, cp, static_cast<uint64_t *>(key.p),
-                                                     static_cast<uint32_t *>(val.p), lut); note_launch();
+        // the FP32 records are written in point order by the cell pass and
+        // moved to cell order by the scatter
+        SJ_B(dev_alloc(err, rtmp, n * ix.rs32 * sizeof(float), s));
+        SJ_B(dev_alloc(err, ix.rec32, n * ix.rs32 * sizeof(float), s));
+        cell_rec_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, n, cp, ix.rs32, static_cast<uint64_t *>(key.p),
+                                                         static_cast<uint32_t *>(val.p), lut,
+                                                         static_cast<float *>(rtmp.p)); note_launch();
         SJ_BC(cudaGetLastError());
         SJ_B(exclusive_scan_u32(err, lut, lut, g.grid_cells + 1, d_counts + 3, s));
         SJ_B(dev_alloc(err, skey_buf, n * sizeof(uint64_t), s));
         skey = static_cast<uint64_t *>(skey_buf.p);
-        scatter_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(key.p),
-                                                        static_cast<uint32_t *>(val.p), lut, n,
-                                                        static_cast<uint32_t *>(ix.A.p), skey); note_launch();
+        scatter_rec_kernel<<<grid_for(n), kThreads, 0, s>>>(
+            static_cast<uint64_t *>(key.p), static_cast<uint32_t *>(val.p), lut, n,
+            static_cast<const float *>(rtmp.p), ix.rs32, static_cast<uint32_t *>(ix.A.p), skey,
+            static_cast<float *>(ix.rec32.p)); note_launch();
         SJ_BC(cudaGetLastError());
+        dev_free(rtmp, s);
     } else if (tuple) {
         uint32_t *v = static_cast<uint32_t *>(val.p);
         iota_kernel<<<grid_for(n), kThreads, 0, s>>>(v, n); note_launch();
@@ -589,6 +693,12 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     }
     note_launch();
     SJ_BC(cudaGetLastError());
+    if (opt && opt->h_counts && opt->ev_counts) {
+        SJ_BC(cudaMemcpyAsync(opt->h_counts, d_counts, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SJ_BC(cudaEventRecord(opt->ev_counts, s));
+        ix.early_counts = opt->h_counts;
+        ix.early_ev = opt->ev_counts;
+    }
 
     // 5. cell coordinates and M_j
     uint64_t maxng = 1;
@@ -597,19 +707,24 @@ sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, doub
     SJ_B(dev_alloc(err, ix.cc, n * d * sizeof(int32_t), s));
     SJ_B(dev_alloc(err, ix.M, (uint64_t)d * ix.mwords * sizeof(uint32_t), s));
     SJ_BC(cudaMemsetAsync(ix.M.p, 0, (uint64_t)d * ix.mwords * sizeof(uint32_t), s));
-    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, static_cast<const uint32_t *>(ix.A.p),
-                                                  static_cast<const uint32_t *>(ix.G.p), d_counts + 1, cp,
-                                                  ix.mwords, static_cast<int32_t *>(ix.cc.p),
-                                                  static_cast<uint32_t *>(ix.M.p)); note_launch();
+    if (tuple)
+        cells_kernel<false><<<grid_stride_blocks(n), kThreads, 0, s>>>(
+            pts, static_cast<const uint32_t *>(ix.A.p), static_cast<const uint32_t *>(ix.G.p), nullptr,
+            d_counts + 1, cp, ix.mwords, static_cast<int32_t *>(ix.cc.p), static_cast<uint32_t *>(ix.M.p));
+    else
+        cells_kernel<true><<<grid_stride_blocks(n), kThreads, 0, s>>>(
+            pts, nullptr, nullptr, static_cast<const uint64_t *>(ix.B.p), d_counts + 1, cp, ix.mwords,
+            static_cast<int32_t *>(ix.cc.p), static_cast<uint32_t *>(ix.M.p));
+    note_launch();
     SJ_BC(cudaGetLastError());
 
-    // 6. FP32 records
-    ix.rs32 = (d + 1 + 3) / 4 * 4;
-    ix.rs64 = (d + 1 + 1) / 2 * 2;
-    SJ_B(dev_alloc(err, ix.rec32, n * ix.rs32 * sizeof(float), s));
-    rec32_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, static_cast<uint32_t *>(ix.A.p), n, cp,
-                                                  ix.rs32, static_cast<float *>(ix.rec32.p)); note_launch();
-    SJ_BC(cudaGetLastError());
+    // 6. FP32 records (already in place on the dense path)
+    if (!ix.rec32.p) {
+        SJ_B(dev_alloc(err, ix.rec32, n * ix.rs32 * sizeof(float), s));
+        rec32_kernel<<<grid_for(n), kThreads, 0, s>>>(pts, static_cast<uint32_t *>(ix.A.p), n, cp,
+                                                      ix.rs32, static_cast<float *>(ix.rec32.p)); note_launch();
+        SJ_BC(cudaGetLastError());
+    }
 
     // 7. work items
     uint32_t *icnt = static_cast<uint32_t *>(val.p);  // reuse: n entries
@@ -717,12 +832,7 @@ sj_status build_index_static(Error &err, const double *d_pts, uint64_t n, int d,
     uint32_t *d_counts = reinterpret_cast<uint32_t *>(d_minmax + 2 * kMaxDim);
     SJ_CUDA_TRY(cudaMemsetAsync(d_counts, 0, 64, s));
     init_minmax_kernel<<<1, 32, 0, s>>>(d_minmax, d, d_counts); note_launch();
-    {
-        int blocks = 2 * sm_count(-1);
-        const uint64_t need = (n + kThreads - 1) / kThreads;
-        if ((uint64_t)blocks > need) blocks = (int)need;
-        bounds_kernel<<<blocks, kThreads, 0, s>>>(d_pts, n, d, d_minmax, d_counts); note_launch();
-    }
+    bounds_kernel<><<<grid_stride_blocks(n), kThreads, 0, s>>>(d_pts, n, d, d_minmax, d_counts); note_launch();
     SJ_CUDA_TRY(cudaGetLastError());
     unsigned long long h_mm[2 * kMaxDim + 8];
     SJ_CUDA_TRY(cudaMemcpyAsync(h_mm, d_minmax, sizeof(h_mm), cudaMemcpyDeviceToHost, s));
@@ -791,10 +901,9 @@ sj_status build_index_static(Error &err, const double *d_pts, uint64_t n, int d,
     rle_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<uint64_t *>(skey.p), hs, n, d_counts + 1,
                                                  static_cast<uint64_t *>(ix.B.p),
                                                  static_cast<uint32_t *>(ix.G.p)); note_launch();
-    cells_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, static_cast<const uint32_t *>(ix.A.p),
-                                                  static_cast<const uint32_t *>(ix.G.p), d_counts + 1, cp,
-                                                  ix.mwords, static_cast<int32_t *>(ix.cc.p),
-                                                  static_cast<uint32_t *>(ix.M.p)); note_launch();
+    cells_kernel<true><<<grid_stride_blocks(n), kThreads, 0, s>>>(
+        d_pts, nullptr, nullptr, static_cast<const uint64_t *>(ix.B.p), d_counts + 1, cp, ix.mwords,
+        static_cast<int32_t *>(ix.cc.p), static_cast<uint32_t *>(ix.M.p)); note_launch();
     rec32_kernel<<<grid_for(n), kThreads, 0, s>>>(d_pts, static_cast<uint32_t *>(ix.A.p), n, cp,
                                                   ix.rs32, static_cast<float *>(ix.rec32.p)); note_launch();
     if (ix.rec64.p) {

@@ -106,7 +106,8 @@ struct Index {
     uint32_t n_items = 0;          // work items (cell, query block)
     uint32_t max_cell = 0;         // largest cell population
     int rs32 = 0, rs64 = 0;        // record strides (floats / doubles)
-    DevBuf pts;                    // n x d FP64 input copy (row-major)
+    DevBuf pts;                    // n x d FP64 input (row-major): a copy, or the caller's array
+    int pts_borrowed = 0;          // pts is the caller's device array (not freed with the index)
     DevBuf rec32;                  // cell-ordered FP32 records: y_0..y_{d-1}, id
     DevBuf rec64;                  // cell-ordered FP64 records: x_0..x_{d-1}, id
     DevBuf A;                      // u32[n] point ids in cell order
@@ -119,6 +120,10 @@ struct Index {
     DevBuf counts_dev;             // device counters: bounds, |G|, work items
     uint32_t mwords = 0;
     int counts_read = 0;
+    // build counters copied to pinned host memory mid-build (BuildOpts):
+    // valid once early_ev has completed; [1] = |G|
+    const uint32_t *early_counts = nullptr;
+    cudaEvent_t early_ev = nullptr;
     uint64_t bytes = 0;
     cudaStream_t owner_stream = nullptr;
     // Points of more than kMaxDim dimensions: the grid (g, and every array
@@ -146,12 +151,26 @@ bool fp32_margin_diff(int d, double eps, const double *fmin, const double *fmax,
 // fp32_ok.
 void fp32_margin(Geometry &g, int frame_mode);
 
+// Options of build_index.
+struct BuildOpts {
+    // when the points are device memory of the current device, the index
+    // reads them in place instead of copying them; only for indexes freed
+    // before the caller's array may change (within one synchronous call)
+    bool borrow_pts = false;
+    // when set: the build counters (4 uint32, [1] = |G|) are copied to this
+    // pinned host memory as soon as |G| is known and ev_counts is recorded
+    // after the copy, so that the host can choose launch parameters while
+    // the rest of the index builds (Index::early_counts)
+    uint32_t *h_counts = nullptr;
+    cudaEvent_t ev_counts = nullptr;
+};
+
 // given_mm: per-dimension bounds (order keys, min/max interleaved) of a grid
 // shared with another point set; null to bound the points themselves.
 // frame_mode: the sj_frame of the FP32 records (SJ_FRAME_AUTO chooses).
 sj_status build_index(Error &err, const double *pts_any, uint64_t n, int d, double eps,
                       int lookup_mode, int frame_mode, cudaStream_t s, Index &ix,
-                      const unsigned long long *given_mm = nullptr);
+                      const unsigned long long *given_mm = nullptr, const BuildOpts *opt = nullptr);
 // Per-dimension min/max (order keys) of device points and a non-finite flag
 // (synchronises s).
 sj_status bounds_of(Error &err, const double *d_pts, uint64_t n, int d, cudaStream_t s,
@@ -277,13 +296,13 @@ sj_status shard_items(Error &err, const Index &ix, bool uni, int rank, int world
 // Launch tuner (tune.cu): on a miss times sampled count-only launches of ix
 // and stores the fastest (grab, ring depth, warps per block) for the key
 // (d, precision, UNICOMP, points-per-cell bucket); *tuned = 0 defaults kept,
-// 1 taken from the cache, 2 tuned now.  ix.n_items and ix.n_cells must be
-// known on the host.
+// 1 taken from the cache, 2 tuned now.  ix.n_cells must be known on the
+// host; a miss reads the work-item count first (read_counts).
 int tune_bucket(const Index &ix);
 int tune_bucket_ppc(double points_per_cell);
 // Smallest join (work items) the tuner times; smaller joins keep the defaults.
 constexpr uint32_t kTuneMinItems = 4096;
-sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned);
+sj_status tune_launch(Error &err, Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned);
 void tune_clear();
 // The multi-join kernel (join.cu): void(const MultiJobs).
 const void *multi_join_fn();
@@ -345,7 +364,8 @@ struct sj_ctx {
     int device = 0;
     cudaStream_t s_main = nullptr, s_copy = nullptr;
     sj::DevBuf misc;                         // join counters, work cursor, error word
-    unsigned long long *h_misc = nullptr;    // pinned read-back
+    unsigned long long *h_misc = nullptr;    // pinned read-back (64 words)
+    cudaEvent_t ev_counts = nullptr;         // build counters copied to h_misc (BuildOpts)
     std::string last_err;
     sj_stats stats;
     double t0 = 0;

@@ -49,7 +49,7 @@ int tune_bucket(const Index &ix) {
     return tune_bucket_ppc(ix.n_cells ? (double)ix.g.n / (double)ix.n_cells : 1.0);
 }
 
-sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned) {
+sj_status tune_launch(Error &err, Index &ix, JoinLaunch &l, cudaStream_t s, int *tuned) {
     *tuned = 0;
     const bool f32 = l.prec_fp32 && ix.g.fp32_ok;
     const auto key = std::make_tuple(ix.g.d, f32 ? 1 : 0, l.unicomp ? 1 : 0, tune_bucket(ix));
@@ -66,6 +66,7 @@ sj_status tune_launch(Error &err, const Index &ix, JoinLaunch &l, cudaStream_t s
             return SJ_OK;
         }
     }
+    SJ_TRY(read_counts(err, ix, s));   // a miss needs the work-item count
     if (ix.n_items < kTuneMinItems) return SJ_OK;
     DevBuf misc;
     SJ_TRY(dev_alloc(err, misc, 64, s));
