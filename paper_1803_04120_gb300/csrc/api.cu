@@ -291,17 +291,24 @@ sj_status join_once(Error &err, sj_ctx *ctx, const Index &ix, uint32_t ib, uint3
     return SJ_OK;
 }
 
+// Sampled work items of the first pair-count estimate (one segment), and of
+// the estimate by segments that follows when the result needs more than
+// the minimum number of batches.  A sampled launch is latency-bound (a few
+// items per warp), so its time grows slowly with the sample.
+constexpr uint32_t kEstimateSamples = 4096;
+constexpr uint32_t kSegmentSamples = 16384;
+
 // Pair-count estimates of S equal segments of the work items, each from a
-// systematic sample (every stride-th item, about 16384 sampled items in
+// systematic sample (every stride-th item, about `samples` sampled items in
 // all): the S count-only launches run back to back on s, each into its
 // own counters, with one read-back at the end.  Pair density varies along
 // the cell order (cells at the boundary of the data have fewer
 // neighbours), so the batches are later cut at equal estimated pairs, not
 // at equal item counts.
 sj_status estimate_segments(Error &err, sj_ctx *ctx, const Index &ix, cudaStream_t s, uint32_t S,
-                            std::vector<double> &seg) {
+                            uint32_t samples, std::vector<double> &seg) {
     const uint32_t ni = ix.n_items;
-    const uint32_t stride = ni > 16384 ? ni / 16384 : 1;
+    const uint32_t stride = ni > samples ? ni / samples : 1;
     seg.assign(S, 0.0);
     DevBuf ctr;
     SJ_TRY(dev_alloc(err, ctr, (size_t)S * 4 * sizeof(unsigned long long), s));
@@ -385,11 +392,11 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     // density along the cell order, each still sampling about 256 items or
     // more) to cut the batches at equal estimated pairs
     std::vector<double> seg;
-    SJ_TRY(estimate_segments(err, ctx, ix, s, 1, seg));
+    SJ_TRY(estimate_segments(err, ctx, ix, s, 1, kEstimateSamples, seg));
     uint32_t S = 1;
     if (batches_for((uint64_t)seg[0]) > min_nb) {
         S = std::max<uint32_t>(1, std::min<uint32_t>(64, ni / 4096));
-        if (S > 1) SJ_TRY(estimate_segments(err, ctx, ix, s, S, seg));
+        if (S > 1) SJ_TRY(estimate_segments(err, ctx, ix, s, S, kSegmentSamples, seg));
     }
     double est_d = 0;
     for (double v : seg) est_d += v;
@@ -398,23 +405,24 @@ sj_status run_batches(Error &err, sj_ctx *ctx, Index &ix, HostSink &sink) {
     const uint64_t padded = est + est / 8 + 4096;
     const uint64_t nb_eq = batches_for(est);
     uint64_t bufcap = std::min<uint64_t>(bufcap_max, padded / nb_eq + padded / (4 * nb_eq) + 65536);
-    // Batch 0's kernel overlaps no copy, while every later batch's kernel
-    // overlaps the copy of the one before: a small first batch (1/16 of the
-    // estimated pairs, or less) leaves little of the join exposed, and the
-    // rest is cut into nb_eq batches of equal estimated pairs.  Batch b
-    // covers items [cut[b], cut[b+1]); the cumulative estimate is
-    // interpolated linearly inside a segment.
-    const bool lead = nb_eq >= 2 && ni >= 2 * nb_eq + 2;
-    const uint64_t nb = nb_eq + (lead ? 1 : 0);
-    const double f0 = lead ? std::min(1.0 / 16.0, 0.5 / (double)nb_eq) : 0.0;
+    // Batch 0's kernel overlaps no copy, and the last batch's copy overlaps
+    // no kernel, while every other batch's kernel overlaps the copy of the
+    // one before: a small first and a small last batch (1/16 of the
+    // estimated pairs each, or less) leave little of the join or of the
+    // copies exposed, and the rest is cut into nb_eq batches of equal
+    // estimated pairs.  Batch b covers items [cut[b], cut[b+1]); the
+    // cumulative estimate is interpolated linearly inside a segment.
+    const bool edges = nb_eq >= 2 && ni >= 2 * nb_eq + 4;
+    const uint64_t nb = nb_eq + (edges ? 2 : 0);
+    const double f0 = edges ? std::min(1.0 / 16.0, 0.5 / (double)nb_eq) : 0.0;
     std::vector<uint32_t> cut(nb + 1, 0);
     cut[nb] = ni;
     {
         double acc = 0;
         uint32_t q = 0;
         for (uint64_t b = 1; b < nb; ++b) {
-            const double frac = lead ? f0 + (1.0 - f0) * (double)(b - 1) / (double)nb_eq
-                                     : (double)b / (double)nb;
+            const double frac = edges ? f0 + (1.0 - 2.0 * f0) * (double)(b - 1) / (double)nb_eq
+                                      : (double)b / (double)nb;
             const double target = est_d * frac;
             while (q < S && acc + seg[q] < target) acc += seg[q++];
             uint32_t x;
