@@ -63,8 +63,11 @@ namespace {
 // The kernel is latency-bound (dependent shared-memory loads and ALU chains
 // per warp), so the per-warp shared memory and registers are sized for
 // resident warps: measured on GB300 with 2,000,000 uniform points.
-// Candidates per lane by dimension and precision (chunk = 32 * CPL).
-__host__ __device__ constexpr int cpl_for(int d, bool f32) { return f32 ? (d <= 3 ? 2 : 4) : 2; }
+// Candidates per lane by dimension and precision (chunk = 32 * CPL): four
+// at d >= 5, where each chunk's loads are shared by the most comparisons;
+// two below, where the smaller registers and ring let three blocks reside
+// (d = 4: 1.28 ms against 1.35 ms with four; d = 5: 2.63 against 2.41).
+__host__ __device__ constexpr int cpl_for(int d, bool f32) { return f32 ? (d <= 4 ? 2 : 4) : 2; }
 // Default depth of the chunk ring (a launch may choose another).
 __host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >= 4) ? 2 : 4; }
 // Staged pairs per warp: many pairs per chunk at low d want a large staging
@@ -77,7 +80,7 @@ __host__ __device__ constexpr int emit_for(int d, bool f32) { return (f32 && d >
 // more as resident warps.
 __host__ __device__ constexpr int slots_for(int d, bool f32) { return (f32 && d >= 4) ? 1 : 2; }
 // Minimum resident blocks of 256 threads the compiler sizes registers for.
-__host__ __device__ constexpr int minb_for(int d, bool f32) { return f32 ? (d <= 2 ? 1 : (d == 3 ? 3 : 2)) : 1; }
+__host__ __device__ constexpr int minb_for(int d, bool f32) { return f32 ? (d <= 2 ? 1 : (d <= 4 ? 3 : 2)) : 1; }
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -234,7 +237,7 @@ __device__ __forceinline__ void flush(Pipe &st, const WarpSmem &ws, const JoinAr
     if (!a.count_only) {
         for (uint32_t i = lane; i < st.fill; i += 32) {
             const uint64_t pos = base + i;
-            if (pos < a.cap) a.out[pos] = ws.emit[i];
+            if (pos < a.cap) __stcs(&a.out[pos], ws.emit[i]);
         }
     }
     __syncwarp();
@@ -520,8 +523,15 @@ __device__ __forceinline__ void put_hits(uint32_t (&m)[CPL], const uint32_t (&ci
         const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, q);
         if (act) {
             const uint64_t pos = base + __popc(bm & lt);
-            if (!GLOBAL || pos < cap) dst[pos] = make_uint2(qid, cand);
-            if (UNI && (!GLOBAL || pos + nb < cap)) dst[pos + nb] = make_uint2(cand, qid);
+            if (GLOBAL) {
+                // streaming stores: the pairs are never read back, so they
+                // should not displace the candidate records from L2
+                if (pos < cap) __stcs(&dst[pos], make_uint2(qid, cand));
+                if (UNI && pos + nb < cap) __stcs(&dst[pos + nb], make_uint2(cand, qid));
+            } else {
+                dst[pos] = make_uint2(qid, cand);
+                if (UNI) dst[pos + nb] = make_uint2(cand, qid);
+            }
         }
         base += kPP * nb;
     }
