@@ -127,19 +127,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
             const uint2 rg = rt[ri];
             const uint32_t len = rg.y - kstart;
             if (F32) {
-                // two candidates per lane (p and p + 32), packed as f32x2
+                // two candidates per lane (p and p + 32), packed as f32x2;
+                // a slot past the range holds coordinates far outside the
+                // data (every sum overflows to +inf: never a hit), so the
+                // comparison needs no per-query validity test
                 for (uint32_t p0 = 0; p0 < len; p0 += 64) {
                     uint32_t cid[2] = {0xffffffffu, 0xffffffffu}, kp[2];
-                    bool valid[2];
                     float4 y4[2][G4];
 #pragma unroll
                     for (int h2 = 0; h2 < 2; ++h2) {
                         const uint32_t p = p0 + 32 * h2 + lane;
-                        valid[h2] = p < len;
                         kp[h2] = kstart + p;
+                        const float far = p < len ? 0.0f : 3.0e38f;
 #pragma unroll
-                        for (int g = 0; g < G4; ++g) y4[h2][g] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (valid[h2]) {
+                        for (int g = 0; g < G4; ++g) y4[h2][g] = make_float4(far, far, far, far);
+                        if (p < len) {
                             const float *r = a.recd32 + (size_t)(rg.x + p) * rs;
 #pragma unroll
                             for (int g = 0; g < G4; ++g) y4[h2][g] = *reinterpret_cast<const float4 *>(r + 4 * g);
@@ -158,7 +160,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                     }
                     const f2_t neg1 = f2_pack(-1.0f, -1.0f);
                     for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
                         const ulonglong2 *qd =
                             reinterpret_cast<const ulonglong2 *>(reinterpret_cast<const f2_t *>(qs) + (size_t)qi * DW);
                         // two running fma sums, even and odd coordinates,
@@ -176,12 +177,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                         }
                         float sv[2];
                         f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
+                        // hits are rare (a few in 1e4 comparisons at 16-D):
+                        // one vote per query, then the UNICOMP home-cell
+                        // rule (only candidates after the query), the band
+                        // rechecks and the writes in that rare branch
+                        if (!__any_sync(0xffffffffu, sv[0] <= a.hi32 || sv[1] <= a.hi32)) continue;
+                        const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
                         bool hit[2], band[2];
 #pragma unroll
                         for (int h2 = 0; h2 < 2; ++h2) {
-                            // in the home cell under UNICOMP only candidates after the query
-                            const bool cand =
-                                valid[h2] && (!UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi);
+                            const bool cand = !UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi;
                             hit[h2] = cand && sv[h2] <= a.hi32;
                             band[h2] = hit[h2] && !(sv[h2] <= a.lo32);
                         }
