@@ -121,6 +121,17 @@ def fp32_rate(dev: int):
             "packed_ms": round(pk_ms, 3), "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")}
 
 
+def fp64_rate(dev: int):
+    """FP64 fused multiply-add rate of the GPU (library kernel, CUDA events),
+    the denominator of the plain FP64 join's roofline; None on failure."""
+    from paper_1803_04120_gb300 import sj
+    try:
+        tf, ms = sj.sj_fp64_fma_rate(dev)
+    except Exception:
+        return None
+    return {"tflops": round(tf, 3), "ms": round(ms, 3)}
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
 
@@ -629,7 +640,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     d_pts = [torch.from_numpy(p).cuda() for _, p in data]
     ctx32 = [sj.Context(prec=sj.SJ_PREC_FP32_RECHECK, device=dev, profile=True) for _ in DIMS]
-    ctx64 = sj.Context(prec=sj.SJ_PREC_FP64, device=dev)
+    ctx64 = [sj.Context(prec=sj.SJ_PREC_FP64, device=dev, profile=True) for _ in DIMS]
     counts = [c.sj_selfjoin_count(p, cfg["eps"]) for c, p, (cfg, _) in zip(ctx32, d_pts, data)]
     outs = [torch.empty((c, 2), dtype=torch.int32, device="cuda") for c in counts]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -677,8 +688,9 @@ def run_gpu(args):
     value = pairs_step / (ms_step / 1e3)
 
     # plain FP64 join, same inputs, fewer steps (it is much slower)
-    t64, _ = timed([ctx64] * len(DIMS), max(1, min(args.steps, 2)), 1)
+    t64, _ = timed(ctx64, max(1, min(args.steps, 2)), 1)
     fp64_value = pairs_step / (sum(t64) / len(t64) / 1e3)
+    prof64 = [c.sj_profile_read() for c in ctx64]
 
     # end to end: host points in, host pairs out, through sj_selfjoin
     host_pts = [torch.from_numpy(p).pin_memory() for _, p in data]
@@ -722,6 +734,19 @@ def run_gpu(args):
                              frac=round(ach / pk, 4), kernel_ms=round(t * 1e3, 4),
                              roofline_ms=round(max(t_alu, t_hbm) * 1e3, 4),
                              evaluations=st["evaluations"], pairs=cnt, rechecks=st["rechecks"]))
+    # the plain FP64 join against the measured FP64 FMA rate: its exact
+    # predicate is d subtractions, d multiplications and d - 1 additions per
+    # evaluation, none fused, so it can reach at most half of the FMA rate
+    f64 = fp64_rate(dev)
+    roof64 = []
+    for (cfg, pts), (ms, nl), st in zip(data, prof64, stats):
+        d = cfg["d"]
+        t = ms / max(nl, 1) / 1e3
+        flops = (3 * d - 1) * st["evaluations"]
+        ach = flops / t / 1e12
+        roof64.append(dict(d=d, kernel_ms=round(t * 1e3, 4), achieved=round(ach, 4),
+                           peak=f64["tflops"] if f64 else None, unit="TFLOP/s",
+                           frac=round(ach / f64["tflops"], 4) if f64 else None))
     dom = max(roof_all, key=lambda r: r["kernel_ms"])
     roofline = dict(bound=dom["bound"], achieved=dom["achieved"], peak=dom["peak"], unit=dom["unit"],
                     frac=dom["frac"], traffic=profiled_traffic(dom["d"]),
@@ -742,7 +767,11 @@ def run_gpu(args):
         "data": DATA, "config": bench_config(data), "pairs_per_step": pairs_step,
         "precision": "FP32 filter with proven margin + FP64 recheck (exact set), UNICOMP",
         "fp64": {"value": round(fp64_value, 1), "unit": UNIT,
-                 "ms_per_step": round(sum(t64) / len(t64), 4), "speedup_fp32": round(value / fp64_value, 2)},
+                 "ms_per_step": round(sum(t64) / len(t64), 4), "speedup_fp32": round(value / fp64_value, 2),
+                 "roofline_all": roof64,
+                 "peak_source": "measured: FP64 FMA chains on every SM (sj_fp64_fma_rate); "
+                                "the join's unfused FP64 operations can reach at most half of it",
+                 "fp64_peak": f64},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 8 * pairs_step, "steps": len(e2e_times),
                 "statistic": "median step time", "value_mean": round(e2e_mean, 1)},
@@ -752,9 +781,8 @@ def run_gpu(args):
         "fp32_peak": dict(fma or {}, derived_tflops=round(fp32_derived, 1)),
         "clocks": clocks,
     }
-    for c in ctx32:
+    for c in ctx32 + ctx64:
         c.close()
-    ctx64.close()
     del outs
     torch.cuda.empty_cache()
     if not args.no_stream:

@@ -289,6 +289,14 @@ SJ_API sj_status sj_fp32_margin_diff(int d, double eps, const double *fmin,
  * SJ_ECUDA when the device or a launch fails. */
 SJ_API sj_status sj_fp32_fma_rate(int device, int packed, double *tflops, double *ms);
 
+/* Measured FP64 rate of this GPU, the denominator of the plain FP64 join's
+ * roofline (the paper has no counterpart).  Independent fma.rn.f64 chains
+ * on every SM of `device` at full occupancy, the best of five timed
+ * launches: *tflops counts two FLOPs per FMA, *ms is that launch's time.
+ * Allocates a small device buffer and a stream for the call.  Errors as
+ * sj_fp32_fma_rate. */
+SJ_API sj_status sj_fp64_fma_rate(int device, double *tflops, double *ms);
+
 /* ------------------------------------------------------------------ */
 /* Self-join.                                                         */
 /* ------------------------------------------------------------------ */

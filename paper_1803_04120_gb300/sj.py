@@ -36,7 +36,7 @@ ABI_FUNCTIONS = (
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds", "sj_shard_bounds_cost",
     "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
-    "sj_fp32_margin_diff", "sj_fp32_fma_rate",
+    "sj_fp32_margin_diff", "sj_fp32_fma_rate", "sj_fp64_fma_rate",
 )
 
 
@@ -149,6 +149,8 @@ def load(build: bool = True):
             "sj_fp32_margin": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
             "sj_fp32_fma_rate": (i32, [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
+            "sj_fp64_fma_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin_diff": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]),
@@ -590,6 +592,17 @@ def sj_fp32_fma_rate(device: int = 0, packed: bool = True):
     st = lib.sj_fp32_fma_rate(int(device), int(bool(packed)), ctypes.byref(tf), ctypes.byref(ms))
     if st != SJ_OK:
         raise SJError(st, "sj_fp32_fma_rate failed")
+    return tf.value, ms.value
+
+
+def sj_fp64_fma_rate(device: int = 0):
+    """(TFLOP/s, ms) of FP64 fused multiply-add chains on every SM of the
+    device (two FLOPs per FMA)."""
+    lib = load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib.sj_fp64_fma_rate(int(device), ctypes.byref(tf), ctypes.byref(ms))
+    if st != SJ_OK:
+        raise SJError(st, "sj_fp64_fma_rate failed")
     return tf.value, ms.value
 
 
