@@ -29,6 +29,10 @@ Printed JSON line (rank 0):
                at once (saturated) and with Poisson arrivals swept over
                0.25..1 of the saturated rate: p50/p99 latency and pairs/s,
                against requests joined one at a time through sj_selfjoin
+  frames       FP32 record frames: grid against four-cell frame
+  highdim      16-dimensional joins (uniform and clustered), FP32 against FP64
+  multi        64 joins of the serving mix in one sj_selfjoin_multi call
+               against the same joins one at a time
 --impl reference times the CPU oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -585,6 +589,67 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
 
 # ---------------------------------------------------------------- streamed 10M
 
+def multi_bench(dev: int, reps: int, n_jobs: int = 64, seed: int = 7):
+    """Many joins in one call (sj_selfjoin_multi: one batched index build and
+    one persistent multi-join launch per wave, replayed as a CUDA graph, the
+    pairs delivered to host memory) against the same joins one at a time
+    through sj_selfjoin (host pairs) and sj_selfjoin_device (pairs left on
+    the device).  Jobs: the request mix of the serving stream (n log-uniform
+    [1e3, 1e6], d uniform {2..6}, eps for U[8, 128] mean neighbours), each
+    on its own seeded uniform set."""
+    import torch
+    from paper_1803_04120_gb300 import sj
+
+    reqs = datagen.serving_requests(n_jobs, seed, rate_hz=1.0)
+    pts = [datagen.uniform(r["n"], r["d"], seed=7000 + k) for k, r in enumerate(reqs)]
+    jobs = [(p, r["eps"]) for p, r in zip(pts, reqs)]
+    with sj.Context(device=dev) as c:
+        counts = c.sj_selfjoin_multi(jobs, copy=False)          # engines, graphs, pools
+        total = sum(counts)
+        t_multi = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            got = c.sj_selfjoin_multi(jobs, copy=False)
+            t_multi.append(time.perf_counter() - t0)
+            assert got == counts
+        for p, e in jobs[:4]:                                    # warm the single-join path
+            c.sj_result_free(c.sj_selfjoin_raw(p, e))
+        t_host = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            tot = 0
+            for p, e in jobs:
+                r = c.sj_selfjoin_raw(p, e)
+                tot += c.sj_result_count(r)
+                c.sj_result_free(r)
+            t_host.append(time.perf_counter() - t0)
+            assert tot == total
+        dpts = [torch.from_numpy(p).cuda() for p in pts]
+        outs = [torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda") for k in counts]
+        t_dev = []
+        for rep in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tot = sum(c.sj_selfjoin_device(p, e, o) for p, (_, e), o in zip(dpts, jobs, outs))
+            torch.cuda.synchronize()
+            if rep:
+                t_dev.append(time.perf_counter() - t0)
+            assert tot == total
+    ms = lambda t: round(1e3 * statistics.median(t), 3)
+    return {"jobs": n_jobs, "pairs": total,
+            "points": sum(int(p.shape[0]) for p in pts),
+            "multi_host_pairs": {"ms": ms(t_multi), "pairs_per_s": round(total / statistics.median(t_multi), 1)},
+            "one_at_a_time_host_pairs": {"ms": ms(t_host),
+                                         "pairs_per_s": round(total / statistics.median(t_host), 1)},
+            "one_at_a_time_device_pairs": {"ms": ms(t_dev),
+                                           "pairs_per_s": round(total / statistics.median(t_dev), 1)},
+            "job_mix": "n log-uniform [1e3, 1e6], d uniform {2..6}, eps for U[8, 128] mean "
+                       "neighbours, uniform [0, 100]^d, one seeded set per job; host inputs are "
+                       "pageable numpy arrays for the host-pair rows",
+            "statistic": "median of %d calls" % reps}
+
+
 def stream_bench(dev: int, reps: int):
     """10,000,000 uniform points for d = 2..6 with 128 mean neighbours (about
     1.3e9 pairs each), device result buffers capped at 2 GB: the pairs stream
@@ -797,6 +862,8 @@ def run_gpu(args):
         line["frames"] = frame_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_highdim:
         line["highdim"] = highdim_bench(dev, max(1, min(args.steps, 3)))
+    if not args.no_multi:
+        line["multi"] = multi_bench(dev, max(1, min(args.steps, 3)))
     if not args.no_cpu:
         r = oracle_sample(data, oracle_build_seconds(data))
         line["cpu_baseline"] = {"value": round(r["value"], 1), "unit": UNIT, "cores": r["cores"],
@@ -867,6 +934,8 @@ def main():
                     help="skip the UNICOMP and brute-force comparisons")
     ap.add_argument("--no-frames", action="store_true",
                     help="skip the FP32 record-frame comparison")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the many-joins-in-one-call comparison")
     ap.add_argument("--no-highdim", action="store_true",
                     help="skip the 16-dimensional workloads")
     args = ap.parse_args()
