@@ -426,7 +426,8 @@ def frame_bench(dev: int, reps: int):
 
 def highdim_bench(dev: int, reps: int):
     """Points of 16 dimensions (grid over the six with the most cells, the
-    difference-form FP32 filter over all sixteen): uniform and clustered
+    FP32 filter over all sixteen: expanded form for the uniform set,
+    difference form for the clustered one): uniform and clustered
     workloads, the FP32 filter with FP64 recheck against plain FP64, pairs
     in device memory, whole call (index build included)."""
     import torch

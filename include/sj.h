@@ -269,7 +269,22 @@ SJ_API sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
                                       float *hi);
 
 /* The margin of the FP32 filter for points of more than 8 dimensions
- * (d <= 16), whose search sums fl32(y_p,j - y_q,j)^2 with fused
+ * (d <= 16) in the expanded form: the grid frame's sum |z_p|^2 + |z_q|^2
+ * - 2 z_p . z_q over all d dimensions, z_j = fl32(y_j - o_j), with the
+ * origin o_j at the home cell centre in a grid dimension (grid[j] != 0;
+ * the search covers the home cell's neighbours there) and at *mid[j] =
+ * fl32((fmax_j - fmin_j) / 2) in the others (written for j < d; 0 for grid
+ * dimensions).  y_j = fl32(fl64(x_j - fmin_j)), fmin_j = min_j - eps,
+ * fmax_j = max_j + eps (derivation in csrc/margin.cu).  s32 <= *lo implies
+ * membership, s32 > *hi non-membership.  Returns SJ_ERANGE when no useful
+ * margin exists (the search then takes the difference form below),
+ * SJ_EINVAL for bad arguments.  Host-only. */
+SJ_API sj_status sj_fp32_margin_hd(int d, double eps, const double *fmin, const double *fmax,
+                                   const int *grid, float *lo, float *hi, float *mid);
+
+/* The margin of the FP32 filter for points of more than 8 dimensions
+ * (d <= 16) in the difference form, used where the expanded form has no
+ * useful margin: the search sums fl32(y_p,j - y_q,j)^2 with fused
  * multiply-adds over all d dimensions, y_j = fl32(fl64(x_j - fmin_j)),
  * fmin_j = min_j - eps, fmax_j = max_j + eps (derivation in
  * csrc/margin.cu).  s32 <= *lo implies membership, s32 > *hi

@@ -26,12 +26,16 @@ __device__ __noinline__ bool exact_member_hd(const double *__restrict__ a,
 // queries (records of all dfull coordinates) in shared memory, and lets each
 // lane take every 32nd candidate of each range, read straight from the
 // cell-ordered records in global memory, and compare it with every query.
-// FP32: the difference-form sum against [lo32, hi32] (margin.cu), values in
-// between rechecked with the exact FP64 predicate on the input points, in a
-// warp-uniform branch; FP64: the exact predicate on the FP64 records.  Hits
-// are written after one atomic reservation per query and 32 candidates.
-// There are no waits, so no time limits.
-template <bool F32, bool UNI, int G4>
+// FP32: the expanded-form sum (EXP: |z_q|^2 + |z_p|^2 - 2 z_p . z_q about
+// an origin at the home cell centre in the grid dimensions and at the
+// middle of the data range in the others, one fma per coordinate) or the
+// difference form (two per coordinate, where the expanded form has no
+// usable margin), against [lo32, hi32] (margin.cu); values in between are
+// rechecked with the exact FP64 predicate on the input points, in a
+// warp-uniform branch.  FP64: the exact predicate on the FP64 records.
+// Hits are written after one atomic reservation per query and 32
+// candidates.  There are no waits, so no time limits.
+template <bool F32, bool UNI, int G4, bool EXP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     hd_join_kernel(const JoinArgs a, const uint32_t *counts) {
     // DW = 4 G4 >= d coordinates take part; those past d are zero on both
@@ -43,8 +47,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
     const int warp = threadIdx.x >> 5;
     unsigned char *wbase = smem + (size_t)warp * a.sm_warp;
     uint2 *rt = reinterpret_cast<uint2 *>(wbase);
-    // staged queries: DW values each, as (q, q) float pairs (FP32) or doubles
+    // staged queries (FP32): the DW floats y (difference form) or m = -2 z
+    // (expanded form) then |z|^2 and three pads, read 16 bytes per four
+    // coordinates and paired in registers (the shared-memory pipe is what
+    // limits these loops); FP64: the DW doubles
     unsigned char *qs = wbase + a.sm_ranges;
+    float *origin = reinterpret_cast<float *>(wbase + a.sm_ranges + a.sm_queries);
+    constexpr int QF = DW + 4;   // floats per staged expanded-form query
     const int dd = a.dfull, rs = a.rsd;
     const uint32_t n_cells = *a.ccells;
     uint32_t item_end = a.item_end;
@@ -91,15 +100,37 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
         uint32_t nranges, kc;
         build_ranges<K, UNI>(c, odd, a, n_cells, lane, rt, nranges, kc);
         uint32_t qid_l = 0;
+        if (EXP) {
+            // the origin: home cell centre in a grid dimension (as in the
+            // grid frame), the middle of the data range in the others
+            if (lane < DW) {
+                const int t = lane < dd ? (int)((a.hgrid4 >> (4 * lane)) & 0xfull) : 15;
+                int32_t ct = 0;
+#pragma unroll
+                for (int tt = 0; tt < K; ++tt) if (tt == t) ct = c[tt];
+                origin[lane] = t < K ? ((float)ct + 0.5f) * a.w32 : (lane < dd ? __ldg(&a.hmid[lane]) : 0.0f);
+            }
+            __syncwarp();
+        }
         if (lane < (int)nq) {
-            if (F32) {
+            if (F32 && EXP) {
                 const float *r = a.recd32 + (size_t)(q0 + lane) * rs;
-                f2_t *qd = reinterpret_cast<f2_t *>(qs) + (size_t)lane * DW;
+                float *qd = reinterpret_cast<float *>(qs) + (size_t)lane * QF;
+                float pp = 0.0f;
 #pragma unroll
                 for (int j = 0; j < DW; ++j) {
-                    const float v = j < dd ? r[j] : 0.0f;
-                    qd[j] = f2_pack(v, v);
+                    const float z = j < dd ? __fsub_rn(r[j], origin[j]) : 0.0f;
+                    pp = __fmaf_rn(z, z, pp);
+                    qd[j] = -2.0f * z;
                 }
+                qd[DW] = pp;
+                qd[DW + 1] = qd[DW + 2] = qd[DW + 3] = 0.0f;
+                qid_l = __float_as_uint(r[dd]);
+            } else if (F32) {
+                const float *r = a.recd32 + (size_t)(q0 + lane) * rs;
+                float *qd = reinterpret_cast<float *>(qs) + (size_t)lane * QF;
+#pragma unroll
+                for (int j = 0; j < DW; ++j) qd[j] = j < dd ? r[j] : 0.0f;
                 qid_l = __float_as_uint(r[dd]);
             } else {
                 const double *r = a.recd64 + (size_t)(q0 + lane) * rs;
@@ -129,8 +160,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
             if (F32) {
                 // two candidates per lane (p and p + 32), packed as f32x2;
                 // a slot past the range holds coordinates far outside the
-                // data (every sum overflows to +inf: never a hit), so the
-                // comparison needs no per-query validity test
+                // data (its sum overflows to +inf, or is NaN: never at or
+                // below hi32), so the comparison needs no per-query
+                // validity test
                 for (uint32_t p0 = 0; p0 < len; p0 += 64) {
                     uint32_t cid[2] = {0xffffffffu, 0xffffffffu}, kp[2];
                     float4 y4[2][G4];
@@ -138,7 +170,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                     for (int h2 = 0; h2 < 2; ++h2) {
                         const uint32_t p = p0 + 32 * h2 + lane;
                         kp[h2] = kstart + p;
-                        const float far = p < len ? 0.0f : 3.0e38f;
+                        const float far = p < len ? 0.0f : 1.0e30f;
 #pragma unroll
                         for (int g = 0; g < G4; ++g) y4[h2][g] = make_float4(far, far, far, far);
                         if (p < len) {
@@ -158,22 +190,77 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                         yy[j + 2] = f2_pack(j + 2 < dd ? u.z : 0.f, j + 2 < dd ? v.z : 0.f);
                         yy[j + 3] = f2_pack(j + 3 < dd ? u.w : 0.f, j + 3 < dd ? v.w : 0.f);
                     }
+                    if (EXP) {
+                        // z = fl(y - o) (exact negation, one rounding) and
+                        // |z|^2 of both candidates
+                        f2_t qq = f2_pack(0.0f, 0.0f);
+#pragma unroll
+                        for (int j = 0; j < DW; ++j) {
+                            const float no = -origin[j];
+                            yy[j] = f2_add(yy[j], f2_pack(no, no));
+                            qq = f2_fma(yy[j], yy[j], qq);
+                        }
+                        for (uint32_t qi = 0; qi < nq; ++qi) {
+                            const float4 *qd =
+                                reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(qs) + (size_t)qi * QF);
+                            // fl(qq + pp), then the m_j z_j terms in two
+                            // chains (even and odd j) added at the end
+                            const float pp = qd[G4].x;
+                            f2_t acc0 = f2_add(qq, f2_pack(pp, pp)), acc1 = f2_pack(0.0f, 0.0f);
+#pragma unroll
+                            for (int g = 0; g < G4; ++g) {
+                                const float4 m4 = qd[g];   // m_4g .. m_4g+3
+                                acc0 = f2_fma(f2_pack(m4.x, m4.x), yy[4 * g], acc0);
+                                acc1 = f2_fma(f2_pack(m4.y, m4.y), yy[4 * g + 1], acc1);
+                                acc0 = f2_fma(f2_pack(m4.z, m4.z), yy[4 * g + 2], acc0);
+                                acc1 = f2_fma(f2_pack(m4.w, m4.w), yy[4 * g + 3], acc1);
+                            }
+                            float sv[2];
+                            f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
+                            if (!__any_sync(0xffffffffu, sv[0] <= a.hi32 || sv[1] <= a.hi32)) continue;
+                            const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
+                            bool hit[2], band[2];
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                const bool cand = !UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi;
+                                hit[h2] = cand && sv[h2] <= a.hi32;
+                                band[h2] = hit[h2] && !(sv[h2] <= a.lo32);
+                            }
+                            if (__any_sync(0xffffffffu, band[0] || band[1])) {
+#pragma unroll
+                                for (int h2 = 0; h2 < 2; ++h2) {
+                                    if (band[h2]) {
+                                        hit[h2] = exact_member_hd(a.ptsd + (size_t)qid * dd,
+                                                                  a.ptsd + (size_t)cid[h2] * dd, dd, a.E2);
+                                        ++rechecks;
+                                    }
+                                }
+                            }
+                            emit(hit[0], qid, cid[0]);
+                            emit(hit[1], qid, cid[1]);
+                        }
+                        continue;
+                    }
                     const f2_t neg1 = f2_pack(-1.0f, -1.0f);
                     for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const ulonglong2 *qd =
-                            reinterpret_cast<const ulonglong2 *>(reinterpret_cast<const f2_t *>(qs) + (size_t)qi * DW);
+                        const float4 *qd =
+                            reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(qs) + (size_t)qi * QF);
                         // two running fma sums, even and odd coordinates,
                         // added at the end (two independent chains; the
                         // margin holds for any grouping, margin.cu)
                         f2_t acc0 = f2_pack(0.0f, 0.0f), acc1 = acc0;
 #pragma unroll
-                        for (int j2 = 0; j2 < DW / 2; ++j2) {
-                            const ulonglong2 q2 = qd[j2];   // (q_j, q_j), (q_j+1, q_j+1)
+                        for (int g = 0; g < G4; ++g) {
+                            const float4 q4 = qd[g];   // q_4g .. q_4g+3, paired in registers
                             // fl(q - y) on both halves
-                            const f2_t t0 = f2_fma(yy[2 * j2], neg1, q2.x);
+                            const f2_t t0 = f2_fma(yy[4 * g], neg1, f2_pack(q4.x, q4.x));
                             acc0 = f2_fma(t0, t0, acc0);
-                            const f2_t t1 = f2_fma(yy[2 * j2 + 1], neg1, q2.y);
+                            const f2_t t1 = f2_fma(yy[4 * g + 1], neg1, f2_pack(q4.y, q4.y));
                             acc1 = f2_fma(t1, t1, acc1);
+                            const f2_t t2 = f2_fma(yy[4 * g + 2], neg1, f2_pack(q4.z, q4.z));
+                            acc0 = f2_fma(t2, t2, acc0);
+                            const f2_t t3 = f2_fma(yy[4 * g + 3], neg1, f2_pack(q4.w, q4.w));
+                            acc1 = f2_fma(t3, t3, acc1);
                         }
                         float sv[2];
                         f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
@@ -248,16 +335,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
 
 // The high-dimensional kernel evaluates 12 (d <= 12) or 16 coordinates.
 template <int G4>
-JoinKernelFn pick_hd(bool f32, bool uni) {
-    if (f32) return uni ? hd_join_kernel<true, true, G4> : hd_join_kernel<true, false, G4>;
-    return uni ? hd_join_kernel<false, true, G4> : hd_join_kernel<false, false, G4>;
+JoinKernelFn pick_hd(bool f32, bool uni, bool exp) {
+    if (f32 && exp) return uni ? hd_join_kernel<true, true, G4, true> : hd_join_kernel<true, false, G4, true>;
+    if (f32) return uni ? hd_join_kernel<true, true, G4, false> : hd_join_kernel<true, false, G4, false>;
+    return uni ? hd_join_kernel<false, true, G4, false> : hd_join_kernel<false, false, G4, false>;
 }
 
 }  // namespace
 
-JoinKernelFn hd_kernel_fn(int d, bool f32, bool uni) {
-    if (d <= 12) return pick_hd<3>(f32, uni);
-    if (d <= kMaxPointDim) return pick_hd<4>(f32, uni);
+JoinKernelFn hd_kernel_fn(int d, bool f32, bool uni, bool exp) {
+    if (d <= 12) return pick_hd<3>(f32, uni, exp);
+    if (d <= kMaxPointDim) return pick_hd<4>(f32, uni, exp);
     return nullptr;
 }
 

@@ -397,7 +397,7 @@ void free_index(Index &ix, cudaStream_t s) {
     }
     DevBuf *all[] = {&ix.pts, &ix.rec32, &ix.rec64, &ix.A,          &ix.B,
                      &ix.G,   &ix.cc,    &ix.M,     &ix.lut,        &ix.items,
-                     &ix.counts_dev,     &ix.ptsd,  &ix.recd32,     &ix.recd64};
+                     &ix.counts_dev,     &ix.ptsd,  &ix.recd32,     &ix.recd64, &ix.hmid_dev};
     for (DevBuf *b : all) dev_free(*b, s);
 }
 
@@ -523,7 +523,27 @@ static sj_status build_index_hd(Error &err, const double *pts_any, uint64_t n, i
         return err.st;
     }
     Geometry &g = ix.g;
-    g.fp32_ok = fp32_margin_diff(d, eps, fmin, fmax, &g.lo32, &g.hi32) ? 1 : 0;  // margin.cu
+    // the expanded-form sum (one fma per coordinate) while its band is
+    // narrow (below 2^-10 E2, the rule of the frame choice), else the
+    // difference form (two per coordinate, a band 10-100x narrower), else
+    // the expanded form when only it has a margin (margin.cu)
+    int grid[kMaxPointDim] = {};
+    for (int t = 0; t < k; ++t) grid[gd.v[t]] = 1;
+    float elo = -1.0f, ehi = 0.0f, dlo = -1.0f, dhi = 0.0f;
+    const bool eok = fp32_margin_hd(d, eps, fmin, fmax, grid, &elo, &ehi, ix.hmid);
+    const bool dok = fp32_margin_diff(d, eps, fmin, fmax, &dlo, &dhi);
+    const double eband = (double)ehi - (elo > 0.0f ? (double)elo : 0.0);
+    ix.hd_exp = (eok && (eband <= std::ldexp(g.E2, -10) || !dok)) ? 1 : 0;
+    g.fp32_ok = (ix.hd_exp || dok) ? 1 : 0;
+    g.lo32 = ix.hd_exp ? elo : dlo;
+    g.hi32 = ix.hd_exp ? ehi : dhi;
+    st = dev_alloc(err, ix.hmid_dev, sizeof(ix.hmid), s);
+    if (st == SJ_OK && cudaMemcpyAsync(ix.hmid_dev.p, ix.hmid, sizeof(ix.hmid), cudaMemcpyHostToDevice, s) !=
+                           cudaSuccess) {
+        cudaGetLastError();
+        st = fail(err, SJ_ECUDA, "copy of the high-dimensional origin failed");
+    }
+    if (st != SJ_OK) { free_index(ix, s); return st; }
     g.frame = SJ_FRAME_GRID;
     ix.bytes += ix.ptsd.bytes + ix.recd32.bytes;
 #undef SJ_HDT

@@ -1188,8 +1188,16 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
         a.ptsd = static_cast<const double *>(ix.ptsd.p);
         a.dfull = ix.dfull;
         a.rsd = f32 ? ix.rsd32 : ix.rsd64;
+        // staged query: 4 ceil(d / 4) value pairs (two floats or one double
+        // each); the expanded form takes fewer (4 ceil(d / 4) + 4 floats)
         a.sm_queries = round16(kQueryBlock * 4 * ((ix.dfull + 3) / 4) * 8);
-        a.sm_warp = a.sm_ranges + a.sm_queries;
+        // the expanded form's origin: 4 ceil(d / 4) floats per warp
+        a.sm_warp = a.sm_ranges + a.sm_queries + 64;
+        a.hd_exp = ix.hd_exp;
+        a.hmid = static_cast<const float *>(ix.hmid_dev.p);
+        a.hgrid4 = ~0ull;
+        for (int t = 0; t < kHdGridDims && t < ix.g.d; ++t)
+            a.hgrid4 &= ~(0xfull << (4 * ix.gdim[t])) | ((uint64_t)t << (4 * ix.gdim[t]));
     }
     return SJ_OK;
 }
@@ -1206,7 +1214,7 @@ sj_status launch_join(Error &err, const Index &ix, const JoinLaunch &cfg, uint32
     const bool f32 = a.f32 != 0;
     const bool uni = cfg.unicomp != 0;
 
-    KernelFn fn = ix.dfull > kMaxDim ? hd_kernel_fn(ix.dfull, f32, uni)   // hd_join.cu
+    KernelFn fn = ix.dfull > kMaxDim ? hd_kernel_fn(ix.dfull, f32, uni, ix.hd_exp != 0)   // hd_join.cu
                                      : pick_kernel(d, f32, uni, a.frame == SJ_FRAME_CELL);
     if (!fn) return fail(err, SJ_EINVAL, "unsupported dimension");
     int dev = 0;

@@ -73,6 +73,21 @@
 // Conversely s32 <= lo = (1 - g_d)(R1 - H1)^2 gives |t| <= T = R1 - H1, each
 // |Delta_j| <= (T + 2 rho_j (1 + u)) / (1 - u) <= D_j (T <= R1), and
 // |Delta| <= T + H1 <= R1 with H1 = |(2 rho_j + u (D_j + 2 rho_j))_j|.
+//
+// Expanded form for points of more than 8 dimensions (the kernel of those
+// points).  The grid covers six of the d dimensions; the kernel evaluates
+// the grid frame's expanded sum over all d coordinates with the origin o_j
+// at the home cell centre in a grid dimension (o_j as in the grid frame)
+// and at the middle of the data range in the others, o_j = fl32(X_j / 2):
+//     z_j = fl(y_j - o_j),  y_j = fl32(fl64(x_j - fmin_j)),
+//     pp, qq as fma chains of z^2, s32 = fl(qq + pp) followed by the fma
+//     terms m_j z_q,j, m_j = -2 z_p,j, in two chains (even and odd j)
+//     added at the end: every term passes through at most d / 2 + 2 <= d + 1
+//     roundings, which the bound (e) allows in any grouping.
+// Bounds (a)-(f) hold per dimension with Rp_j, Rq_j as in the grid frame
+// for a grid dimension (U = the largest grid dimension's cell count), and
+// for the others |y_j - o_j| <= (1 + 2u) X_j / 2 + rho_j, so
+// Rp_j = Rq_j = (1 + u)((1 + 2u) X_j / 2 + rho_j).
 #include <cmath>
 
 #include "sj_internal.cuh"
@@ -86,8 +101,50 @@ struct FrameMargin {
     float lo32 = -1.0f, hi32 = 0.0f;
 };
 
-FrameMargin frame_margin(const Geometry &g, int frame) {
+// The expanded-form bound from per-dimension bounds (the sums of squares
+// over dimensions of eta_j, Rp_j and Rq_j; derivation above): hi and lo in
+// FP32, rounded outward, or no margin when `valid` is false, the inputs are
+// out of range or the band is wider than half of E2.
+FrameMargin margin_tail(int d, double E2, float w32, bool valid, double Xmax, double H2, double Rp2,
+                        double Rq2) {
     FrameMargin fm;
+    const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
+    const double safety = std::ldexp(1.0, -20);
+    const double H = std::sqrt(H2) * (1.0 + safety);
+    const double Rp = std::sqrt(Rp2) * (1.0 + safety), Rq = std::sqrt(Rq2) * (1.0 + safety);
+    auto gam = [&](int k) { return k * u / (1.0 - k * u); };
+    const double E = (gam(d) * (Rp * Rp + Rq * Rq) +
+                      gam(d + 1) * (Rp + Rq) * (Rp + Rq) * (1.0 + gam(d + 1)) +
+                      (3.0 * d + 2.0) * std::ldexp(1.0, -149)) *
+                     (1.0 + safety);
+    const double g64 = (d + 3) * v / (1.0 - (d + 3) * v);
+    const double a64 = 2.0 * d * std::ldexp(1.0, -1074);
+    if (!valid || !std::isfinite(E2) || !(Xmax < std::ldexp(1.0, 60)) ||
+        E2 < std::ldexp(1.0, -100) || !((Rp + Rq) * (Rp + Rq) < std::ldexp(1.0, 100)) ||
+        !(w32 > 0.0f) || !std::isfinite(4.0f * w32))
+        return fm;
+    const double R2 = std::sqrt((E2 + a64) / (1.0 - g64)) * (1.0 + safety);
+    const double hi = ((R2 + H) * (R2 + H) + E) * (1.0 + safety);
+    float hi32 = (float)hi;
+    if ((double)hi32 < hi) hi32 = std::nextafter(hi32, INFINITY);
+    float lo32 = -1.0f;
+    const double R1 = std::sqrt((E2 - a64) / (1.0 + g64)) * (1.0 - safety);
+    if (R1 > H) {
+        const double lo = ((R1 - H) * (R1 - H) - E) * (1.0 - safety);
+        if (lo > 0.0) {
+            lo32 = (float)lo;
+            if ((double)lo32 > lo) lo32 = std::nextafter(lo32, -INFINITY);
+        }
+    }
+    // a band wider than half of E2 makes the filter pointless: compute in FP64
+    if ((double)hi32 - (lo32 > 0.0f ? (double)lo32 : 0.0) > 0.5 * E2) return fm;
+    fm.ok = true;
+    fm.lo32 = lo32;
+    fm.hi32 = hi32;
+    return fm;
+}
+
+FrameMargin frame_margin(const Geometry &g, int frame) {
     const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
     const int d = g.d;
     const double w = g.w;
@@ -120,40 +177,7 @@ FrameMargin frame_margin(const Geometry &g, int frame) {
         Rp2 += rp * rp;
         Rq2 += rq * rq;
     }
-    const double safety = std::ldexp(1.0, -20);
-    const double H = std::sqrt(H2) * (1.0 + safety);
-    const double Rp = std::sqrt(Rp2) * (1.0 + safety), Rq = std::sqrt(Rq2) * (1.0 + safety);
-    auto gam = [&](int k) { return k * u / (1.0 - k * u); };
-    const double E = (gam(d) * (Rp * Rp + Rq * Rq) +
-                      gam(d + 1) * (Rp + Rq) * (Rp + Rq) * (1.0 + gam(d + 1)) +
-                      (3.0 * d + 2.0) * std::ldexp(1.0, -149)) *
-                     (1.0 + safety);
-    const double g64 = (d + 3) * v / (1.0 - (d + 3) * v);
-    const double a64 = 2.0 * d * std::ldexp(1.0, -1074);
-    const float w32 = (float)w;
-    if (!wrap_ok || !std::isfinite(g.E2) || !(Xmax < std::ldexp(1.0, 60)) ||
-        g.E2 < std::ldexp(1.0, -100) || !((Rp + Rq) * (Rp + Rq) < std::ldexp(1.0, 100)) ||
-        !(w32 > 0.0f) || !std::isfinite(4.0f * w32))
-        return fm;
-    const double R2 = std::sqrt((g.E2 + a64) / (1.0 - g64)) * (1.0 + safety);
-    const double hi = ((R2 + H) * (R2 + H) + E) * (1.0 + safety);
-    float hi32 = (float)hi;
-    if ((double)hi32 < hi) hi32 = std::nextafter(hi32, INFINITY);
-    float lo32 = -1.0f;
-    const double R1 = std::sqrt((g.E2 - a64) / (1.0 + g64)) * (1.0 - safety);
-    if (R1 > H) {
-        const double lo = ((R1 - H) * (R1 - H) - E) * (1.0 - safety);
-        if (lo > 0.0) {
-            lo32 = (float)lo;
-            if ((double)lo32 > lo) lo32 = std::nextafter(lo32, -INFINITY);
-        }
-    }
-    // a band wider than half of E2 makes the filter pointless: compute in FP64
-    if ((double)hi32 - (lo32 > 0.0f ? (double)lo32 : 0.0) > 0.5 * g.E2) return fm;
-    fm.ok = true;
-    fm.lo32 = lo32;
-    fm.hi32 = hi32;
-    return fm;
+    return margin_tail(d, g.E2, (float)w, wrap_ok, Xmax, H2, Rp2, Rq2);
 }
 
 double band_of(const FrameMargin &m) {
@@ -201,6 +225,45 @@ bool fp32_margin_diff(int d, double eps, const double *fmin, const double *fmax,
     if (!std::isfinite(h) || (double)h - (l > 0.0f ? (double)l : 0.0) > 0.5 * E2) return false;
     *lo32 = l;
     *hi32 = h;
+    return true;
+}
+
+bool fp32_margin_hd(int d, double eps, const double *fmin, const double *fmax, const int *grid,
+                    float *lo32, float *hi32, float *mid32) {
+    const double u = std::ldexp(1.0, -24), v = std::ldexp(1.0, -53);
+    const double E2 = eps * eps;
+    const double w = eps * (1.0 + std::ldexp(1.0, -16));
+    *lo32 = -1.0f;
+    *hi32 = 0.0f;
+    double U = 0.0;
+    for (int j = 0; j < d; ++j)
+        if (grid[j]) U = std::fmax(U, std::floor((fmax[j] - fmin[j]) / w) + 1.0);
+    double H2 = 0.0, Rp2 = 0.0, Rq2 = 0.0, Xmax = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double X = (fmax[j] - fmin[j]) * (1.0 + 4.0 * v);
+        Xmax = std::fmax(Xmax, X);
+        const double rho = X * (u + v + u * v) + std::ldexp(1.0, -150);
+        double rp, rq;
+        if (grid[j]) {
+            // bounded by the home cell and its neighbours, as in the grid frame
+            const double oerr = 3.1 * u * (X + w);
+            rp = (1.0 + u) * ((0.5 + 3.0 * v * U) * w + rho + oerr);
+            rq = (1.0 + u) * ((1.5 + 3.0 * v * U) * w + rho + oerr);
+            mid32[j] = 0.0f;
+        } else {
+            // anywhere in the data range: origin at its middle
+            mid32[j] = (float)(0.5 * (fmax[j] - fmin[j]));
+            rp = rq = (1.0 + u) * ((1.0 + 2.0 * u) * 0.5 * X + rho);
+        }
+        const double eta = 2.0 * rho + u * (rp + rq) * (1.0 + u);
+        H2 += eta * eta;
+        Rp2 += rp * rp;
+        Rq2 += rq * rq;
+    }
+    const FrameMargin m = margin_tail(d, E2, (float)w, U < 2147483648.0, Xmax, H2, Rp2, Rq2);
+    if (!m.ok) return false;
+    *lo32 = m.lo32;
+    *hi32 = m.hi32;
     return true;
 }
 
@@ -272,6 +335,19 @@ extern "C" sj_status sj_fp32_margin_frame(int d, double eps, const double *gmin,
                                           const double *gmax, int frame, float *w32, float *lo,
                                           float *hi) {
     return margin_entry(d, eps, gmin, gmax, frame, w32, lo, hi);
+}
+
+extern "C" sj_status sj_fp32_margin_hd(int d, double eps, const double *fmin, const double *fmax,
+                                       const int *grid, float *lo, float *hi, float *mid) {
+    if (d < 1 || d > sj::kMaxPointDim || !fmin || !fmax || !grid || !(eps > 0.0) || !std::isfinite(eps))
+        return SJ_EINVAL;
+    float l = -1.0f, h = 0.0f, md[sj::kMaxPointDim] = {};
+    const bool ok = sj::fp32_margin_hd(d, eps, fmin, fmax, grid, &l, &h, md);
+    if (lo) *lo = l;
+    if (hi) *hi = h;
+    if (mid)
+        for (int j = 0; j < d; ++j) mid[j] = md[j];
+    return ok ? SJ_OK : SJ_ERANGE;
 }
 
 extern "C" sj_status sj_fp32_margin_diff(int d, double eps, const double *fmin,

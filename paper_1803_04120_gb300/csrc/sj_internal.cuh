@@ -139,8 +139,19 @@ struct Index {
     DevBuf recd32;                 // cell-ordered fl32(x_j - fmin_j), j < dfull, then the id
     DevBuf recd64;                 // cell-ordered x_j, j < dfull, then the id
     int rsd32 = 0, rsd64 = 0;      // their strides (floats / doubles)
+    // FP32 sum of the search: expanded form (origin mid32[j] outside the grid
+    // dimensions) when its margin is usable, else the difference form
+    int hd_exp = 0;
+    float hmid[kMaxPointDim] = {};
+    DevBuf hmid_dev;               // hmid in device memory
 };
 
+// FP32 margin of the expanded-form sum of the high-dimensional kernel
+// (margin.cu): grid[j] != 0 marks the grid dimensions (origin at the home
+// cell centre), the others take their origin mid32[j] = fl32(X_j / 2).
+// Returns false when no useful margin exists.
+bool fp32_margin_hd(int d, double eps, const double *fmin, const double *fmax, const int *grid,
+                    float *lo32, float *hi32, float *mid32);
 // FP32 margin of the high-dimensional path (margin.cu): the kernel sums
 // fl32(y_p - y_q)^2 with fused multiply-adds over all d dimensions,
 // y = fl32(fl64(x_j - fmin_j)).  Returns false when no useful margin exists.
@@ -248,6 +259,12 @@ struct JoinArgs {
     const double *ptsd;
     int dfull;
     int rsd;                        // their stride in elements of the mode's type
+    // expanded-form FP32 sum (margin.cu, fp32_margin_hd): nibble j of hgrid4
+    // is the grid dimension that dimension j is (15: none); hmid[j] (device
+    // memory) the origin of the others
+    int hd_exp;
+    uint64_t hgrid4;
+    const float *hmid;
 };
 
 struct JoinLaunch {
@@ -276,7 +293,7 @@ static_assert(sizeof(MultiJobs) <= 32000, "multi-join table exceeds the kernel p
 // A search-and-refine kernel: (arguments, device counters |G| and items).
 typedef void (*JoinKernelFn)(const JoinArgs, const uint32_t *);
 // The kernel for points of d = 9..16 dimensions (hd_join.cu), null otherwise.
-JoinKernelFn hd_kernel_fn(int d, bool f32, bool uni);
+JoinKernelFn hd_kernel_fn(int d, bool f32, bool uni, bool exp);
 
 sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uint32_t item_begin,
                          uint32_t item_end, uint2 *out, uint64_t cap,

@@ -36,7 +36,7 @@ ABI_FUNCTIONS = (
     "sj_result_times", "sj_fp32_margin", "sj_selfjoin_noalloc", "sj_selfjoin_multi",
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds", "sj_shard_bounds_cost",
     "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
-    "sj_fp32_margin_diff", "sj_fp32_fma_rate", "sj_fp64_fma_rate",
+    "sj_fp32_margin_diff", "sj_fp32_margin_hd", "sj_fp32_fma_rate", "sj_fp64_fma_rate",
 )
 
 
@@ -154,6 +154,8 @@ def load(build: bool = True):
                                        ctypes.POINTER(ctypes.c_double)]),
             "sj_fp32_margin_diff": (i32, [i32, f64, P, P, ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]),
+            "sj_fp32_margin_hd": (i32, [i32, f64, P, P, P, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float), P]),
             "sj_fp32_margin_frame": (i32, [i32, f64, P, P, i32, ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float)]),
@@ -582,6 +584,21 @@ def sj_fp32_margin_diff(d: int, eps: float, fmin, fmax):
     st = lib.sj_fp32_margin_diff(d, float(eps), fmin.ctypes.data, fmax.ctypes.data,
                                  ctypes.byref(lo), ctypes.byref(hi))
     return st, lo.value, hi.value
+
+
+def sj_fp32_margin_hd(d: int, eps: float, fmin, fmax, grid):
+    """(status, lo, hi, mid) of the expanded-form FP32 margin for points of
+    more than 8 dimensions: grid[j] marks the grid dimensions, mid[j] is the
+    origin of the others (host only)."""
+    lib = load()
+    fmin = np.ascontiguousarray(fmin, dtype=np.float64)
+    fmax = np.ascontiguousarray(fmax, dtype=np.float64)
+    g = np.ascontiguousarray(grid, dtype=np.int32)
+    mid = np.zeros(max(d, 1), dtype=np.float32)
+    lo, hi = ctypes.c_float(), ctypes.c_float()
+    st = lib.sj_fp32_margin_hd(d, float(eps), fmin.ctypes.data, fmax.ctypes.data, g.ctypes.data,
+                               ctypes.byref(lo), ctypes.byref(hi), mid.ctypes.data)
+    return st, lo.value, hi.value, mid[:d].copy()
 
 
 def sj_fp32_fma_rate(device: int = 0, packed: bool = True):

@@ -31,6 +31,9 @@ def test_highdim_matches_bruteforce(d):
     rng = np.random.default_rng(400 + d)
     cases = [(rng.uniform(0, 100, size=(3000, d)), eps_for(3000, d, 20)),
              (clustered(5000, d, 500 + d), 4.0)]
+    # the uniform case takes the expanded-form sum, the clustered one (small
+    # eps against the data range) the difference form
+    assert [hd_form(p, e) for p, e in cases] == ["expanded", "difference"]
     for pts, eps in cases:
         want = orc.bruteforce(pts, eps)
         for prec in (sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64):
@@ -44,9 +47,32 @@ def test_highdim_matches_bruteforce(d):
         assert len(want) > len(pts)
 
 
-def test_highdim_band_pairs_are_rechecked():
+def hd_form(pts, eps):
+    """'expanded' or 'difference': the FP32 sum the index chooses (the
+    expanded form while its band is below 2^-10 eps^2, as the library
+    decides from the same margins), for the six dimensions with the most
+    cells as the grid."""
+    d = pts.shape[1]
+    fmin = pts.min(axis=0) - eps
+    fmax = pts.max(axis=0) + eps
+    w = eps * (1.0 + 2.0 ** -16)
+    cells = np.floor((fmax - fmin) / w) + 1.0
+    grid = np.zeros(d, dtype=np.int32)
+    taken = []
+    for _ in range(6):
+        best = max((j for j in range(d) if j not in taken), key=lambda j: (cells[j], -j))
+        taken.append(best)
+    grid[taken] = 1
+    est, elo, ehi, _ = sj.sj_fp32_margin_hd(d, eps, fmin, fmax, grid)
+    dst, _, _ = sj.sj_fp32_margin_diff(d, eps, fmin, fmax)
+    narrow = est == sj.SJ_OK and ehi - max(elo, 0.0) <= eps * eps * 2.0 ** -10
+    return "expanded" if est == sj.SJ_OK and (narrow or dst != sj.SJ_OK) else "difference"
+
+
+@pytest.mark.parametrize("eps,form", [(3.0, "difference"), (30.0, "expanded")])
+def test_highdim_band_pairs_are_rechecked(eps, form):
     rng = np.random.default_rng(410)
-    d, eps = 11, 3.0
+    d = 11
     base = rng.uniform(0, 40, size=(600, d))
     extra = []
     for p in base:
@@ -57,6 +83,7 @@ def test_highdim_band_pairs_are_rechecked():
             f = 1.0 + float(rng.choice([-3, -1, 0, 1, 3])) * 2.0 ** -24 * float(rng.random())
         extra.append(p + v * eps * f)
     pts = np.concatenate([base, np.array(extra)])
+    assert hd_form(pts, eps) == form
     want = np.sort(orc.bruteforce(pts, eps))
     with sj.Context() as ctx:
         assert np.array_equal(keys(ctx.sj_selfjoin(pts, eps)), want)

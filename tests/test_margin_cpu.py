@@ -324,3 +324,88 @@ def test_difference_form_margin_arguments():
     assert st == sj.SJ_EINVAL
     st, _, _ = sj.sj_fp32_margin_diff(10, 1e-9, np.zeros(10), np.full(10, 1e8))
     assert st == sj.SJ_ERANGE
+
+
+# ---------------------------------------------------------------- expanded form (d > 8)
+
+def kernel_s32_hd(p, q, fmin, w32, cells, grid, mid):
+    """s32 of the high-dimensional kernel's expanded form: z_j = fl32(y_j -
+    o_j) about the home cell centre in a grid dimension and mid[j] in the
+    others; |z|^2 as fma chains; fl(qq + pp) starts the chain of the even
+    coordinates' terms m_j z_q,j, the odd ones form a second chain, and the
+    two are added at the end."""
+    d = len(p)
+    zp, zq = [], []
+    for j in range(d):
+        o = r32(r32(F(cells[j]) + F(1, 2)) * F(w32)) if grid[j] else F(float(mid[j]))
+        yp = r32(r64(F(p[j]) - F(fmin[j])))
+        yq = r32(r64(F(q[j]) - F(fmin[j])))
+        zp.append(r32(yp - o))
+        zq.append(r32(yq - o))
+    pp = qq = F(0)
+    for j in range(d):
+        pp = r32(zp[j] * zp[j] + pp)
+        qq = r32(zq[j] * zq[j] + qq)
+    acc = [r32(qq + pp), F(0)]
+    for j in range(d):
+        acc[j % 2] = r32((-2 * zp[j]) * zq[j] + acc[j % 2])
+    return r32(acc[0] + acc[1])
+
+
+@pytest.mark.parametrize("d,eps,scale,offset", [
+    (9, 30.0, 100.0, 0.0), (12, 20.0, 100.0, -50.0), (16, 55.0, 100.0, 0.0), (16, 66.2, 100.0, 1e3)])
+def test_expanded_form_hd_margin_sound_on_threshold_pairs(d, eps, scale, offset):
+    rng = np.random.default_rng(int(eps * 10) + d)
+    pts = offset + rng.uniform(0, scale, size=(40, d))
+    extra = []
+    for p in pts:
+        v = rng.normal(size=d)
+        v /= np.linalg.norm(v)
+        for f in (1.0, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -52, 1.0 + 3e-7, 1.0 - 3e-7,
+                  1.0 + 2e-6, 1.0 - 2e-6, 0.5):
+            extra.append(p + v * eps * f)
+    allp = np.concatenate([pts, np.array(extra)])
+    fmin = allp.min(axis=0) - eps
+    fmax = allp.max(axis=0) + eps
+    grid = np.zeros(d, dtype=np.int32)
+    grid[rng.choice(d, size=6, replace=False)] = 1
+    st, lo, hi, mid = sj.sj_fp32_margin_hd(d, eps, fmin, fmax, grid)
+    assert st == sj.SJ_OK
+    E2 = r64(F(eps) * F(eps))
+    assert 0.0 < lo < float(E2) < hi
+    # the band grows with the extent of the dimensions outside the grid
+    X = float(np.max(fmax - fmin))
+    assert (hi - lo) / float(E2) < 1e-4 + 200 * d * 2.0 ** -24 * (X / eps) ** 2
+    for j in range(d):
+        if not grid[j]:
+            assert mid[j] == np.float32(0.5 * (fmax[j] - fmin[j]))
+    w = eps * (1.0 + 2.0 ** -16)
+    inv_w = 1.0 / w
+    w32 = float(np.float32(w))
+    ng = [int(math.floor((fmax[j] - fmin[j]) / w)) + 1 for j in range(d)]
+    checked = 0
+    for k, p in enumerate(pts):
+        cells = [cell_of(p[j], fmin[j], inv_w, ng[j]) if grid[j] else 0 for j in range(d)]
+        for q in extra[8 * k: 8 * k + 8]:
+            cq = [cell_of(q[j], fmin[j], inv_w, ng[j]) if grid[j] else 0 for j in range(d)]
+            if max(abs(a - b) for a, b in zip(cells, cq)) > 1:
+                continue           # not adjacent in the grid: never compared
+            s = kernel_s32_hd(p, q, fmin, w32, cells, grid, mid)
+            mem = exact_member(p, q, E2)
+            if s <= F(lo):
+                assert mem, (d, k)
+            if s > F(hi):
+                assert not mem, (d, k)
+            checked += 1
+    assert checked > 100
+
+
+def test_expanded_form_hd_margin_arguments():
+    g = np.ones(17, dtype=np.int32)
+    st, _, _, _ = sj.sj_fp32_margin_hd(17, 1.0, np.zeros(17), np.ones(17), g)
+    assert st == sj.SJ_EINVAL
+    # a data range far wider than eps outside the grid leaves no usable band
+    g = np.zeros(10, dtype=np.int32)
+    g[:6] = 1
+    st, _, _, _ = sj.sj_fp32_margin_hd(10, 1e-3, np.zeros(10), np.full(10, 1e6), g)
+    assert st == sj.SJ_ERANGE
