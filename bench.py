@@ -713,11 +713,10 @@ def run_gpu(args):
     pairs_step = sum(counts)
 
     def step(ctxs, s):
-        tot, launches, ev = 0, 0, []
+        tot = 0
         for c, p, o, (cfg, _) in zip(ctxs, d_pts, outs, data):
             tot += c.sj_selfjoin_device(p, cfg["eps"], o, stream=s)
-            launches += c.sj_last_stats()["kernel_launches"]
-        return tot, launches
+        return tot
 
     def timed(ctxs, steps, warmup):
         for _ in range(warmup):
@@ -733,12 +732,15 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            n, l = step(ctxs, stream)
+            n = step(ctxs, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             assert n == pairs_step, (n, pairs_step)
             times.append(e0.elapsed_time(e1))
-            launches += l
+            # each context made one call in the step: its last call's kernel
+            # count, read after the timed region so that the calls run back
+            # to back inside it
+            launches += sum(c.sj_last_stats()["kernel_launches"] for c in ctxs)
         return times, launches
 
     clk = ClockSampler(dev)
