@@ -205,6 +205,34 @@ def test_device_entry_point_and_overflow():
         assert st["evaluations"] > 0
 
 
+def test_device_points_read_in_place():
+    """Calls whose index ends with them read device points in place (no
+    copy): a view that starts one row into a larger tensor (8-byte but not
+    256-byte aligned) joins like the oracle, and no call writes the caller's
+    array; the persistent index (sj_build_index) keeps its own copy, so a
+    later change of the array does not reach it."""
+    torch = pytest.importorskip("torch")
+    pts = datagen.uniform(6001, 4, seed=13)
+    eps = 4.0
+    want = orc.grid_join(pts[1:], eps)
+    big = torch.from_numpy(pts).cuda()
+    view = big[1:]
+    assert view.data_ptr() % 256 != 0
+    before = big.clone()
+    with sj.Context() as ctx:
+        out = torch.empty((want.size + 10, 2), dtype=torch.int32, device="cuda")
+        n = ctx.sj_selfjoin_device(view, eps, out)
+        assert n == want.size
+        assert_same(sj.pairs_to_keys(out[:n].cpu().numpy().view(np.uint32)), want, "row-offset view")
+        assert ctx.sj_selfjoin_count(view, eps) == want.size
+        assert_same(sj.pairs_to_keys(ctx.sj_selfjoin(view, eps)), want, "host result from device points")
+        assert torch.equal(big, before)
+        idx = ctx.sj_build_index(view, eps)
+        big.fill_(0.0)          # the index holds its own copy of the points
+        assert_same(sj.pairs_to_keys(ctx.sj_selfjoin_index(idx)), want, "index after the array changed")
+        idx.free()
+
+
 def test_batching_small_cap_many_batches_and_retries():
     pts = datagen.uniform(20000, 2, seed=13)
     eps = 1.5
