@@ -190,85 +190,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                         yy[j + 2] = f2_pack(j + 2 < dd ? u.z : 0.f, j + 2 < dd ? v.z : 0.f);
                         yy[j + 3] = f2_pack(j + 3 < dd ? u.w : 0.f, j + 3 < dd ? v.w : 0.f);
                     }
+                    f2_t qq = f2_pack(0.0f, 0.0f);
                     if (EXP) {
                         // z = fl(y - o) (exact negation, one rounding) and
                         // |z|^2 of both candidates
-                        f2_t qq = f2_pack(0.0f, 0.0f);
 #pragma unroll
                         for (int j = 0; j < DW; ++j) {
                             const float no = -origin[j];
                             yy[j] = f2_add(yy[j], f2_pack(no, no));
                             qq = f2_fma(yy[j], yy[j], qq);
                         }
-                        for (uint32_t qi = 0; qi < nq; ++qi) {
-                            const float4 *qd =
-                                reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(qs) + (size_t)qi * QF);
-                            // fl(qq + pp), then the m_j z_j terms in two
-                            // chains (even and odd j) added at the end
-                            const float pp = qd[G4].x;
-                            f2_t acc0 = f2_add(qq, f2_pack(pp, pp)), acc1 = f2_pack(0.0f, 0.0f);
-#pragma unroll
-                            for (int g = 0; g < G4; ++g) {
-                                const float4 m4 = qd[g];   // m_4g .. m_4g+3
-                                acc0 = f2_fma(f2_pack(m4.x, m4.x), yy[4 * g], acc0);
-                                acc1 = f2_fma(f2_pack(m4.y, m4.y), yy[4 * g + 1], acc1);
-                                acc0 = f2_fma(f2_pack(m4.z, m4.z), yy[4 * g + 2], acc0);
-                                acc1 = f2_fma(f2_pack(m4.w, m4.w), yy[4 * g + 3], acc1);
-                            }
-                            float sv[2];
-                            f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
-                            if (!__any_sync(0xffffffffu, sv[0] <= a.hi32 || sv[1] <= a.hi32)) continue;
-                            const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
-                            bool hit[2], band[2];
-#pragma unroll
-                            for (int h2 = 0; h2 < 2; ++h2) {
-                                const bool cand = !UNI || kp[h2] >= home_len || kp[h2] > ql0 + qi;
-                                hit[h2] = cand && sv[h2] <= a.hi32;
-                                band[h2] = hit[h2] && !(sv[h2] <= a.lo32);
-                            }
-                            if (__any_sync(0xffffffffu, band[0] || band[1])) {
-#pragma unroll
-                                for (int h2 = 0; h2 < 2; ++h2) {
-                                    if (band[h2]) {
-                                        hit[h2] = exact_member_hd(a.ptsd + (size_t)qid * dd,
-                                                                  a.ptsd + (size_t)cid[h2] * dd, dd, a.E2);
-                                        ++rechecks;
-                                    }
-                                }
-                            }
-                            emit(hit[0], qid, cid[0]);
-                            emit(hit[1], qid, cid[1]);
-                        }
-                        continue;
                     }
-                    const f2_t neg1 = f2_pack(-1.0f, -1.0f);
-                    for (uint32_t qi = 0; qi < nq; ++qi) {
-                        const float4 *qd =
-                            reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(qs) + (size_t)qi * QF);
-                        // two running fma sums, even and odd coordinates,
-                        // added at the end (two independent chains; the
-                        // margin holds for any grouping, margin.cu)
-                        f2_t acc0 = f2_pack(0.0f, 0.0f), acc1 = acc0;
-#pragma unroll
-                        for (int g = 0; g < G4; ++g) {
-                            const float4 q4 = qd[g];   // q_4g .. q_4g+3, paired in registers
-                            // fl(q - y) on both halves
-                            const f2_t t0 = f2_fma(yy[4 * g], neg1, f2_pack(q4.x, q4.x));
-                            acc0 = f2_fma(t0, t0, acc0);
-                            const f2_t t1 = f2_fma(yy[4 * g + 1], neg1, f2_pack(q4.y, q4.y));
-                            acc1 = f2_fma(t1, t1, acc1);
-                            const f2_t t2 = f2_fma(yy[4 * g + 2], neg1, f2_pack(q4.z, q4.z));
-                            acc0 = f2_fma(t2, t2, acc0);
-                            const f2_t t3 = f2_fma(yy[4 * g + 3], neg1, f2_pack(q4.w, q4.w));
-                            acc1 = f2_fma(t3, t3, acc1);
-                        }
-                        float sv[2];
-                        f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
-                        // hits are rare (a few in 1e4 comparisons at 16-D):
-                        // one vote per query, then the UNICOMP home-cell
-                        // rule (only candidates after the query), the band
-                        // rechecks and the writes in that rare branch
-                        if (!__any_sync(0xffffffffu, sv[0] <= a.hi32 || sv[1] <= a.hi32)) continue;
+                    // the UNICOMP home-cell rule, the band rechecks and the
+                    // writes of one query, in the rare branch where a lane
+                    // has a hit
+                    auto handle = [&](uint32_t qi, const float *sv) {
                         const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, qi);
                         bool hit[2], band[2];
 #pragma unroll
@@ -289,6 +225,59 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
                         }
                         emit(hit[0], qid, cid[0]);
                         emit(hit[1], qid, cid[1]);
+                    };
+                    // s32 of query q against this lane's two candidates
+                    auto sum_of = [&](uint32_t q, float *sv) {
+                        const float4 *qd =
+                            reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(qs) + (size_t)q * QF);
+                        f2_t acc0 = f2_pack(0.0f, 0.0f), acc1 = acc0;
+                        if (EXP) {
+                            // fl(qq + pp), then the m_j z_j terms in two
+                            // chains (even and odd j) added at the end
+                            const float pp = qd[G4].x;
+                            acc0 = f2_add(qq, f2_pack(pp, pp));
+#pragma unroll
+                            for (int g = 0; g < G4; ++g) {
+                                const float4 m4 = qd[g];   // m_4g .. m_4g+3, paired in registers
+                                acc0 = f2_fma(f2_pack(m4.x, m4.x), yy[4 * g], acc0);
+                                acc1 = f2_fma(f2_pack(m4.y, m4.y), yy[4 * g + 1], acc1);
+                                acc0 = f2_fma(f2_pack(m4.z, m4.z), yy[4 * g + 2], acc0);
+                                acc1 = f2_fma(f2_pack(m4.w, m4.w), yy[4 * g + 3], acc1);
+                            }
+                        } else {
+                            // fl(q - y)^2 in two running fma sums, even and
+                            // odd coordinates, added at the end (the margin
+                            // holds for any grouping, margin.cu); the
+                            // difference as fma(y, -1, q) rounds once like q - y
+                            const f2_t neg1 = f2_pack(-1.0f, -1.0f);
+#pragma unroll
+                            for (int g = 0; g < G4; ++g) {
+                                const float4 q4 = qd[g];   // q_4g .. q_4g+3, paired in registers
+                                const f2_t t0 = f2_fma(yy[4 * g], neg1, f2_pack(q4.x, q4.x));
+                                acc0 = f2_fma(t0, t0, acc0);
+                                const f2_t t1 = f2_fma(yy[4 * g + 1], neg1, f2_pack(q4.y, q4.y));
+                                acc1 = f2_fma(t1, t1, acc1);
+                                const f2_t t2 = f2_fma(yy[4 * g + 2], neg1, f2_pack(q4.z, q4.z));
+                                acc0 = f2_fma(t2, t2, acc0);
+                                const f2_t t3 = f2_fma(yy[4 * g + 3], neg1, f2_pack(q4.w, q4.w));
+                                acc1 = f2_fma(t3, t3, acc1);
+                            }
+                        }
+                        f2_unpack(f2_add(acc0, acc1), sv[0], sv[1]);
+                    };
+                    // two queries per vote: hits are a few in 1e4
+                    // comparisons, and the vote and its branch per query
+                    // were the loop's largest stall after the arithmetic
+                    for (uint32_t qi = 0; qi < nq; qi += 2) {
+                        const uint32_t qb = qi + 1 < nq ? qi + 1 : qi;
+                        float sa[2], sb[2];
+                        sum_of(qi, sa);
+                        sum_of(qb, sb);
+                        const bool ha = sa[0] <= a.hi32 || sa[1] <= a.hi32;
+                        const bool hb = qb != qi && (sb[0] <= a.hi32 || sb[1] <= a.hi32);
+                        if (!__any_sync(0xffffffffu, ha || hb)) continue;
+                        if (__any_sync(0xffffffffu, ha)) handle(qi, sa);
+                        if (__any_sync(0xffffffffu, hb)) handle(qb, sb);
                     }
                 }
             } else {
