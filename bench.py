@@ -553,6 +553,8 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
         return sum(c for c, _ in got), wall, lat
 
     run([0.0] * nb)                       # untimed pass: pinned result buffers, pool
+    run([0.0] * n_req)                    # untimed: the wave tuner meets the saturated waves' keys
+    tune_info = ctx_on.sj_serve_stats()
     p_sat, wall_sat, lat_sat = run([0.0] * n_req)
     assert n_req > nb or p_sat == tot64
     rate_sat = n_req / wall_sat
@@ -567,6 +569,12 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
                       "p50_ms": _pct(lat_poi, 50), "p99_ms": _pct(lat_poi, 99)})
     info = ctx_on.sj_serve_stats()
     ctx_on.close()
+    # the same saturated stream with the fixed launch parameters
+    ctx_off = sj.Context(device=dev, max_inflight=64, serve_mem_bytes=64 << 30, autotune=False)
+    run([0.0] * nb, ctx_off)
+    p_fix, wall_fix, lat_fix = run([0.0] * n_req, ctx_off)
+    ctx_off.close()
+    assert p_fix == p_sat
     return {
         "requests": n_req, "pairs": p_sat,
         "request_mix": "n log-uniform [1e3,1e6], d uniform {2..6}, eps for U[8,128] mean neighbours, "
@@ -574,7 +582,11 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
         "saturated": {"pairs_per_s": round(p_sat / wall_sat, 1), "req_per_s": round(rate_sat, 1),
                       "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99)},
         "sweep": sweep,
-
+        "saturated_fixed_launch": {"pairs_per_s": round(p_fix / wall_fix, 1),
+                                   "req_per_s": round(n_req / wall_fix, 1),
+                                   "p50_ms": _pct(lat_fix, 50), "p99_ms": _pct(lat_fix, 99)},
+        "wave_tuner": {"tuned_waves": info["tuned_waves"], "ms_tune": round(info["ms_tune"], 1),
+                       "tuned_waves_in_timed_passes": info["tuned_waves"] - tune_info["tuned_waves"]},
         "one_at_a_time_fp64": {"requests": nb, "pairs_per_s": round(tot64 / wall64, 1),
                                "p50_ms": _pct(lat64, 50), "p99_ms": _pct(lat64, 99)},
         "one_at_a_time_fp32": {"requests": nb, "pairs_per_s": round(tot32 / wall32, 1),
@@ -604,8 +616,20 @@ def multi_bench(dev: int, reps: int, n_jobs: int = 64, seed: int = 7):
     reqs = datagen.serving_requests(n_jobs, seed, rate_hz=1.0)
     pts = [datagen.uniform(r["n"], r["d"], seed=7000 + k) for k, r in enumerate(reqs)]
     jobs = [(p, r["eps"]) for p, r in zip(pts, reqs)]
-    with sj.Context(device=dev) as c:
+    with sj.Context(device=dev, autotune=False) as c:
         counts = c.sj_selfjoin_multi(jobs, copy=False)          # engines, graphs, pools
+        t_fixed = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            got = c.sj_selfjoin_multi(jobs, copy=False)
+            t_fixed.append(time.perf_counter() - t0)
+            assert got == counts
+    with sj.Context(device=dev) as c:
+        sj.sj_tune_reset()
+        t0 = time.perf_counter()
+        assert c.sj_selfjoin_multi(jobs, copy=False) == counts  # waves tuned here
+        t_tuning = time.perf_counter() - t0
         total = sum(counts)
         t_multi = []
         for _ in range(reps):
@@ -614,6 +638,9 @@ def multi_bench(dev: int, reps: int, n_jobs: int = 64, seed: int = 7):
             got = c.sj_selfjoin_multi(jobs, copy=False)
             t_multi.append(time.perf_counter() - t0)
             assert got == counts
+        lst = c.sj_last_stats()
+        choice = {"tuned": lst["tuned"], "grab": lst["grab"], "nbuf": lst["nbuf"],
+                  "staging": lst["staging"], "waves": lst["batches"]}
         for p, e in jobs[:4]:                                    # warm the single-join path
             c.sj_result_free(c.sj_selfjoin_raw(p, e))
         t_host = []
@@ -640,7 +667,11 @@ def multi_bench(dev: int, reps: int, n_jobs: int = 64, seed: int = 7):
     ms = lambda t: round(1e3 * statistics.median(t), 3)
     return {"jobs": n_jobs, "pairs": total,
             "points": sum(int(p.shape[0]) for p in pts),
-            "multi_host_pairs": {"ms": ms(t_multi), "pairs_per_s": round(total / statistics.median(t_multi), 1)},
+            "multi_host_pairs": {"ms": ms(t_multi), "pairs_per_s": round(total / statistics.median(t_multi), 1),
+                                 "launch": "wave tuner", "last_wave_choice": choice,
+                                 "tuning_call_ms": round(1e3 * t_tuning, 3)},
+            "multi_host_pairs_fixed_launch": {"ms": ms(t_fixed),
+                                              "pairs_per_s": round(total / statistics.median(t_fixed), 1)},
             "one_at_a_time_host_pairs": {"ms": ms(t_host),
                                          "pairs_per_s": round(total / statistics.median(t_host), 1)},
             "one_at_a_time_device_pairs": {"ms": ms(t_dev),

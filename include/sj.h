@@ -141,9 +141,15 @@ typedef struct {
                                 launches the first time a (d, precision,
                                 UNICOMP, points-per-cell bucket) key is met
                                 in the process and reuses the choice after;
-                                0: fixed defaults.  The many-join launch of
-                                sj_selfjoin_multi and sj_submit keeps the
-                                defaults.  Never changes the result. */
+                                the many-join launch of sj_selfjoin_multi
+                                and sj_submit takes the wave tuner's choice
+                                (grab, ring depth, staging size, item
+                                slots for every job of a wave), which times
+                                the multi-join launch of the first wave of
+                                a (precision, log2 points per SM) key of at
+                                least 2^17 points with each candidate and
+                                reuses the choice after; 0: fixed defaults.
+                                Never changes the result. */
     int32_t device;          /* CUDA device ordinal; default 0 */
     int32_t lookup;          /* sj_lookup; default SJ_LOOKUP_AUTO */
     int32_t profile;         /* 1: time every join-kernel launch with CUDA
@@ -482,7 +488,9 @@ typedef struct {
  * succeeded, else the first job error (message in sj_last_error); the other
  * jobs' results are still returned.  sj_last_stats sums over the jobs
  * (batches = waves, retries = jobs re-joined alone because their result
- * outgrew its estimated buffer). */
+ * outgrew its estimated buffer); its grab, nbuf and staging are the last
+ * wave's launch parameters and tuned is 2 when a wave of the call was
+ * tuned, 1 when a wave took the wave tuner's cached choice, else 0. */
 SJ_API sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs,
                                    sj_result **out, sj_status *status);
 
@@ -561,9 +569,16 @@ typedef struct {
      * and the bounds pass, the graph replay (index build + join), the result
      * copies to the host */
     double ms_bounds, ms_graph, ms_output;
+    uint64_t tuned_waves;      /* waves whose multi-join launch the wave tuner timed */
+    double ms_tune;            /* host wall time of those tuning passes (ms) */
 } sj_serve_info;
 
 SJ_API sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out);
+
+/* Forgets every choice of the launch tuners of the process (single joins
+ * and many-join waves), so that the next join or wave of each key is tuned
+ * again.  Safe while no join is running. */
+SJ_API void sj_tune_reset(void);
 
 /* Per-request timestamps (seconds since the context was created) of a
  * finished result: submitted, admitted, completed.  Zero for results not

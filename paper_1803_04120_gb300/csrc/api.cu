@@ -19,6 +19,7 @@
 #include <utility>
 #include <vector>
 
+#include "engine.cuh"
 #include "sj_internal.cuh"
 
 namespace sj {
@@ -1139,6 +1140,11 @@ sj_status sj_result_times(const sj_result *r, double *t_submit, double *t_admit,
     if (t_admit) *t_admit = r->t_admit;
     if (t_done) *t_done = r->t_done;
     return SJ_OK;
+}
+
+void sj_tune_reset(void) {
+    tune_clear();
+    engine_tune_reset();
 }
 
 sj_status sj_last_stats(const sj_ctx *ctx, sj_stats *out) {

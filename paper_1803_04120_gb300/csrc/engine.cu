@@ -17,13 +17,23 @@
 // table from device memory, so only the multi-join node's launch shape and
 // job table (kernel parameters) are updated per wave.
 //
-// Launch parameters are per job: the context's forced ones, else the
-// defaults.  The launch tuner (tune.cu) is not applied to waves: its
-// choices come from single joins, and in one launch of many small joins
-// they lost (measured on the 10,000-request stream, passes interleaved:
-// 0.90x of the fixed defaults with the tuned grab alone; 9.3 against
-// 12.9 G pairs/s with every tuned parameter, since one job's larger
-// shared memory per warp lowers the occupancy of the whole wave).
+// Launch parameters: the context's forced ones, else those of the wave
+// tuner, else the defaults.  The wave tuner times the multi-join launch of
+// a wave itself, not single joins: the choices of the single-join tuner
+// (tune.cu) lost in one launch of many small joins (measured on the
+// 10,000-request stream, passes interleaved: 0.90x of the fixed defaults
+// with the tuned grab alone; 9.3 against 12.9 G pairs/s with every tuned
+// parameter, since one job's larger shared memory per warp lowers the
+// occupancy of the whole wave).  The first wave of a key (precision,
+// log2 of the wave's points per SM) is re-joined with each candidate
+// setting, applied to every job of the wave (the work items a warp takes
+// per cursor bump, the candidate-chunk ring depth, the pair staging size,
+// the item slots), one parameter after another; a change is kept when
+// its launch is at least 3% faster.  Every timed launch writes the whole
+// result again, so the wave's result is that of the last one.  Timing
+// needs the GPU alone: the waves of all engines of the process hold a
+// shared gate for their graph replay and a tuning pass holds it
+// exclusively (a waiting pass holds back new waves).
 //
 // The engine takes jobs whose grid fits the dense lookup table (at most
 // max(2^25, 16 n) cells, and at most kEngMaxLut) with n <= kEngMaxN; any
@@ -33,9 +43,13 @@
 // alone into a buffer of the exact size, using the index already built.
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "engine.cuh"
@@ -550,16 +564,166 @@ uint64_t engine_estimate(const double *pts, uint64_t n, int d, double eps, uint6
 
 namespace {
 
-// Launch parameters of a job: the context's forced ones, else the defaults.
-JoinLaunch job_launch(const Engine *e) {
+// Launch parameters of the wave tuner, applied to every job of a wave.
+struct WaveTune {
+    int grab = 1, nbuf = 0, eb = 0, slots = 0;
+};
+
+// Waves below this many points are not tuned: their launch is too short to
+// time apart from noise.
+constexpr uint64_t kWaveTuneMinPoints = 1ull << 17;
+
+std::mutex g_wave_mu;
+std::map<std::pair<int, int>, WaveTune> g_wave_tuned;   // (precision, bucket) -> choice
+std::set<std::pair<int, int>> g_wave_pending;           // keys a tuning pass is working on
+
+// The GPU gate of the waves of every engine of the process: waves hold it
+// shared for their graph replay, a tuning pass exclusively.  A waiting
+// tuning pass holds back new shared holders, so that it is not starved by
+// overlapping waves.
+class GpuGate {
+public:
+    void lock_shared() {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return !writer_ && waiting_ == 0; });
+        ++readers_;
+    }
+    void unlock_shared() {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (--readers_ == 0) cv_.notify_all();
+    }
+    void lock() {
+        std::unique_lock<std::mutex> lk(mu_);
+        ++waiting_;
+        cv_.wait(lk, [&] { return !writer_ && readers_ == 0; });
+        --waiting_;
+        writer_ = true;
+    }
+    void unlock() {
+        std::lock_guard<std::mutex> lk(mu_);
+        writer_ = false;
+        cv_.notify_all();
+    }
+
+private:
+    std::mutex mu_;
+    std::condition_variable cv_;
+    int readers_ = 0, waiting_ = 0;
+    bool writer_ = false;
+};
+GpuGate g_gate;
+
+// Key of a wave: (precision, round(log2(points of the wave per SM))).
+std::pair<int, int> wave_key(const Engine *e, uint64_t points) {
+    const double per_sm = (double)points / (double)std::max(1, e->sms);
+    return std::make_pair(e->cfg.prec == SJ_PREC_FP32_RECHECK ? 1 : 0,
+                          (int)std::lround(std::log2(std::max(1.0, per_sm))));
+}
+
+bool launch_forced_cfg(const sj_config &c) {
+    return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.slots > 0 || c.wpb > 0;
+}
+
+// Launch parameters of a job: the context's forced ones, else the wave
+// tuner's choice t (when given), else the defaults.
+JoinLaunch job_launch(const Engine *e, const WaveTune *t = nullptr) {
     JoinLaunch l;
     l.prec_fp32 = e->cfg.prec == SJ_PREC_FP32_RECHECK;
     l.unicomp = 1;
-    l.grab = e->cfg.grab > 0 ? e->cfg.grab : 1;
-    l.nbuf = e->cfg.nbuf > 0 ? e->cfg.nbuf : 0;
-    l.eb = e->cfg.staging > 0 ? e->cfg.staging : 0;
-    l.slots = e->cfg.slots > 0 ? e->cfg.slots : 0;
+    if (launch_forced_cfg(e->cfg) || !t) {
+        l.grab = e->cfg.grab > 0 ? e->cfg.grab : 1;
+        l.nbuf = e->cfg.nbuf > 0 ? e->cfg.nbuf : 0;
+        l.eb = e->cfg.staging > 0 ? e->cfg.staging : 0;
+        l.slots = e->cfg.slots > 0 ? e->cfg.slots : 0;
+    } else {
+        l.grab = t->grab;
+        l.nbuf = t->nbuf;
+        l.eb = t->eb;
+        l.slots = t->slots;
+    }
     return l;
+}
+
+// The tuning pass of a wave whose graph replay has finished (the jobs in
+// `order` are built and joined): times the multi-join launch over the whole
+// wave with candidate settings, one parameter after another, and returns
+// the best in *best (*ok false when a timed launch failed: the defaults
+// are then launched once more, so that the wave still ends with a complete
+// result).  Each timed launch clears the jobs' counters and writes every
+// result again.
+sj_status tune_wave(Error &err, Engine *e, const std::vector<int> &order, std::vector<JobMem> &mem,
+                    WaveTune *best, bool *ok) {
+    cudaStream_t s = e->st;
+    MultiJobs *MJ = e->h_mj;
+    const int nj = (int)order.size();
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    SJ_CUDA_TRY(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(ev[0]);
+        return fail(err, SJ_ECUDA, "cudaEventCreate failed");
+    }
+    auto time_it = [&](const WaveTune &t, double *ms) -> sj_status {
+        const JoinLaunch l = job_launch(e, &t);
+        int smw = 0;
+        for (int q = 0; q < nj; ++q) {
+            const int i = order[q];
+            unsigned long long *misc = e->d_misc + (size_t)i * kMiscWords;
+            SJ_TRY(fill_join_args(err, mem[i].view, l, 0, 0xffffffffu, mem[i].out, mem[i].cap, misc,
+                                  reinterpret_cast<uint32_t *>(misc + 4),
+                                  reinterpret_cast<uint32_t *>(misc + 5), 0, MJ->job[q]));
+            smw = std::max(smw, MJ->job[q].sm_warp);
+        }
+        for (int q = 0; q < nj; ++q) MJ->job[q].sm_warp = smw;
+        MJ->n = (uint32_t)nj;
+        int wpb = 0, per_sm = 0;
+        SJ_TRY(block_shape(err, multi_join_fn(), smw, 0, e->device, &wpb, &per_sm));
+        SJ_CUDA_TRY(cudaMemsetAsync(e->d_misc, 0, sizeof(unsigned long long) * kMultiJobs * kMiscWords, s));
+        void *args[] = {MJ};
+        SJ_CUDA_TRY(cudaEventRecord(ev[0], s));
+        SJ_CUDA_TRY(cudaLaunchKernel(multi_join_fn(), dim3((unsigned)(per_sm * e->sms)),
+                                     dim3((unsigned)(wpb * 32)), args, (size_t)smw * wpb, s));
+        note_launch();
+        SJ_CUDA_TRY(cudaEventRecord(ev[1], s));
+        SJ_CUDA_TRY(cudaEventSynchronize(ev[1]));
+        float t_ms = 0;
+        SJ_CUDA_TRY(cudaEventElapsedTime(&t_ms, ev[0], ev[1]));
+        *ms = t_ms;
+        return SJ_OK;
+    };
+    WaveTune cur;   // the defaults
+    double t_cur = 0;
+    sj_status st = time_it(cur, &t_cur);
+    auto try_one = [&](WaveTune c) {
+        if (st != SJ_OK) return;
+        double t = 0;
+        st = time_it(c, &t);
+        if (st == SJ_OK && t < 0.97 * t_cur) {
+            cur = c;
+            t_cur = t;
+        }
+    };
+    const int grabs[] = {2, 4, 8};
+    for (int g : grabs) { WaveTune c = cur; c.grab = g; try_one(c); }
+    const int nbufs[] = {2, 3, 4};
+    for (int nb : nbufs) { WaveTune c = cur; c.nbuf = nb; try_one(c); }
+    const int ebs[] = {256, 512, 1024};
+    for (int eb : ebs) { WaveTune c = cur; c.eb = eb; try_one(c); }
+    const int slotss[] = {1, 2};
+    for (int sl : slotss) { WaveTune c = cur; c.slots = sl; try_one(c); }
+    *ok = st == SJ_OK;
+    if (st != SJ_OK) {
+        // the wave must still end with a complete result: the defaults once more
+        cudaGetLastError();
+        err = Error();
+        double t = 0;
+        cur = WaveTune();
+        st = time_it(cur, &t);
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    *best = cur;
+    return st;
 }
 
 sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
@@ -667,6 +831,34 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         mem[i].est = uniform_pairs(g.n, g.d, g.eps, side);
     }
     std::stable_sort(run.begin(), run.end(), [&](int a, int b) { return mem[a].est > mem[b].est; });
+    // the wave tuner: the choice for this wave's key, else (first wave of
+    // the key) a tuning pass after the graph replay
+    uint64_t wave_points = 0;
+    for (int i : run) wave_points += jobs[i]->n;
+    const std::pair<int, int> wkey = wave_key(e, wave_points);
+    WaveTune wt;
+    bool have_wt = false, tune_now = false;
+    if (e->cfg.autotune && !launch_forced_cfg(e->cfg) && wave_points >= kWaveTuneMinPoints) {
+        std::lock_guard<std::mutex> lk(g_wave_mu);
+        auto it = g_wave_tuned.find(wkey);
+        if (it != g_wave_tuned.end()) {
+            wt = it->second;
+            have_wt = true;
+        } else if (!g_wave_pending.count(wkey)) {
+            g_wave_pending.insert(wkey);
+            tune_now = true;
+        }
+    }
+    // a pending key is released on every path out of this wave
+    struct PendingRelease {
+        std::pair<int, int> k;
+        bool on;
+        ~PendingRelease() {
+            if (!on) return;
+            std::lock_guard<std::mutex> lk(g_wave_mu);
+            g_wave_pending.erase(k);
+        }
+    } pending_release{wkey, tune_now};
     std::vector<int> order;
     for (int i : run) {
         EngJob &J = *jobs[i];
@@ -751,7 +943,7 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         v.lut.p = sl.lut;
         v.items.p = sl.items;
         v.counts_dev.p = sl.mm;
-        const JoinLaunch l = job_launch(e);
+        const JoinLaunch l = job_launch(e, have_wt ? &wt : nullptr);
         JoinArgs &a = MJ->job[slot];
         if (fill_join_args(e2, v, l, 0, 0xffffffffu, m.out, m.cap, sl.misc,
                            reinterpret_cast<uint32_t *>(sl.misc + 4),
@@ -774,6 +966,15 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         SJ_TRY(block_shape(err, multi_join_fn(), sm_warp_max, 0, e->device, &wpb, &per_sm));
         const size_t tb = offsetof(EngTable, slot) + nj * sizeof(EngSlot);
         SJ_CUDA_TRY(cudaMemcpyAsync(e->d_table, T, tb, cudaMemcpyHostToDevice, s));
+        // the graph replay holds the GPU gate shared (a tuning pass of
+        // another engine then waits for it)
+        struct SharedHold {
+            bool on = false;
+            void take() { g_gate.lock_shared(); on = true; }
+            void drop() { if (on) g_gate.unlock_shared(); on = false; }
+            ~SharedHold() { drop(); }
+        } hold;
+        hold.take();
         cudaKernelNodeParams kp = {};
         void *args[] = {MJ};
         kp.func = const_cast<void *>(multi_join_fn());
@@ -785,12 +986,45 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
         SJ_CUDA_TRY(cudaGraphLaunch(e->exec, s));
         for (uint64_t q = 0; q < e->stats.kernel_nodes; ++q) note_launch();
         e->stats.graph_launches++;
-        SJ_CUDA_TRY(cudaMemcpyAsync(e->h_misc, e->d_misc,
-                                    sizeof(unsigned long long) * kMultiJobs * kMiscWords,
-                                    cudaMemcpyDeviceToHost, s));
+        if (!tune_now)
+            SJ_CUDA_TRY(cudaMemcpyAsync(e->h_misc, e->d_misc,
+                                        sizeof(unsigned long long) * kMultiJobs * kMiscWords,
+                                        cudaMemcpyDeviceToHost, s));
         SJ_CUDA_TRY(cudaStreamSynchronize(s));
+        hold.drop();
+        if (tune_now) {
+            // the first wave of its key: re-joined with each candidate
+            // setting while no other wave runs
+            const double tt0 = now_ms();
+            struct ExclusiveHold {
+                ExclusiveHold() { g_gate.lock(); }
+                ~ExclusiveHold() { g_gate.unlock(); }
+            } excl;
+            WaveTune best;
+            bool ok = false;
+            SJ_TRY(tune_wave(err, e, order, mem, &best, &ok));
+            if (ok) {
+                std::lock_guard<std::mutex> lk(g_wave_mu);
+                g_wave_tuned[wkey] = best;
+            }
+            wt = best;
+            e->stats.tuned_waves++;
+            e->stats.ms_tune += now_ms() - tt0;
+            SJ_CUDA_TRY(cudaMemcpyAsync(e->h_misc, e->d_misc,
+                                        sizeof(unsigned long long) * kMultiJobs * kMiscWords,
+                                        cudaMemcpyDeviceToHost, s));
+            SJ_CUDA_TRY(cudaStreamSynchronize(s));
+        }
     }
     const double t3 = now_ms();
+    {
+        const JoinLaunch l = job_launch(e, (have_wt || tune_now) ? &wt : nullptr);
+        e->stats.last_tuned = tune_now ? 2 : (have_wt ? 1 : 0);
+        e->stats.last_grab = l.grab;
+        e->stats.last_nbuf = l.nbuf;
+        e->stats.last_eb = l.eb;
+        e->stats.last_slots = l.slots;
+    }
 
     // 3. counts, reruns after overflow, pairs to the host
     std::vector<int> ready;
@@ -920,6 +1154,11 @@ sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k,
     }
     if (cudaStreamSynchronize(e->st) != cudaSuccess) cudaGetLastError();
     return st;
+}
+
+void engine_tune_reset() {
+    std::lock_guard<std::mutex> lk(g_wave_mu);
+    g_wave_tuned.clear();
 }
 
 }  // namespace sj

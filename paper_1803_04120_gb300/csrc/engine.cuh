@@ -27,6 +27,11 @@ struct EngJob {
 struct EngStats {
     uint64_t waves = 0, jobs = 0, graph_launches = 0, kernel_nodes = 0;
     uint64_t overflow_reruns = 0, standalone = 0;
+    uint64_t tuned_waves = 0;    // waves whose multi-join launch was tuned
+    double ms_tune = 0;          // host wall time of those tuning passes
+    // the last wave's launch: 0 defaults (or forced), 1 the wave tuner's
+    // cached choice, 2 tuned by that wave; its parameters (0: by dimension)
+    int last_tuned = 0, last_grab = 1, last_nbuf = 0, last_eb = 0, last_slots = 0;
     double ms_bounds = 0, ms_graph = 0, ms_output = 0;
 };
 
@@ -46,6 +51,9 @@ void engine_destroy(Engine *e);
 sj_status engine_run(Error &err, Engine *e, EngJob *const *jobs, int k,
                      void (*on_done)(void *user, int job) = nullptr, void *user = nullptr);
 EngStats engine_stats(const Engine *e);
+// Forgets the choices of the wave tuner (the next wave of every key is
+// tuned again).
+void engine_tune_reset();
 
 // Device bytes a job is expected to hold in the engine (points, index,
 // result buffer), from the bounding box of a sample of its points, and the

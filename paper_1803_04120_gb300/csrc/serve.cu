@@ -357,6 +357,8 @@ sj_status sj_serve_stats(sj_ctx *ctx, sj_serve_info *out) {
     for (Engine *E : S->engines) {
         const EngStats es = engine_stats(E);
         g += es.graph_launches;
+        out->tuned_waves += es.tuned_waves;
+        out->ms_tune += es.ms_tune;
         out->ms_bounds += es.ms_bounds;
         out->ms_graph += es.ms_graph;
         out->ms_output += es.ms_output;
@@ -397,6 +399,8 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
     sj_status first = SJ_OK;
     std::string first_msg;
     uint64_t pairs = 0, evals = 0, rechecks = 0, waves = 0, reruns = 0;
+    int tuned = 0;
+    EngStats last;
     const double t0 = now_ms();
     for (uint64_t b = 0; b < n_jobs;) {
         std::vector<EngJob> wave;
@@ -423,6 +427,8 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
         for (EngJob &e : wave) ptrs.push_back(&e);
         const sj_status st = engine_run(err, E, ptrs.data(), (int)ptrs.size());
         ++waves;
+        last = engine_stats(E);
+        tuned = std::max(tuned, last.last_tuned);
         const uint64_t base = b - wave.size();
         for (size_t q = 0; q < wave.size(); ++q) {
             sj_status js = st != SJ_OK ? st : wave[q].st;
@@ -456,6 +462,12 @@ sj_status sj_selfjoin_multi(sj_ctx *ctx, const sj_job *jobs, uint64_t n_jobs, sj
     ctx->stats.retries = (uint32_t)reruns;
     ctx->stats.ms_total = now_ms() - t0;
     ctx->stats.kernel_launches = launches_so_far() - l0;
+    // the multi-join launch parameters of the last wave; tuned: the most
+    // any wave of the call saw (2 when one was tuned)
+    ctx->stats.tuned = tuned;
+    ctx->stats.grab = last.last_grab;
+    ctx->stats.nbuf = last.last_nbuf;
+    ctx->stats.staging = last.last_eb;
     ctx->last_err = first == SJ_OK ? std::string() : first_msg;
     return first;
 }

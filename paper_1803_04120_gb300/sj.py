@@ -37,6 +37,7 @@ ABI_FUNCTIONS = (
     "sj_serve_stats", "sj_selfjoin_shard_device", "sj_shard_bounds", "sj_shard_bounds_cost",
     "sj_selfjoin_bruteforce_device", "sj_join2_device", "sj_fp32_margin_frame",
     "sj_fp32_margin_diff", "sj_fp32_margin_hd", "sj_fp32_fma_rate", "sj_fp64_fma_rate",
+    "sj_tune_reset",
 )
 
 
@@ -92,7 +93,8 @@ class sj_serve_info(ctypes.Structure):
                 ("mem_in_use", ctypes.c_uint64), ("inflight", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("max_concurrent_waves", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("ms_bounds", ctypes.c_double),
-                ("ms_graph", ctypes.c_double), ("ms_output", ctypes.c_double)]
+                ("ms_graph", ctypes.c_double), ("ms_output", ctypes.c_double),
+                ("tuned_waves", ctypes.c_uint64), ("ms_tune", ctypes.c_double)]
 
 
 CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
@@ -120,6 +122,7 @@ def load(build: bool = True):
         PP = ctypes.POINTER(ctypes.c_void_p)
         sig = {
             "sj_config_default": (None, [ctypes.POINTER(sj_config)]),
+            "sj_tune_reset": (None, []),
             "sj_create": (i32, [ctypes.POINTER(sj_config), PP]),
             "sj_destroy": (None, [P]),
             "sj_last_error": (ctypes.c_char_p, [P]),
@@ -621,6 +624,12 @@ def sj_fp64_fma_rate(device: int = 0):
     if st != SJ_OK:
         raise SJError(st, "sj_fp64_fma_rate failed")
     return tf.value, ms.value
+
+
+def sj_tune_reset():
+    """Forgets every choice of the launch tuners of the process (single joins
+    and many-join waves); the next join or wave of each key is tuned again."""
+    load().sj_tune_reset()
 
 
 def sj_shard_bounds(item_block, rank: int, world: int):

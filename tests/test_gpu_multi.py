@@ -100,6 +100,34 @@ def test_multi_per_job_errors_and_device_inputs():
         assert ctx.sj_selfjoin_multi([]) == []
 
 
+@pytest.mark.parametrize("prec", [sj.SJ_PREC_FP32_RECHECK, sj.SJ_PREC_FP64])
+def test_wave_tuner_times_the_wave_and_keeps_the_result(prec):
+    # a wave of 2^17 points or more is tuned the first time its key is met:
+    # every job equals the oracle on the tuning wave (whose result is that of
+    # the last timed launch), on the next wave (the cached choice) and with
+    # the tuner off (the defaults)
+    jobs = mixed_jobs(5, 48, n_lo=2000, n_hi=9000)
+    assert sum(p.shape[0] for p, _ in jobs) >= 1 << 17
+    want = [oracle_keys(p, e) for p, e in jobs]
+    sj.sj_tune_reset()
+    with sj.Context(prec=prec) as ctx:
+        first = ctx.sj_selfjoin_multi(jobs)
+        st1 = ctx.sj_last_stats()
+        again = ctx.sj_selfjoin_multi(jobs)
+        st2 = ctx.sj_last_stats()
+    with sj.Context(prec=prec, autotune=False) as ctx:
+        fixed = ctx.sj_selfjoin_multi(jobs)
+        st0 = ctx.sj_last_stats()
+    assert (st1["tuned"], st2["tuned"], st0["tuned"]) == (2, 1, 0)
+    assert (st0["grab"], st0["nbuf"], st0["staging"]) == (1, 0, 0)
+    assert st2["grab"] in (1, 2, 4, 8) and st2["nbuf"] in (0, 2, 3, 4)
+    assert st2["staging"] in (0, 256, 512, 1024)
+    for w, a, b, c in zip(want, first, again, fixed):
+        assert np.array_equal(keys(a), w)
+        assert np.array_equal(keys(b), w)
+        assert np.array_equal(keys(c), w)
+
+
 def test_multi_sorted_results():
     jobs = mixed_jobs(4, 6)
     with sj.Context(sorted=True) as ctx:
