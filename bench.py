@@ -567,14 +567,20 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
                       "req_per_s": round(n_req / wall_poi, 1),
                       "pairs_per_s": round(p_poi / wall_poi, 1),
                       "p50_ms": _pct(lat_poi, 50), "p99_ms": _pct(lat_poi, 99)})
-    info = ctx_on.sj_serve_stats()
-    ctx_on.close()
-    # the same saturated stream with the fixed launch parameters
+    # the saturated stream with the wave tuner's choices and with the fixed
+    # launch parameters, runs interleaved (two each)
     ctx_off = sj.Context(device=dev, max_inflight=64, serve_mem_bytes=64 << 30, autotune=False)
     run([0.0] * nb, ctx_off)
-    p_fix, wall_fix, lat_fix = run([0.0] * n_req, ctx_off)
+    cmp_on, cmp_off = [], []
+    for _ in range(2):
+        for ctx_, acc in ((ctx_off, cmp_off), (ctx_on, cmp_on)):
+            p_c, wall_c, lat_c = run([0.0] * n_req, ctx_)
+            assert p_c == p_sat
+            acc.append({"pairs_per_s": round(p_c / wall_c, 1), "p50_ms": _pct(lat_c, 50),
+                        "p99_ms": _pct(lat_c, 99)})
     ctx_off.close()
-    assert p_fix == p_sat
+    info = ctx_on.sj_serve_stats()
+    ctx_on.close()
     return {
         "requests": n_req, "pairs": p_sat,
         "request_mix": "n log-uniform [1e3,1e6], d uniform {2..6}, eps for U[8,128] mean neighbours, "
@@ -582,9 +588,8 @@ def serving_bench(dev: int, n_req: int, seed: int = 5, baseline_req: int = 500):
         "saturated": {"pairs_per_s": round(p_sat / wall_sat, 1), "req_per_s": round(rate_sat, 1),
                       "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99)},
         "sweep": sweep,
-        "saturated_fixed_launch": {"pairs_per_s": round(p_fix / wall_fix, 1),
-                                   "req_per_s": round(n_req / wall_fix, 1),
-                                   "p50_ms": _pct(lat_fix, 50), "p99_ms": _pct(lat_fix, 99)},
+        "saturated_wave_tuner_vs_fixed_launch": {"wave_tuner": cmp_on, "fixed": cmp_off,
+                                                 "order": "fixed, tuner, fixed, tuner"},
         "wave_tuner": {"tuned_waves": info["tuned_waves"], "ms_tune": round(info["ms_tune"], 1),
                        "tuned_waves_in_timed_passes": info["tuned_waves"] - tune_info["tuned_waves"]},
         "one_at_a_time_fp64": {"requests": nb, "pairs_per_s": round(tot64 / wall64, 1),
@@ -616,28 +621,24 @@ def multi_bench(dev: int, reps: int, n_jobs: int = 64, seed: int = 7):
     reqs = datagen.serving_requests(n_jobs, seed, rate_hz=1.0)
     pts = [datagen.uniform(r["n"], r["d"], seed=7000 + k) for k, r in enumerate(reqs)]
     jobs = [(p, r["eps"]) for p, r in zip(pts, reqs)]
-    with sj.Context(device=dev, autotune=False) as c:
-        counts = c.sj_selfjoin_multi(jobs, copy=False)          # engines, graphs, pools
-        t_fixed = []
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            got = c.sj_selfjoin_multi(jobs, copy=False)
-            t_fixed.append(time.perf_counter() - t0)
-            assert got == counts
-    with sj.Context(device=dev) as c:
-        sj.sj_tune_reset()
+    sj.sj_tune_reset()
+    with sj.Context(device=dev) as c, sj.Context(device=dev, autotune=False) as cf:
         t0 = time.perf_counter()
-        assert c.sj_selfjoin_multi(jobs, copy=False) == counts  # waves tuned here
+        counts = c.sj_selfjoin_multi(jobs, copy=False)          # waves tuned here
         t_tuning = time.perf_counter() - t0
+        assert cf.sj_selfjoin_multi(jobs, copy=False) == counts  # engines, graphs, pools
+        assert c.sj_selfjoin_multi(jobs, copy=False) == counts
         total = sum(counts)
-        t_multi = []
+        # the wave tuner's choice and the fixed launch parameters, calls interleaved
+        t_multi, t_fixed = [], []
         for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            got = c.sj_selfjoin_multi(jobs, copy=False)
-            t_multi.append(time.perf_counter() - t0)
-            assert got == counts
+            for ctx_, t_ in ((cf, t_fixed), (c, t_multi)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                got = ctx_.sj_selfjoin_multi(jobs, copy=False)
+                t_.append(time.perf_counter() - t0)
+                assert got == counts
+        c.sj_selfjoin_multi(jobs, copy=False)
         lst = c.sj_last_stats()
         choice = {"tuned": lst["tuned"], "grab": lst["grab"], "nbuf": lst["nbuf"],
                   "staging": lst["staging"], "waves": lst["batches"]}
@@ -679,7 +680,7 @@ def multi_bench(dev: int, reps: int, n_jobs: int = 64, seed: int = 7):
             "job_mix": "n log-uniform [1e3, 1e6], d uniform {2..6}, eps for U[8, 128] mean "
                        "neighbours, uniform [0, 100]^d, one seeded set per job; host inputs are "
                        "pageable numpy arrays for the host-pair rows",
-            "statistic": "median of %d calls" % reps}
+            "statistic": "median of %d calls (wave-tuner and fixed-launch calls interleaved)" % reps}
 
 
 def stream_bench(dev: int, reps: int):
