@@ -495,13 +495,19 @@ constexpr uint32_t kDirectPairs = 128;
 // (t, lane) order: at step t the pairs (p, q) of the active lanes, then
 // their (q, p) under UNICOMP.  Lane l holds the id of query l in qid_l; the
 // query id of a hit comes by shuffle.  Global destinations are bounded by
-// cap.
+// cap.  Positions are kept relative to base in 32 bits (a chunk holds at
+// most 2 * 32 * 32 * CPL pairs).
 template <int CPL, bool UNI, bool GLOBAL>
 __device__ __forceinline__ void put_hits(uint32_t (&m)[CPL], const uint32_t (&cid)[CPL],
                                          uint32_t qid_l, uint32_t c, uint64_t base, uint2 *dst,
                                          uint64_t cap, int lane) {
     constexpr uint32_t kPP = UNI ? 2u : 1u;
     const unsigned lt = (1u << lane) - 1u;
+    uint2 *const out = dst + base;
+    // pairs that still fit below cap, from base on
+    const uint32_t room =
+        GLOBAL ? (uint32_t)(cap > base ? min(cap - base, (uint64_t)0xffffffffu) : 0ull) : 0xffffffffu;
+    uint32_t rel = 0;
     for (uint32_t t = 0;; ++t) {
         const bool act = t < c;
         const unsigned bm = __ballot_sync(0xffffffffu, act);
@@ -522,18 +528,18 @@ __device__ __forceinline__ void put_hits(uint32_t (&m)[CPL], const uint32_t (&ci
         }
         const uint32_t qid = __shfl_sync(0xffffffffu, qid_l, q);
         if (act) {
-            const uint64_t pos = base + __popc(bm & lt);
+            const uint32_t p = rel + __popc(bm & lt);
             if (GLOBAL) {
                 // streaming stores: the pairs are never read back, so they
                 // should not displace the candidate records from L2
-                if (pos < cap) __stcs(&dst[pos], make_uint2(qid, cand));
-                if (UNI && pos + nb < cap) __stcs(&dst[pos + nb], make_uint2(cand, qid));
+                if (p < room) __stcs(&out[p], make_uint2(qid, cand));
+                if (UNI && p + nb < room) __stcs(&out[p + nb], make_uint2(cand, qid));
             } else {
-                dst[pos] = make_uint2(qid, cand);
-                if (UNI) dst[pos + nb] = make_uint2(cand, qid);
+                out[p] = make_uint2(qid, cand);
+                if (UNI) out[p + nb] = make_uint2(cand, qid);
             }
         }
-        base += kPP * nb;
+        rel += kPP * nb;
     }
 }
 
