@@ -68,6 +68,11 @@ namespace {
 // two below, where the smaller registers and ring let three blocks reside
 // (d = 4: 1.28 ms against 1.35 ms with four; d = 5: 2.63 against 2.41).
 __host__ __device__ constexpr int cpl_for(int d, bool f32) { return f32 ? (d <= 4 ? 2 : 4) : 2; }
+// FP32 strides in floats (the host's index and launch set the same): a
+// point record x_0 .. x_{d-1}, id padded to 16 bytes; a staged query record
+// m_0 .. m_{d-1}, pp, id padded to 16 bytes.  Compile-time in the kernel.
+__host__ __device__ constexpr int rs32_for(int d) { return (d + 1 + 3) / 4 * 4; }
+__host__ __device__ constexpr int qrs32_for(int d) { return (d + 2 + 3) & ~3; }
 // Default depth of the chunk ring (a launch may choose another).
 __host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >= 4) ? 2 : 4; }
 // Staged pairs per warp: many pairs per chunk at low d want a large staging
@@ -235,10 +240,10 @@ __device__ __forceinline__ void flush(Pipe &st, const WarpSmem &ws, const JoinAr
     if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)st.fill);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (!a.count_only) {
-        for (uint32_t i = lane; i < st.fill; i += 32) {
-            const uint64_t pos = base + i;
-            if (pos < a.cap) __stcs(&a.out[pos], ws.emit[i]);
-        }
+        // positions relative to the reservation, bounded by cap once
+        uint2 *const out = a.out + base;
+        const uint32_t n = a.cap > base ? (uint32_t)min((uint64_t)(a.cap - base), (uint64_t)st.fill) : 0u;
+        for (uint32_t i = lane; i < n; i += 32) __stcs(&out[i], ws.emit[i]);
     }
     __syncwarp();
     st.fill = 0;
@@ -407,7 +412,7 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
             o[j] = ((float)(a.frame == SJ_FRAME_CELL ? (c[j] & 3) : c[j]) + 0.5f) * a.w32;
         if (lane < (int)nq) {
             const float *r = reinterpret_cast<const float *>(rec + (size_t)(q0 + lane) * rsb);
-            float *qd = reinterpret_cast<float *>(ws.q[sl]) + (size_t)lane * a.qrs;
+            float *qd = reinterpret_cast<float *>(ws.q[sl]) + (size_t)lane * qrs32_for(D);
             float pp = 0.0f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
@@ -562,13 +567,14 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
 
     if (F32) {
         constexpr int NP = CPL / 2;
+        constexpr int QRS = qrs32_for(D), RS = rs32_for(D);
         const float hi32 = a.hi32, lo32 = a.lo32;
         f2_t z[NP][D], qq2[NP];
         uint32_t cid[CPL];
         if (FR == 2 ? a.frame == SJ_FRAME_CELL : FR == 1)
-            load_candidates<D, CPL, true>(buf, a.rs, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
+            load_candidates<D, CPL, true>(buf, RS, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
         else
-            load_candidates<D, CPL, false>(buf, a.rs, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
+            load_candidates<D, CPL, false>(buf, RS, clen, lane, hd->o, a.w4, a.inv_w4, z, qq2, cid);
         const float *qbase = reinterpret_cast<const float *>(ws.q[sl]);
         if (UNI && ch == 0) {
             // UNICOMP: the item's self-pairs, one per query point; every
@@ -576,7 +582,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
             // search meets the query itself as an ordinary hit.)
             if (st.fill + nq > (uint32_t)a.eb) flush(st, ws, a, lane);
             if (!a.count_only && lane < (int)nq) {
-                const uint32_t qid = __float_as_uint(qbase[(size_t)lane * a.qrs + D + 1]);
+                const uint32_t qid = __float_as_uint(qbase[(size_t)lane * QRS + D + 1]);
                 ws.emit[st.fill + lane] = make_uint2(qid, qid);
             }
             st.fill += nq;
@@ -601,7 +607,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         int mn = 0x7fffffff;
         for (int qi = (int)nq - 1; qi >= 0; --qi) {
             float sv[CPL];
-            eval_query<D, NP, true>(qbase + (size_t)qi * a.qrs, z, qq2, sv, mh);
+            eval_query<D, NP, true>(qbase + (size_t)qi * QRS, z, qq2, sv, mh);
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
                 m[s] = __funnelshift_l(__float_as_uint(sv[s]), m[s], 1);
@@ -635,7 +641,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                     const uint32_t q = __ffs(w) - 1;
                     w &= w - 1;
                     float sv2[2];
-                    eval_query<D, 1>(qbase + (size_t)q * a.qrs, &z[s >> 1], &qq2[s >> 1], sv2);
+                    eval_query<D, 1>(qbase + (size_t)q * QRS, &z[s >> 1], &qq2[s >> 1], sv2);
                     if (sv2[s & 1] > lo32) b[s] |= 1u << q;
                 }
             }
@@ -654,7 +660,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                     const uint32_t q = __ffs(w) - 1;
                     w &= w - 1;
                     ++rechecks;
-                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + D + 1]);
+                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * QRS + D + 1]);
                     if (!exact_member_ni(a.qpts + (size_t)qid * D, a.pts + (size_t)cid[s] * D, D, a.E2))
                         m[s] &= ~(1u << q);
                 }
@@ -674,9 +680,9 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         for (int s = 0; s < CPL; ++s) left += __popc(m[s]);
         const uint32_t hits = __reduce_add_sync(0xffffffffu, left);
         if (hits == 0) return;
-        const uint32_t qid_l =
-            lane < (int)nq ? __float_as_uint(qbase[(size_t)lane * a.qrs + D + 1]) : 0u;
         if (hits * kPP >= kDirectPairs) {
+            const uint32_t qid_l =
+                lane < (int)nq ? __float_as_uint(qbase[(size_t)lane * QRS + D + 1]) : 0u;
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(&a.counter[0], (unsigned long long)hits * kPP);
             base = __shfl_sync(0xffffffffu, base, 0);
@@ -702,7 +708,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
                 while (w) {
                     const uint32_t q = __ffs(w) - 1;
                     w &= w - 1;
-                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * a.qrs + D + 1]);
+                    const uint32_t qid = __float_as_uint(qbase[(size_t)q * QRS + D + 1]);
                     ws.emit[pos] = make_uint2(qid, cid[s]);
                     if (UNI) ws.emit[pos + 1] = make_uint2(cid[s], qid);
                     pos += kPP;
@@ -1169,7 +1175,9 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     const int rsb = a.rs * esz;
     // query record: FP32 m_0 .. m_{d-1}, pp, id -> d + 2 floats;
     // FP64: x_0..x_{d-1}, id
-    a.qrs = f32 ? ((d + 2 + 3) & ~3) : ((d + 1 + 1) & ~1);
+    a.qrs = f32 ? qrs32_for(d) : ((d + 1 + 1) & ~1);
+    // the search kernel takes the FP32 record stride as a compile-time constant
+    if (f32 && !hd && a.rs != rs32_for(d)) return fail(err, SJ_EINVAL, "FP32 record stride");
     a.cb = 32 * cpl_for(d, f32);
     a.sm_ranges = round16(a.n_templates * (int)sizeof(uint2));
     a.sm_queries = round16(kQueryBlock * a.qrs * esz);
