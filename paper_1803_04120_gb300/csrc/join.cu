@@ -379,7 +379,7 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
                                              const JoinArgs &a, uint32_t n_cells, int lane,
                                              unsigned long long &evals) {
     typedef typename std::conditional<F32, float, double>::type T;
-    const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
+    const uint32_t rsb = F32 ? (uint32_t)rs32_for(D) * 4u : (uint32_t)a.rs * sizeof(T);
     // the query side: the item's cell and points (the candidate side is
     // read through a.lut / a.B / a.G and the ranges)
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.qrec32)
@@ -563,7 +563,8 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
     const uint32_t clen = min((uint32_t)CB, K - kb);
     const bool home_chunk = UNI && kb < home_len;
     const uint32_t ql_base = hd->qb * kQueryBlock;
-    const unsigned char *buf = ws.ring + (size_t)r * a.sm_chunk;
+    const unsigned char *buf =
+        ws.ring + (size_t)r * (F32 ? CB * rs32_for(D) * 4 : a.sm_chunk);
 
     if (F32) {
         constexpr int NP = CPL / 2;
@@ -780,7 +781,9 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     const uint32_t smask = a.slots > 1 ? 1u : 0u;   // item slot of a sequence number
     typedef typename std::conditional<F32, float, double>::type T;
     const WarpSmem ws = carve(smem, a, warp, nbuf);
-    const uint32_t rsb = (uint32_t)a.rs * sizeof(T);
+    // FP32: record and chunk sizes are compile-time (the host checks the stride)
+    const uint32_t rsb = F32 ? (uint32_t)rs32_for(D) * 4u : (uint32_t)a.rs * sizeof(T);
+    const int sm_chunk = F32 ? CB * rs32_for(D) * 4 : a.sm_chunk;
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
                                    : reinterpret_cast<const unsigned char *>(a.rec64);
 
@@ -844,7 +847,7 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
                 // wait for that chunk runs out (no copy is in flight for it)
                 if (!(a.stall && st.issued == 0 && blockIdx.x == 0 && warp == 0))
                     issue_chunk<CB>(ws, ps, st.p_chunk, (int)st.p_slot, st.rcur, rec, rsb, lane,
-                                    a.sm_chunk);
+                                    sm_chunk);
                 ++st.issued;
                 ++st.p_chunk;
                 st.p_slot = st.p_slot + 1 == nbuf ? 0u : st.p_slot + 1;
