@@ -73,6 +73,10 @@ __host__ __device__ constexpr int cpl_for(int d, bool f32) { return f32 ? (d <= 
 // m_0 .. m_{d-1}, pp, id padded to 16 bytes.  Compile-time in the kernel.
 __host__ __device__ constexpr int rs32_for(int d) { return (d + 1 + 3) / 4 * 4; }
 __host__ __device__ constexpr int qrs32_for(int d) { return (d + 2 + 3) & ~3; }
+// FP64 strides in doubles: a point record and a staged query record are
+// both x_0 .. x_{d-1}, id padded to 16 bytes.
+__host__ __device__ constexpr int rs64_for(int d) { return (d + 1 + 1) / 2 * 2; }
+__host__ __device__ constexpr int rs_for(int d, bool f32) { return f32 ? rs32_for(d) : rs64_for(d); }
 // Default depth of the chunk ring (a launch may choose another).
 __host__ __device__ constexpr int nbuf_for(int d, bool f32) { return (f32 && d >= 4) ? 2 : 4; }
 // Staged pairs per warp: many pairs per chunk at low d want a large staging
@@ -379,7 +383,7 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
                                              const JoinArgs &a, uint32_t n_cells, int lane,
                                              unsigned long long &evals) {
     typedef typename std::conditional<F32, float, double>::type T;
-    const uint32_t rsb = F32 ? (uint32_t)rs32_for(D) * 4u : (uint32_t)a.rs * sizeof(T);
+    const uint32_t rsb = (uint32_t)(rs_for(D, F32) * sizeof(T));
     // the query side: the item's cell and points (the candidate side is
     // read through a.lut / a.B / a.G and the ranges)
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.qrec32)
@@ -428,7 +432,7 @@ __device__ __forceinline__ void prepare_item(const WarpSmem &ws, int sl, uint2 i
     } else {
         if (lane < (int)nq) {
             const double *r = reinterpret_cast<const double *>(rec + (size_t)(q0 + lane) * rsb);
-            double *qd = reinterpret_cast<double *>(ws.q[sl]) + (size_t)lane * a.qrs;
+            double *qd = reinterpret_cast<double *>(ws.q[sl]) + (size_t)lane * rs64_for(D);
 #pragma unroll
             for (int j = 0; j <= D; ++j) qd[j] = r[j];
         }
@@ -564,7 +568,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
     const bool home_chunk = UNI && kb < home_len;
     const uint32_t ql_base = hd->qb * kQueryBlock;
     const unsigned char *buf =
-        ws.ring + (size_t)r * (F32 ? CB * rs32_for(D) * 4 : a.sm_chunk);
+        ws.ring + (size_t)r * ((CB * rs_for(D, F32) * (F32 ? 4 : 8) + 15) & ~15);
 
     if (F32) {
         constexpr int NP = CPL / 2;
@@ -727,7 +731,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
 #pragma unroll
             for (int j = 0; j < D; ++j) y[s][j] = 0.0;
             if (slot < clen) {
-                const double *rr = reinterpret_cast<const double *>(buf + (size_t)slot * a.rs * 8);
+                const double *rr = reinterpret_cast<const double *>(buf + (size_t)slot * rs64_for(D) * 8);
 #pragma unroll
                 for (int j = 0; j < D; ++j) y[s][j] = rr[j];
                 cid[s] = (uint32_t)__double_as_longlong(rr[D]);
@@ -735,7 +739,7 @@ __device__ __forceinline__ void consume_chunk(Pipe &st, const WarpSmem &ws, int 
         }
         const double *qbase = reinterpret_cast<const double *>(ws.q[sl]);
         for (uint32_t qi = 0; qi < nq; ++qi) {
-            const double *qd = qbase + (size_t)qi * a.qrs;
+            const double *qd = qbase + (size_t)qi * rs64_for(D);
             bool hit[CPL];
             bool any = false;
 #pragma unroll
@@ -781,9 +785,9 @@ __device__ __forceinline__ bool join_body(const JoinArgs &a, const uint32_t *cou
     const uint32_t smask = a.slots > 1 ? 1u : 0u;   // item slot of a sequence number
     typedef typename std::conditional<F32, float, double>::type T;
     const WarpSmem ws = carve(smem, a, warp, nbuf);
-    // FP32: record and chunk sizes are compile-time (the host checks the stride)
-    const uint32_t rsb = F32 ? (uint32_t)rs32_for(D) * 4u : (uint32_t)a.rs * sizeof(T);
-    const int sm_chunk = F32 ? CB * rs32_for(D) * 4 : a.sm_chunk;
+    // record and chunk sizes are compile-time (the host checks the stride)
+    const uint32_t rsb = (uint32_t)(rs_for(D, F32) * sizeof(T));
+    constexpr int sm_chunk = (CB * rs_for(D, F32) * (int)sizeof(T) + 15) & ~15;
     const unsigned char *rec = F32 ? reinterpret_cast<const unsigned char *>(a.rec32)
                                    : reinterpret_cast<const unsigned char *>(a.rec64);
 
@@ -1178,9 +1182,9 @@ sj_status fill_join_args(Error &err, const Index &ix, const JoinLaunch &cfg, uin
     const int rsb = a.rs * esz;
     // query record: FP32 m_0 .. m_{d-1}, pp, id -> d + 2 floats;
     // FP64: x_0..x_{d-1}, id
-    a.qrs = f32 ? qrs32_for(d) : ((d + 1 + 1) & ~1);
-    // the search kernel takes the FP32 record stride as a compile-time constant
-    if (f32 && !hd && a.rs != rs32_for(d)) return fail(err, SJ_EINVAL, "FP32 record stride");
+    a.qrs = f32 ? qrs32_for(d) : rs64_for(d);
+    // the search kernel takes the record strides as compile-time constants
+    if (!hd && a.rs != rs_for(d, f32)) return fail(err, SJ_EINVAL, "record stride");
     a.cb = 32 * cpl_for(d, f32);
     a.sm_ranges = round16(a.n_templates * (int)sizeof(uint2));
     a.sm_queries = round16(kQueryBlock * a.qrs * esz);
