@@ -221,10 +221,6 @@ JoinLaunch default_launch(const sj_ctx *ctx) {
     return l;
 }
 
-bool launch_forced(const sj_config &c) {
-    return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.wpb > 0 || c.slots > 0;
-}
-
 JoinLaunch launch_cfg(const sj_ctx *ctx) { return ctx->launch; }
 
 // Launch parameters of the join on ix: the defaults, or with autotune = 1

@@ -620,17 +620,13 @@ std::pair<int, int> wave_key(const Engine *e, uint64_t points) {
                           (int)std::lround(std::log2(std::max(1.0, per_sm))));
 }
 
-bool launch_forced_cfg(const sj_config &c) {
-    return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.slots > 0 || c.wpb > 0;
-}
-
 // Launch parameters of a job: the context's forced ones, else the wave
 // tuner's choice t (when given), else the defaults.
 JoinLaunch job_launch(const Engine *e, const WaveTune *t = nullptr) {
     JoinLaunch l;
     l.prec_fp32 = e->cfg.prec == SJ_PREC_FP32_RECHECK;
     l.unicomp = 1;
-    if (launch_forced_cfg(e->cfg) || !t) {
+    if (launch_forced(e->cfg) || !t) {
         l.grab = e->cfg.grab > 0 ? e->cfg.grab : 1;
         l.nbuf = e->cfg.nbuf > 0 ? e->cfg.nbuf : 0;
         l.eb = e->cfg.staging > 0 ? e->cfg.staging : 0;
@@ -838,7 +834,7 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
     const std::pair<int, int> wkey = wave_key(e, wave_points);
     WaveTune wt;
     bool have_wt = false, tune_now = false;
-    if (e->cfg.autotune && !launch_forced_cfg(e->cfg) && wave_points >= kWaveTuneMinPoints) {
+    if (e->cfg.autotune && !launch_forced(e->cfg) && wave_points >= kWaveTuneMinPoints) {
         std::lock_guard<std::mutex> lk(g_wave_mu);
         auto it = g_wave_tuned.find(wkey);
         if (it != g_wave_tuned.end()) {

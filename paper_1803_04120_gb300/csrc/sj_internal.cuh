@@ -315,6 +315,9 @@ sj_status shard_items(Error &err, const Index &ix, bool uni, int rank, int world
 // (d, precision, UNICOMP, points-per-cell bucket); *tuned = 0 defaults kept,
 // 1 taken from the cache, 2 tuned now.  ix.n_cells must be known on the
 // host; a miss reads the work-item count first (read_counts).
+// True when the configuration forces a launch parameter (the tuners then
+// keep out).
+bool launch_forced(const sj_config &c);
 int tune_bucket(const Index &ix);
 int tune_bucket_ppc(double points_per_cell);
 // Smallest join (work items) the tuner times; smaller joins keep the defaults.

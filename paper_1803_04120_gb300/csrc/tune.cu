@@ -41,6 +41,10 @@ constexpr uint64_t kTuneMaxOutBytes = 512ull << 20;  // above: time count-only l
 
 }  // namespace
 
+bool launch_forced(const sj_config &c) {
+    return c.grab > 0 || c.nbuf > 0 || c.staging > 0 || c.wpb > 0 || c.slots > 0;
+}
+
 int tune_bucket_ppc(double points_per_cell) {
     return (int)std::lround(std::log2(std::max(1.0, points_per_cell)));
 }
