@@ -999,7 +999,10 @@ sj_status engine_run_impl(Error &err, Engine *e, EngJob *const *jobs, int k,
             WaveTune best;
             bool ok = false;
             SJ_TRY(tune_wave(err, e, order, mem, &best, &ok));
-            if (ok) {
+            {
+                // a pass that failed (ok false) returned the defaults: they
+                // are kept for its key, so that the key is not tuned again
+                // on every wave
                 std::lock_guard<std::mutex> lk(g_wave_mu);
                 g_wave_tuned[wkey] = best;
             }
