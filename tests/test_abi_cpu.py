@@ -37,6 +37,13 @@ def test_binding_loads_and_status_names():
     assert cfg.min_batches == 3 and cfg.out_cap_bytes == 2 << 30
 
 
+def test_tune_reset_is_host_only():
+    # forgetting the tuners' choices touches no device: callable anywhere,
+    # any number of times
+    sj.sj_tune_reset()
+    sj.sj_tune_reset()
+
+
 def test_no_device_is_an_error_not_a_fallback():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
